@@ -352,6 +352,7 @@ def two_year_two_channel(seed=1002, n_inj=20, inject=True, n_tranche=6144, L=204
     w1[:, 0] = 0.0
     w = np.stack([w1, w1])
     sd = np.sqrt(S / (4 * df))
+    sd[:, 0] = 0.0  # the DC bin carries no weight (S = inf there)
     d = np.empty((2, n_tranche, n_bins), np.complex128)
     for c in range(2):
         d[c].real = rng.standard_normal((n_tranche, n_bins)) * sd
