@@ -1,0 +1,177 @@
+/*
+ * tfs.h -- C ABI of libtfs, a B300 (sm_103a) library that evaluates the
+ * time-frequency semi-coherent detection statistic of arXiv:2510.19047
+ * ("Global time-frequency search for stellar-mass binary black holes in LISA")
+ * for large banks of inspiral templates, and its gradient.
+ *
+ * What is computed (paper notation):
+ *   For every template theta and segment n (segment length T_seg = N_t dT / N_seg,
+ *   Eq. Upsilon-seg), the tranche-decomposed complex inner products
+ *     Z_n = sum_alpha sum_{m in n} T_alpha,nm sum_{k in window} conj(d~_alpha,nm[k])
+ *           h~_nm[k] / S_alpha,nm[k] delta f                 (Eqs. inner-tf, inner-tranche-tf)
+ *     N_n = sum_alpha sum_{m in n} |T_alpha,nm|^2 sum_k |h~_nm[k]|^2 / S_alpha,nm[k] delta f
+ *   with h~_nm the Fresnel-kernel transform of the quadratic-phase tranche
+ *   (Eq. fresnel-ft, Eq. kernel-function, the paper's Fresnel forms for |z| > 6 and
+ *   |z| <= 6), N_F = 21 bins about k_c = ceil(f_nm / delta f), and
+ *     Upsilon_{N_seg} = sum_{n: N_n > 0} 4 |Z_n|^2 / N_n           (Eqs. overlap-n, Upsilon-seg)
+ *   A tranche is active iff it is not masked (gaps: a tranche that overlaps a gap
+ *   is left out of Eq. inner-tf), t'_nm < t_c, fdot_nm > 0 and its window lies in
+ *   bins [1, N_bins - 1].
+ *
+ * Templates: theta is structure-of-arrays double [8][n_tpl] in the order
+ *   (M_c [M_sun], eta, f_0 [Hz], phi_0 [rad], lambda, beta, psi, iota [rad]);
+ *   f_0, phi_0 are the GW frequency and phase at barycentre time t' = 0.
+ *   Chirp: Newtonian (pn_order 0) or 1PN TaylorT3 (pn_order 1). Response: none
+ *   (T = 1, one or two identical channels) or the long-wavelength A/E response of
+ *   a rigid constellation on a 1 AU orbit with Doppler delay t' = t + n.r(t)/c.
+ *
+ * Pointers: every array argument may be a host pointer or a device pointer of the
+ *   context's device (the library asks the CUDA runtime which). Inputs are read
+ *   or copied, never retained after the call returns. Outputs are owned by the
+ *   caller. A call runs on `stream` (a cudaStream_t, NULL = legacy default stream);
+ *   it returns before the GPU finishes only if every output pointer is a device
+ *   pointer, otherwise it synchronises the stream before returning.
+ *
+ * Errors: every entry point returns TFS_OK (0) or a negative tfs_status; a
+ *   human-readable message is then available from tfs_last_error(). No C++
+ *   exception crosses this interface. Functions are not re-entrant on one
+ *   context; distinct contexts are independent.
+ */
+#ifndef TFS_H
+#define TFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tfs_ctx tfs_ctx; /* opaque; owns all device memory it allocates */
+
+typedef enum tfs_status {
+  TFS_OK = 0,
+  TFS_ERR_ARG = -1,          /* bad argument: null pointer, size, value out of range */
+  TFS_ERR_STATE = -2,        /* data or noise weights not loaded yet */
+  TFS_ERR_NSEG = -3,         /* N_t is not divisible by a requested N_seg */
+  TFS_ERR_OOM = -4,          /* device allocation failed or over the context's cap */
+  TFS_ERR_CUDA = -5,         /* a CUDA runtime call failed (message has the detail) */
+  TFS_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+  TFS_ERR_DEVICE_CHECK = -7  /* checked mode: a kernel saw an out-of-range index */
+} tfs_status;
+
+typedef enum tfs_path {
+  TFS_PATH_FP64 = 0,  /* all-FP64 parity path, one thread per template */
+  TFS_PATH_PLAIN = 1, /* the paper's mapping: one thread per template, Eq. fresnel-ft
+                         evaluated bin by bin as printed, FP32 pixels, FP64 phase */
+  TFS_PATH_MIXED = 2  /* warp per template, lane per tranche, phase-cancelled Fresnel
+                         kernel, FP16/BF16 pixels, FP32 accumulation, double-float
+                         phase track, length-sorted persistent launch */
+} tfs_path;
+
+typedef enum tfs_pixel {
+  TFS_PIX_F32 = 0,
+  TFS_PIX_F16 = 1,
+  TFS_PIX_BF16 = 2
+} tfs_pixel;
+
+typedef struct tfs_options {
+  int path;          /* tfs_path used by tfs_eval_statistic (default MIXED) */
+  int pixel;         /* tfs_pixel: storage of d~/S and 1/S for the mixed path (default F16) */
+  int pn_order;      /* 0 Newtonian chirp, 1 1PN TaylorT3 (default 1) */
+  int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1) */
+  int checked;       /* 1: kernels bounds-check every pixel index (slower) */
+  int sort;          /* 1: length/frequency-sort templates before the mixed launch (default 1) */
+  int warps_per_cta; /* mixed path CTA size in warps; 0 = autotuned on first use */
+  int use_graph;     /* 1: replay the mixed evaluation as a CUDA graph per batch shape */
+  int profile;       /* 1: time each kernel of a call with CUDA events (tfs_last_profile) */
+  int64_t max_device_bytes; /* cap on the context's device allocations, 0 = none */
+} tfs_options;
+
+/* Default options (see the field comments). */
+void tfs_default_options(tfs_options* opt);
+
+/* Create a context on CUDA device `device` (the device becomes current for the
+ * calling thread). opt may be NULL for defaults. *out receives the handle. */
+int tfs_create(tfs_ctx** out, int device, const tfs_options* opt);
+
+/* Free every device allocation of the context and the context itself. NULL is ok. */
+int tfs_destroy(tfs_ctx* ctx);
+
+/* Replace the context's options (takes effect at the next call). */
+int tfs_set_options(tfs_ctx* ctx, const tfs_options* opt);
+int tfs_get_options(const tfs_ctx* ctx, tfs_options* opt);
+
+/* Load the time-frequency data grid d~_alpha,m[k] (Eq. inner-tranche-tf):
+ *   n_chan 1 or 2 (A, E), n_tranche N_t >= 1, n_bins >= 22 complex bins per tranche
+ *   (bin k at f_k = k / dT), dt the sample cadence (dT / dt >= 2 n_bins), dT the
+ *   tranche length [s], t0 the start time of tranche 0 [s].
+ *   d_re, d_im: double [n_chan][n_tranche][n_bins], host or device, copied.
+ * Any previously loaded data and noise weights are dropped. */
+int tfs_load_tf_data(tfs_ctx* ctx, int n_chan, int n_tranche, int n_bins, double dt,
+                     double dT, double t0, const double* d_re, const double* d_im);
+
+/* Set the noise weights 1/S_alpha,m[k] (one-sided PSD per tranche; the paper lets the
+ * PSD change between tranches, "Search extension to data with gaps") and the tranche
+ * mask (gaps: 0 = tranche overlaps a gap and is left out).
+ *   inv_psd: double [n_chan][n_tranche][n_bins], >= 0 and finite, host or device.
+ *   tranche_mask: uint8 [n_tranche], or NULL for "keep all".
+ * Forms the weighted data u = d~ w once, in every storage the paths use. */
+int tfs_set_noise_weights(tfs_ctx* ctx, const double* inv_psd, const uint8_t* tranche_mask);
+
+/* Upsilon_{N_seg} (Eq. Upsilon-seg) for n_tpl templates.
+ *   theta: double [8][n_tpl] (SoA, order above).
+ *   per_template == 0: n_seg[0..n_levels-1] are 1..4 segment counts applied to every
+ *     template, all evaluated in one pass; out_stat is double [n_levels][n_tpl] and
+ *     out_neff (optional) int32 [n_levels][n_tpl].
+ *   per_template == 1: n_seg is int32 [n_tpl], one segment count per template
+ *     (n_levels is ignored); out_stat double [n_tpl], out_neff int32 [n_tpl].
+ *   Every N_seg must divide N_t (else TFS_ERR_NSEG).
+ *   out_neff: number of segments with N_n > 0 (the chi^2 test has 2 N_eff dof).
+ *   out_diag (optional): int32 [2][n_tpl] = active tranches, active tranches that
+ *     violate the compactness condition fdot dT <= 10 delta f (Appendix A). */
+int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const int32_t* n_seg,
+                       int n_levels, int per_template, double* out_stat, int32_t* out_neff,
+                       int32_t* out_diag, void* stream);
+
+/* Upsilon_{N_seg} and its gradient d Upsilon / d theta (out_grad double [8][n_tpl]) by
+ * the adjoint of Eq. Upsilon-seg: a forward pass keeps Z_n, N_n per segment, a second
+ * pass recomputes the track and accumulates
+ *   dUpsilon = sum_n [8 Re(conj(Z_n) dZ_n) / N_n - 4 |Z_n|^2 dN_n / N_n^2].
+ * The window position and the Fresnel branch are held fixed (the almost-everywhere
+ * derivative). FP32 arithmetic with a double-float phase track. */
+int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
+                       double* out_stat, double* out_grad, void* stream);
+
+/* Indices of the k largest values of stat[n] (ties broken by the lower index), in
+ * decreasing order of stat, into out_index int64 [k]: the survivors of one stage of
+ * the adaptive N_seg ladder (Sec. "Time-frequency search statistic": N_seg is reduced
+ * as the search progresses). stat and out_index may be host or device pointers. */
+int tfs_select_top(tfs_ctx* ctx, const double* stat, int64_t n, int64_t k, int64_t* out_index,
+                   void* stream);
+
+/* One projected gradient-ascent step on a batch of templates, in place:
+ *   theta[p][i] += step[p] * grad[p][i], then clamped to [lo[p], hi[p]];
+ *   phi_0, lambda, psi are wrapped to [0, 2 pi) / [0, pi) instead of clamped.
+ * theta, grad: double [8][n] device or host; step, lo, hi: double [8] host. */
+int tfs_ascent_step(tfs_ctx* ctx, double* theta, const double* grad, int64_t n,
+                    const double* step, const double* lo, const double* hi, void* stream);
+
+/* Per-kernel GPU times [ms] of the last tfs_eval_statistic / tfs_grad_statistic call
+ * made with options.profile = 1: ms[0] set-up, ms[1] sort, ms[2] statistic kernel,
+ * ms[3] output fold/copy. Returns TFS_ERR_STATE if nothing was profiled. */
+int tfs_last_profile(const tfs_ctx* ctx, double ms[4]);
+
+/* Kernel launches issued by the last call (for launch accounting). */
+int64_t tfs_last_launch_count(const tfs_ctx* ctx);
+
+/* Message of the last error on this context ("" if none). Never NULL. */
+const char* tfs_last_error(const tfs_ctx* ctx);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFS_H */

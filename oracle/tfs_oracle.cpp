@@ -7,11 +7,15 @@
 // CPU-baseline leg of bench.py may load it; the product path never does. It shares
 // no code, header or constant table with the CUDA sources.
 //
-// Everything is FP64. The per-template evaluation is written once as templates
-// over the scalar type R: R = double gives the statistic, R = Dual (forward-mode
-// derivative in the 8 template parameters) gives its exact gradient, with the
-// window position (ceil) and the Fresnel branch held fixed, i.e. the
-// almost-everywhere derivative.
+// Inputs and outputs are FP64. The per-template evaluation is written once as
+// templates over the scalar type R: R = long double (x87 extended precision, 64-bit
+// mantissa) gives the statistic, R = Dual (FP64 forward-mode derivative in the 8
+// template parameters) gives its exact gradient, with the window position (ceil) and
+// the Fresnel branch held fixed, i.e. the almost-everywhere derivative. The value
+// path uses extended precision because the printed tranche transform takes sines of
+// arguments up to ~1e7 rad (pi v^2 / 2 and pi fdot zeta^2, which cancel) and a
+// two-year phase reaches ~1e7 rad: in FP64 those carry ~1e-9 rad of rounding, in
+// extended precision ~1e-12.
 //
 // Paper passages followed (section / equation of the paper):
 //   inner products ............ Eqs. inner-cont, inner-complex-cont, inner-all-cont
@@ -122,7 +126,11 @@ static inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
 static inline Dual& operator*=(Dual& a, const Dual& b) { a = a * b; return a; }
 
 static inline double val(double x) { return x; }
+static inline double val(long double x) { return (double)x; }
 static inline double val(const Dual& x) { return x.v; }
+static inline long double lval(double x) { return x; }
+static inline long double lval(long double x) { return x; }
+static inline long double lval(const Dual& x) { return x.v; }
 
 static inline double sin_(double x) { return std::sin(x); }
 static inline double cos_(double x) { return std::cos(x); }
@@ -132,6 +140,14 @@ static inline double exp_(double x) { return std::exp(x); }
 static inline double expm1_(double x) { return std::expm1(x); }
 static inline double log1p_(double x) { return std::log1p(x); }
 static inline double pow_(double x, double p) { return std::pow(x, p); }
+static inline long double sin_(long double x) { return std::sin(x); }
+static inline long double cos_(long double x) { return std::cos(x); }
+static inline long double sqrt_(long double x) { return std::sqrt(x); }
+static inline long double log_(long double x) { return std::log(x); }
+static inline long double exp_(long double x) { return std::exp(x); }
+static inline long double expm1_(long double x) { return std::expm1(x); }
+static inline long double log1p_(long double x) { return std::log1p(x); }
+static inline long double pow_(long double x, double p) { return std::pow(x, (long double)p); }
 static inline Dual sin_(const Dual& x) { return chain(x, std::sin(x.v), std::cos(x.v)); }
 static inline Dual cos_(const Dual& x) { return chain(x, std::cos(x.v), -std::sin(x.v)); }
 static inline Dual sqrt_(const Dual& x) {
@@ -272,6 +288,12 @@ static void fresnel_exact_value(double z, double& C, double& S) {
   }
 }
 static inline void fresnel_exact(double z, double& C, double& S) { fresnel_exact_value(z, C, S); }
+static inline void fresnel_exact(long double z, long double& C, long double& S) {
+  double c, s;
+  fresnel_exact_value((double)z, c, s);
+  C = c;
+  S = s;
+}
 static inline void fresnel_exact(const Dual& z, Dual& C, Dual& S) {
   double c, s;
   fresnel_exact_value(z.v, c, s);
@@ -537,7 +559,7 @@ static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp
       const TrackPoint<R> tp = track_point(src, resp, tm, t_anchor);
       if (!tp.alive) continue;
       if (!(val(tp.fdot) > 0.0)) continue;
-      const long kc = (long)std::ceil(val(tp.f) / g.df);
+      const long kc = (long)std::ceil(lval(tp.f) / (long double)g.df);
       if (kc - NF_HALF < 1 || kc + NF_HALF > g.n_bins - 1) continue;
       ++nact;
       if (val(tp.fdot) * g.dT > 10.0 * g.df) ++nnc;
@@ -617,12 +639,13 @@ int oracle_statistic(int n_chan, int n_tranche, int n_bins, double dT, double t0
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int64_t i = 0; i < n_tpl; ++i) {
-    double th[NPAR];
+    long double th[NPAR];
     for (int p = 0; p < NPAR; ++p) th[p] = theta[p * n_tpl + i];
-    double ups;
+    long double ups;
     Diag dg;
-    const int neff = statistic_one<double>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, &dg);
-    out_stat[i] = ups;
+    const int neff =
+        statistic_one<long double>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, &dg);
+    out_stat[i] = (double)ups;
     if (out_neff) out_neff[i] = neff;
     if (out_nact) out_nact[i] = dg.n_active;
     if (out_nnc) out_nnc[i] = dg.n_noncompact;
@@ -669,9 +692,12 @@ int oracle_segments(int n_chan, int n_tranche, int n_bins, double dT, double t0,
   if (!grid_ok(n_chan, n_tranche, n_bins, dT) || !th8 || !zr || !zi || !nn) return ORC_ERR_ARG;
   if (n_seg < 1 || n_tranche % n_seg != 0) return ORC_ERR_NSEG;
   Grid g{n_chan, n_tranche, n_bins, dT, t0, 1.0 / dT, d_re, d_im, w, mask};
-  double ups;
-  statistic_one<double>(g, th8, pn_order, resp, fresnel_mode, n_seg, ups, nullptr, zr, zi, nn);
-  if (out_stat) *out_stat = ups;
+  long double th[NPAR];
+  for (int p = 0; p < NPAR; ++p) th[p] = th8[p];
+  long double ups;
+  statistic_one<long double>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, nullptr, zr, zi,
+                             nn);
+  if (out_stat) *out_stat = (double)ups;
   return ORC_OK;
 }
 
@@ -685,9 +711,10 @@ void oracle_tranche_ft(double amp, double phi, double fm, double fdot, double dT
                        int64_t nk, int fresnel_mode, double* re, double* im) {
   const double df = 1.0 / dT;
   for (int64_t i = 0; i < nk; ++i) {
-    const Cx<double> h = tranche_ft_bin<double>(amp, phi, fm, fdot, dT, (k0 + i) * df, fresnel_mode);
-    re[i] = h.re;
-    im[i] = h.im;
+    const Cx<long double> h = tranche_ft_bin<long double>(amp, phi, fm, fdot, dT,
+                                                          (long double)(k0 + i) * df, fresnel_mode);
+    re[i] = (double)h.re;
+    im[i] = (double)h.im;
   }
 }
 
@@ -706,17 +733,19 @@ void oracle_source(const double* th8, int pn_order, double* out5) {
 void oracle_track(const double* th8, int pn_order, int resp, const double* t, int64_t n,
                   double t_anchor, double* f, double* fdot, double* amp, double* dphi,
                   double* tprime, uint8_t* alive) {
-  const Source<double> s = make_source<double>(th8, pn_order);
+  long double th[NPAR];
+  for (int p = 0; p < NPAR; ++p) th[p] = th8[p];
+  const Source<long double> s = make_source<long double>(th, pn_order);
   for (int64_t i = 0; i < n; ++i) {
-    const TrackPoint<double> tp = track_point(s, resp, t[i], t_anchor);
-    double d0, d1, d2;
+    const TrackPoint<long double> tp = track_point(s, resp, t[i], t_anchor);
+    long double d0, d1, d2;
     doppler(s, t[i], resp, d0, d1, d2);
-    tprime[i] = t[i] + d0;
+    tprime[i] = (double)(t[i] + d0);
     alive[i] = tp.alive ? 1 : 0;
-    f[i] = tp.alive ? tp.f : 0.0;
-    fdot[i] = tp.alive ? tp.fdot : 0.0;
-    amp[i] = tp.alive ? tp.amp : 0.0;
-    dphi[i] = tp.alive ? tp.dphi : 0.0;
+    f[i] = tp.alive ? (double)tp.f : 0.0;
+    fdot[i] = tp.alive ? (double)tp.fdot : 0.0;
+    amp[i] = tp.alive ? (double)tp.amp : 0.0;
+    dphi[i] = tp.alive ? (double)tp.dphi : 0.0;
   }
 }
 
