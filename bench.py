@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the semi-coherent statistic Upsilon_{N_seg} (rho^2_sc) on one B300.
+
+Workload: two-year, two-channel (A/E) TF grid of 2048-sample tranches x 6144 tranches
+(dt = 5 s, 1024 complex bins per tranche), PSD modulated +-20 % with a 30-day period,
+3.5 h gaps every 14 days plus 20 Poisson gaps, 20 injections; a bank of 1e6
+non-spinning 1PN templates (M_c in [10, 60], eta in [0.1, 0.25], f_0 in [15, 30] mHz,
+isotropic sky, random psi, cos iota, phi_0), each evaluated at N_seg = 256, 64 and 16
+in one pass. All inputs are seeded synthetic data.
+
+One step = one eval_statistic call over the whole bank (set-up, length sort, the
+mixed-precision statistic kernel, output) with inputs resident in HBM; the L2 cache is
+flushed (a 256 MB write) between timed steps. The plain FP32 path (the paper's
+one-thread-per-template mapping) is timed on a subset of the same bank for the
+mixed-vs-plain ratio, and the FP64 CPU oracle on a bounded sample for the CPU
+baseline. `--impl reference` times the oracle itself as the reference arm.
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "templates/s of ρ²_sc (2-yr A+E TF grid), mixed vs plain form; % roofline"
+N_SEG = [256, 64, 16]
+NF = 21
+# algorithmic FP32 work per active (template, tranche), phase-cancelled form, 2 channels:
+# per bin and channel conj(u) W accumulate (8 flops) + w |W|^2 accumulate (2 flops);
+# per bin the kernel value (x1, x2, W re/im: 4 flops after the two reciprocals) and
+# |W|^2 (3 flops); per tranche the response (2 ch x 2 pol x 6 FMA = 48 flops), the
+# channel combination (24 flops) and the amplitude-phase factor (8 flops).
+FLOP_PER_BIN_CH = 10
+FLOP_PER_BIN = 7
+FLOP_PER_TRANCHE = 80
+SM_COUNT = 148
+FP32_LANES = 128
+SM_MAX_GHZ = 2.032
+PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0  # 76.96
+
+
+def flop_per_unit(n_chan):
+    return NF * (FLOP_PER_BIN_CH * n_chan + FLOP_PER_BIN) + FLOP_PER_TRANCHE
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-templates", type=int, default=1_000_000)
+    p.add_argument("--path", default="mixed", choices=["mixed", "plain", "fp64"])
+    p.add_argument("--pixel", default="f16", choices=["f16", "bf16", "f32"])
+    p.add_argument("--plain-templates", type=int, default=20_000)
+    p.add_argument("--cpu-sample", type=int, default=12)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample_rate(D, theta, n_seg, threads=0):
+    """templates/s of the FP64 CPU oracle (all N_seg levels) on the given templates."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for L in n_seg:
+        oracle.statistic(D.d, D.w, D.mask, theta, L, D.dT, pn_order=D.pn_order,
+                         response=D.response, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return theta.shape[1] / dt, dt
+
+
+def traffic_record():
+    """Per-launch DRAM bytes of the statistic kernel from a committed ncu summary, valid
+    only while the kernel source is unchanged."""
+    src = os.path.join(ROOT, "paper_2510_19047_b300", "csrc", "tfs_eval_mixed.cu")
+    path = os.path.join(ROOT, "profiles", "k_eval_mixed_dram.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if rec.get("source_sha1") != h:
+        return None
+    return rec
+
+
+def run_reference(args):
+    """The oracle as the reference arm (FP64 CPU, all host cores)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2510_19047_b300 import synth
+    import oracle
+    D = synth.cached(synth.two_year_two_channel)
+    theta = synth.two_year_bank(args.cpu_sample, seed=2002)
+    cores = oracle.max_threads()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample_rate(D, theta[:, :2], N_SEG)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = oracle_sample_rate(D, theta, N_SEG)
+        rates.append(r)
+        times.append(dt)
+    v = args.cpu_sample * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "templates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "AE-2yr-2048x6144, N_seg 256/64/16",
+                   "sample": f"{args.cpu_sample} templates of the 1e6 bank per step"},
+        "cpu_baseline": {"value": v, "unit": "templates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.cpu_sample} templates x 3 N_seg levels per step"},
+        "e2e": {"value": v, "unit": "templates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.binding import TFS
+
+    D = synth.cached(synth.two_year_two_channel)
+    n = args.n_templates
+    theta_np = synth.two_year_bank(n, seed=2002 + rank)  # weak scaling: own bank per rank
+    theta = torch.from_numpy(theta_np).cuda()
+    ctx = TFS(local, path=args.path, pixel=args.pixel, profile=1)
+    ctx.load_tf_data(D.d, D.dt, D.dT)
+    ctx.set_noise_weights(D.w, D.mask)
+    stat = torch.empty((len(N_SEG), n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    # one untimed call with diagnostics: active (template, tranche) units per launch
+    _, _, diag = ctx.eval_statistic(theta, N_SEG, diag=True)
+    units = int(diag[0].sum().item())
+    for _ in range(args.warmup):
+        ctx.eval_statistic(theta, N_SEG, out=stat)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, kern_ms, launches = [], [], 0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.eval_statistic(theta, N_SEG, out=stat)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(ctx.last_profile()["statistic"])
+        launches += ctx.last_launch_count()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world / (ms / 1000.0)
+
+    # roofline of the statistic kernel
+    kms = statistics.mean(kern_ms)
+    flops = units * flop_per_unit(D.n_chan)
+    achieved = flops / (kms / 1000.0) / 1e12
+    trec = traffic_record()
+    roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / PEAK_FP32_TFLOPS,
+            "traffic": (trec["dram_bytes_per_unit"] * units) if trec else None,
+            "kernel": "k_eval_mixed", "kernel_ms": kms, "units_per_launch": units,
+            "flop_per_unit": flop_per_unit(D.n_chan),
+            "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz"}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "templates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "AE-2yr-2048x6144 (12.58M samples/ch, 1e6 templates, "
+                               "N_seg 256/64/16 in one pass)",
+                   "n_templates_per_gpu": n, "n_seg": N_SEG, "path": args.path,
+                   "pixel": args.pixel, "phase": "double-float", "l2": "flushed between steps",
+                   "parallelism": f"templates sharded, {world} GPU(s)"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    if rank == 0 and not args.no_plain and args.path == "mixed":
+        ctx.set_options(path="plain", profile=1)
+        sub = theta[:, : args.plain_templates].contiguous()
+        ctx.eval_statistic(sub, N_SEG)
+        pms = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.eval_statistic(sub, N_SEG)
+            e1.record(stream)
+            e1.synchronize()
+            pms.append(e0.elapsed_time(e1))
+        pv = sub.shape[1] / (statistics.mean(pms) / 1000.0)
+        result["plain"] = {"value": pv, "unit": "templates/s", "n_templates": sub.shape[1],
+                           "ms_per_step": statistics.mean(pms), "dtype": "f32 pixels, f64 phase"}
+        result["mixed_vs_plain"] = value / world / pv
+        ctx.set_options(path=args.path, pixel=args.pixel, profile=1)
+
+    if rank == 0 and not args.no_e2e:
+        ctx.set_options(path=args.path, pixel=args.pixel, profile=0)
+        th_host = torch.from_numpy(theta_np).pin_memory()
+        out_host = torch.empty((len(N_SEG), n), dtype=torch.float64).pin_memory()
+        ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
+        ets = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
+            torch.cuda.synchronize()
+            ets.append(time.perf_counter() - t0)
+        result["e2e"] = {"value": n / statistics.mean(ets), "unit": "templates/s",
+                         "h2d_bytes_per_step": int(theta_np.nbytes),
+                         "d2h_bytes_per_step": int(len(N_SEG) * n * (8 + 4))}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        sample = theta_np[:, : args.cpu_sample].copy()
+        rate, dt = oracle_sample_rate(D, sample, N_SEG)
+        result["cpu_baseline"] = {"value": rate, "unit": "templates/s",
+                                  "cores": oracle.max_threads(), "kind": "oracle",
+                                  "sample": f"first {args.cpu_sample} templates of the bank, "
+                                            f"3 N_seg levels, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,632 @@
+// C ABI of libtfs (declared in include/tfs.h): the context, data loading, noise
+// weights, and dispatch of the evaluation paths. Host code only; the kernels live in
+// tfs_setup.cu, tfs_eval_ref.cu, tfs_eval_mixed.cu, tfs_sort.cu and tfs_grad.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tfs_internal.cuh"
+#include "tfs_kernels.cuh"
+#include "tfs_sort.cuh"
+
+using namespace tfs;
+
+namespace {
+
+constexpr int kMixedMaxFine = 1024;  // shared-memory segment slots per warp, mixed path
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tfs_ctx {
+  int device = 0;
+  int n_sm = 0;
+  tfs_options opt{};
+  std::string err;
+  int64_t alloc_bytes = 0;
+  int64_t launches = 0;
+  // data
+  bool has_data = false, has_weights = false;
+  GridDesc g{};
+  double dt = 0;
+  DevBuf d_re, d_im, w_in, mask, tabD, tabF;
+  // packed pixels
+  DevBuf u64, w64, u32, w32, Umix, Wmix;
+  int pitch = 0;
+  int pix_built = -1;
+  double su = 1.0, sw = 1.0;
+  // per-call scratch
+  DevBuf theta, tpl, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
+  // profiling
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double prof[4] = {0, 0, 0, 0};
+  bool prof_valid = false;
+  int mixed_warps = 0;
+};
+
+namespace {
+
+int fail(tfs_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TFS_ERR_OOM : TFS_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+void buf_free(tfs_ctx* c, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    c->alloc_bytes -= (int64_t)b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// Grow-only device buffer with the context's allocation cap.
+int buf_ensure(tfs_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.p && b.bytes >= bytes) return TFS_OK;
+  buf_free(c, b);
+  if (c->opt.max_device_bytes > 0 && c->alloc_bytes + (int64_t)bytes > c->opt.max_device_bytes)
+    return fail(c, TFS_ERR_OOM,
+                "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap of " +
+                    std::to_string(c->opt.max_device_bytes) + " bytes");
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(c, TFS_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  c->alloc_bytes += (int64_t)bytes;
+  return TFS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: the pointer itself if it is device memory, else a
+// copy into `tmp`.
+int device_view(tfs_ctx* c, const void* src, size_t bytes, DevBuf& tmp, cudaStream_t s,
+                const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return TFS_OK;
+  }
+  int r = buf_ensure(c, tmp, bytes);
+  if (r) return r;
+  CUDA_TRY(c, cudaMemcpyAsync(tmp.p, src, bytes, cudaMemcpyHostToDevice, s));
+  *out = tmp.p;
+  return TFS_OK;
+}
+
+int64_t lcm64(int64_t a, int64_t b) { return a / std::gcd(a, b) * b; }
+
+double pow2_scale(double maxval) {
+  // power of two that brings the largest value to ~2^14 (FP16 keeps 4x headroom)
+  if (!(maxval > 0.0) || !std::isfinite(maxval)) return 1.0;
+  return std::ldexp(1.0, 14 - (int)std::ceil(std::log2(maxval)));
+}
+
+int pack_mixed(tfs_ctx* c, cudaStream_t s) {
+  const int pix = c->opt.pixel;
+  const size_t ue = pix == TFS_PIX_F32 ? 16 : 8, we = pix == TFS_PIX_F32 ? 8 : 4;
+  const size_t npix = (size_t)c->g.n_bins * c->pitch;
+  int r = buf_ensure(c, c->Umix, npix * ue);
+  if (r) return r;
+  r = buf_ensure(c, c->Wmix, npix * we);
+  if (r) return r;
+  CUDA_TRY(c, launch_pack_mixed(pix, c->g, c->pitch, (const double*)c->d_re.p,
+                                (const double*)c->d_im.p, (const double*)c->w_in.p, c->su, c->sw,
+                                c->Umix.p, c->Wmix.p, c->n_sm, s));
+  c->launches++;
+  c->pix_built = pix;
+  return TFS_OK;
+}
+
+int make_levels(tfs_ctx* c, const int32_t* n_seg, int n_levels, Levels* lv) {
+  if (n_levels < 1 || n_levels > kMaxLevels)
+    return fail(c, TFS_ERR_ARG, "n_levels must be 1..4");
+  lv->n = n_levels;
+  int64_t anchor = 1, fine = 0;
+  for (int l = 0; l < kMaxLevels; ++l) lv->seg_len[l] = c->g.n_tranche;
+  for (int l = 0; l < n_levels; ++l) {
+    const int ns = n_seg[l];
+    if (ns < 1) return fail(c, TFS_ERR_ARG, "N_seg must be >= 1");
+    if (c->g.n_tranche % ns != 0)
+      return fail(c, TFS_ERR_NSEG,
+                  "N_t = " + std::to_string(c->g.n_tranche) + " is not divisible by N_seg = " +
+                      std::to_string(ns));
+    lv->seg_len[l] = c->g.n_tranche / ns;
+    anchor = lcm64(anchor, lv->seg_len[l]);
+    fine = std::gcd<int64_t>(fine, lv->seg_len[l]);
+  }
+  lv->anchor_len = (int)anchor;  // divides N_t since every segment length does
+  lv->fine_len = (int)fine;
+  lv->n_fine = c->g.n_tranche / (int)fine;
+  return TFS_OK;
+}
+
+void prof_record(tfs_ctx* c, int i, cudaStream_t s) {
+  if (c->opt.profile) cudaEventRecord(c->ev[i], s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tfs_version(void) { return 10000; }
+
+void tfs_default_options(tfs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->path = TFS_PATH_MIXED;
+  o->pixel = TFS_PIX_F16;
+  o->pn_order = 1;
+  o->response = 1;
+  o->checked = 0;
+  o->sort = 1;
+  o->warps_per_cta = 0;
+  o->use_graph = 0;
+  o->profile = 0;
+  o->max_device_bytes = 0;
+}
+
+static int check_options(tfs_ctx* c, const tfs_options* o) {
+  if (o->path < 0 || o->path > 2) return fail(c, TFS_ERR_ARG, "options.path must be 0, 1 or 2");
+  if (o->pixel < 0 || o->pixel > 2) return fail(c, TFS_ERR_ARG, "options.pixel must be 0, 1 or 2");
+  if (o->pn_order < 0 || o->pn_order > 1) return fail(c, TFS_ERR_ARG, "options.pn_order must be 0 or 1");
+  if (o->response < 0 || o->response > 1) return fail(c, TFS_ERR_ARG, "options.response must be 0 or 1");
+  if (o->warps_per_cta < 0 || o->warps_per_cta > 8 ||
+      (o->warps_per_cta && (o->warps_per_cta & (o->warps_per_cta - 1))))
+    return fail(c, TFS_ERR_ARG, "options.warps_per_cta must be 0 or a power of two <= 8");
+  if (o->max_device_bytes < 0) return fail(c, TFS_ERR_ARG, "options.max_device_bytes must be >= 0");
+  return TFS_OK;
+}
+
+int tfs_create(tfs_ctx** out, int device, const tfs_options* opt) {
+  if (!out) return TFS_ERR_ARG;
+  *out = nullptr;
+  tfs_ctx* c = new (std::nothrow) tfs_ctx();
+  if (!c) return TFS_ERR_OOM;
+  tfs_default_options(&c->opt);
+  if (opt) {
+    int r = check_options(c, opt);
+    if (r) {
+      delete c;
+      return r;
+    }
+    c->opt = *opt;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return TFS_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return TFS_ERR_CUDA;
+  }
+  c->device = device;
+  for (int i = 0; i < 5; ++i) cudaEventCreate(&c->ev[i]);
+  *out = c;
+  return TFS_OK;
+}
+
+int tfs_destroy(tfs_ctx* c) {
+  if (!c) return TFS_OK;
+  cudaSetDevice(c->device);
+  DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
+                   &c->w64, &c->u32, &c->w32, &c->Umix, &c->Wmix, &c->theta, &c->tpl,
+                   &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
+                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ};
+  for (DevBuf* b : all) buf_free(c, *b);
+  for (int i = 0; i < 5; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+  return TFS_OK;
+}
+
+int tfs_set_options(tfs_ctx* c, const tfs_options* o) {
+  if (!c || !o) return TFS_ERR_ARG;
+  int r = check_options(c, o);
+  if (r) return r;
+  c->opt = *o;
+  c->mixed_warps = 0;
+  return TFS_OK;
+}
+
+int tfs_get_options(const tfs_ctx* c, tfs_options* o) {
+  if (!c || !o) return TFS_ERR_ARG;
+  *o = c->opt;
+  return TFS_OK;
+}
+
+const char* tfs_last_error(const tfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t tfs_last_launch_count(const tfs_ctx* c) { return c ? c->launches : -1; }
+
+int tfs_last_profile(const tfs_ctx* c, double ms[4]) {
+  if (!c || !ms) return TFS_ERR_ARG;
+  if (!c->prof_valid) return TFS_ERR_STATE;
+  for (int i = 0; i < 4; ++i) ms[i] = c->prof[i];
+  return TFS_OK;
+}
+
+int tfs_load_tf_data(tfs_ctx* c, int n_chan, int n_tranche, int n_bins, double dt, double dT,
+                     double t0, const double* d_re, const double* d_im) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (n_chan < 1 || n_chan > 2) return fail(c, TFS_ERR_ARG, "n_chan must be 1 or 2");
+  if (n_tranche < 1) return fail(c, TFS_ERR_ARG, "n_tranche must be >= 1");
+  if (n_bins < 2 * kNFHalf + 2) return fail(c, TFS_ERR_ARG, "n_bins must be >= 22");
+  if (!(dT > 0.0) || !(dt > 0.0) || !std::isfinite(dT) || !std::isfinite(t0))
+    return fail(c, TFS_ERR_ARG, "dt and dT must be positive and finite");
+  if (dT / dt + 1e-9 < 2.0 * n_bins)
+    return fail(c, TFS_ERR_ARG, "n_bins exceeds dT / (2 dt) (bins above the Nyquist frequency)");
+  if (!d_re || !d_im) return fail(c, TFS_ERR_ARG, "d_re and d_im must not be null");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  c->has_data = c->has_weights = false;
+  c->g.n_chan = n_chan;
+  c->g.n_tranche = n_tranche;
+  c->g.n_bins = n_bins;
+  c->g.dT = dT;
+  c->g.df = 1.0 / dT;
+  c->g.t0 = t0;
+  c->dt = dt;
+  c->pitch = (n_tranche + 31) / 32 * 32;
+  const size_t n = (size_t)n_chan * n_tranche * n_bins;
+  int r;
+  if ((r = buf_ensure(c, c->d_re, n * 8)) || (r = buf_ensure(c, c->d_im, n * 8)) ||
+      (r = buf_ensure(c, c->tabD, (size_t)n_tranche * sizeof(TrancheD))) ||
+      (r = buf_ensure(c, c->tabF, (size_t)n_tranche * sizeof(TrancheF))))
+    return r;
+  const cudaMemcpyKind k1 = is_device_ptr(d_re) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind k2 = is_device_ptr(d_im) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUDA_TRY(c, cudaMemcpy(c->d_re.p, d_re, n * 8, k1));
+  CUDA_TRY(c, cudaMemcpy(c->d_im.p, d_im, n * 8, k2));
+  CUDA_TRY(c, launch_tranche_table(c->g, (TrancheD*)c->tabD.p, (TrancheF*)c->tabF.p, 0));
+  c->launches = 1;
+  CUDA_TRY(c, cudaDeviceSynchronize());
+  c->has_data = true;
+  return TFS_OK;
+}
+
+int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tranche_mask) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (!c->has_data) return fail(c, TFS_ERR_STATE, "load_tf_data must be called first");
+  if (!inv_psd) return fail(c, TFS_ERR_ARG, "inv_psd must not be null");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const size_t n = (size_t)c->g.n_chan * c->g.n_tranche * c->g.n_bins;
+  int r;
+  if ((r = buf_ensure(c, c->w_in, n * 8)) || (r = buf_ensure(c, c->mask, c->g.n_tranche)) ||
+      (r = buf_ensure(c, c->u64, n * 16)) || (r = buf_ensure(c, c->w64, n * 8)) ||
+      (r = buf_ensure(c, c->u32, n * 8)) || (r = buf_ensure(c, c->w32, n * 4)) ||
+      (r = buf_ensure(c, c->counter, 64)))
+    return r;
+  CUDA_TRY(c, cudaMemcpy(c->w_in.p, inv_psd, n * 8,
+                         is_device_ptr(inv_psd) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  if (tranche_mask) {
+    CUDA_TRY(c, cudaMemcpy(c->mask.p, tranche_mask, c->g.n_tranche,
+                           is_device_ptr(tranche_mask) ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice));
+  } else {
+    CUDA_TRY(c, cudaMemset(c->mask.p, 1, c->g.n_tranche));
+  }
+  // validate and find the ranges of u = d w and w
+  unsigned long long* mx = (unsigned long long*)c->counter.p;
+  int* bad = (int*)((char*)c->counter.p + 16);
+  CUDA_TRY(c, cudaMemset(c->counter.p, 0, 64));
+  CUDA_TRY(c, launch_absmax((int64_t)n, (const double*)c->d_re.p, (const double*)c->d_im.p,
+                            (const double*)c->w_in.p, mx, mx + 1, bad, c->n_sm, 0));
+  unsigned long long hm[2];
+  int hbad = 0;
+  CUDA_TRY(c, cudaMemcpy(hm, mx, 16, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(&hbad, bad, 4, cudaMemcpyDeviceToHost));
+  c->launches = 1;
+  if (hbad)
+    return fail(c, TFS_ERR_ARG,
+                std::to_string(hbad) +
+                    " pixels have a negative or non-finite weight, or non-finite data under a "
+                    "positive weight");
+  double umax, wmax;
+  std::memcpy(&umax, &hm[0], 8);
+  std::memcpy(&wmax, &hm[1], 8);
+  c->su = pow2_scale(umax);
+  c->sw = pow2_scale(wmax);
+  CUDA_TRY(c, launch_pack_ref((int64_t)n, (const double*)c->d_re.p, (const double*)c->d_im.p,
+                              (const double*)c->w_in.p, c->su, c->sw, (double2*)c->u64.p,
+                              (double*)c->w64.p, (float2*)c->u32.p, (float*)c->w32.p, c->n_sm, 0));
+  r = pack_mixed(c, 0);
+  if (r) return r;
+  CUDA_TRY(c, cudaDeviceSynchronize());
+  c->has_weights = true;
+  return TFS_OK;
+}
+
+static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32_t* n_seg,
+                     int n_levels, int per_template, double* out_stat, int32_t* out_neff,
+                     int32_t* out_diag, cudaStream_t s) {
+  const GridDesc& g = c->g;
+  Levels lv{};
+  int r;
+  int fine_cap = 0;
+  const int32_t* nseg_dev = nullptr;
+  if (!per_template) {
+    if (!n_seg) return fail(c, TFS_ERR_ARG, "n_seg must not be null");
+    int32_t hs[kMaxLevels] = {0, 0, 0, 0};
+    if (n_levels < 1 || n_levels > kMaxLevels) return fail(c, TFS_ERR_ARG, "n_levels must be 1..4");
+    if (is_device_ptr(n_seg)) {
+      CUDA_TRY(c, cudaMemcpy(hs, n_seg, n_levels * 4, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(hs, n_seg, n_levels * 4);
+    }
+    if ((r = make_levels(c, hs, n_levels, &lv))) return r;
+    fine_cap = lv.n_fine;
+  } else {
+    n_levels = 1;
+    std::vector<int32_t> hs(n_tpl > 0 ? n_tpl : 1);
+    if (n_tpl > 0) {
+      if (!n_seg) return fail(c, TFS_ERR_ARG, "n_seg must not be null");
+      CUDA_TRY(c, cudaMemcpy(hs.data(), n_seg, n_tpl * 4,
+                             is_device_ptr(n_seg) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    }
+    int mx = 1;
+    for (int64_t i = 0; i < n_tpl; ++i) {
+      if (hs[i] < 1) return fail(c, TFS_ERR_ARG, "N_seg must be >= 1");
+      if (g.n_tranche % hs[i] != 0)
+        return fail(c, TFS_ERR_NSEG, "N_t = " + std::to_string(g.n_tranche) +
+                                         " is not divisible by N_seg = " + std::to_string(hs[i]));
+      mx = std::max(mx, (int)hs[i]);
+    }
+    lv.n = 0;
+    fine_cap = mx;
+    if ((r = buf_ensure(c, c->nseg, (size_t)std::max<int64_t>(n_tpl, 1) * 4))) return r;
+    if (n_tpl > 0)
+      CUDA_TRY(c, cudaMemcpyAsync(c->nseg.p, hs.data(), n_tpl * 4, cudaMemcpyHostToDevice, s));
+    nseg_dev = (const int32_t*)c->nseg.p;
+  }
+  const int path = c->opt.path;
+  if (path == TFS_PATH_MIXED && fine_cap > kMixedMaxFine)
+    return fail(c, TFS_ERR_ARG,
+                "the mixed path folds at most 1024 finest segments per template (N_t / gcd of "
+                "segment lengths); use the plain or FP64 path for finer segmentations");
+  c->launches = 0;
+  c->prof_valid = false;
+  if (n_tpl == 0) return TFS_OK;
+  // inputs
+  const void* th = nullptr;
+  if ((r = device_view(c, theta, (size_t)n_tpl * 8 * 8, c->theta, s, &th))) return r;
+  if ((r = buf_ensure(c, c->tpl, (size_t)n_tpl * sizeof(TplConst)))) return r;
+  // outputs: device pointers are written directly, host ones through scratch
+  const bool dev_stat = is_device_ptr(out_stat);
+  const bool dev_neff = !out_neff || is_device_ptr(out_neff);
+  const bool dev_diag = !out_diag || is_device_ptr(out_diag);
+  double* o_stat = out_stat;
+  int32_t* o_neff = out_neff;
+  int32_t* o_diag = out_diag;
+  if (!dev_stat) {
+    if ((r = buf_ensure(c, c->stat, (size_t)n_levels * n_tpl * 8))) return r;
+    o_stat = (double*)c->stat.p;
+  }
+  if (!dev_neff) {
+    if ((r = buf_ensure(c, c->neff, (size_t)n_levels * n_tpl * 4))) return r;
+    o_neff = (int32_t*)c->neff.p;
+  }
+  if (!dev_diag) {
+    if ((r = buf_ensure(c, c->diag, (size_t)2 * n_tpl * 4))) return r;
+    o_diag = (int32_t*)c->diag.p;
+  }
+  if ((r = buf_ensure(c, c->counter, 64))) return r;
+
+  prof_record(c, 0, s);
+  CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, g, (TplConst*)c->tpl.p, s));
+  c->launches++;
+  prof_record(c, 1, s);
+
+  EvalArgs a{};
+  a.g = g;
+  a.response = c->opt.response;
+  a.pitch = c->pitch;
+  a.tabD = (const TrancheD*)c->tabD.p;
+  a.tabF = (const TrancheF*)c->tabF.p;
+  a.u64 = (const double2*)c->u64.p;
+  a.w64 = (const double*)c->w64.p;
+  a.u32 = (const float2*)c->u32.p;
+  a.w32 = (const float*)c->w32.p;
+  a.Umix = c->Umix.p;
+  a.Wmix = c->Wmix.p;
+  a.mask = (const uint8_t*)c->mask.p;
+  a.tpl = (const TplConst*)c->tpl.p;
+  a.perm = nullptr;
+  a.n_tpl = n_tpl;
+  a.lv = lv;
+  a.nseg_pt = nseg_dev;
+  a.fine_cap = fine_cap;
+  a.out_stat = o_stat;
+  a.out_neff = o_neff;
+  a.out_diag = o_diag;
+  a.counter = (int*)c->counter.p;
+  a.dev_err = (int*)c->counter.p + 8;
+  a.checked = c->opt.checked;
+  const double scale32 = 4.0 * g.df * c->sw / (c->su * c->su);
+
+  if (path == TFS_PATH_MIXED) {
+    if (c->pix_built != c->opt.pixel && (r = pack_mixed(c, s))) return r;
+    if (c->opt.sort) {
+      if ((r = buf_ensure(c, c->perm, (size_t)n_tpl * 4)) ||
+          (r = buf_ensure(c, c->sortbuf, sort_scratch_bytes(n_tpl))))
+        return r;
+      int nl = 0;
+      CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p,
+                                 c->sortbuf.p, c->n_sm, s, &nl));
+      c->launches += nl;
+      a.perm = (const int32_t*)c->perm.p;
+    }
+    prof_record(c, 2, s);
+    const int warps = c->opt.warps_per_cta ? c->opt.warps_per_cta : 8;
+    int per_sm = 0;
+    CUDA_TRY(c, mixed_occupancy(g.n_chan, c->opt.pixel, warps, fine_cap, &per_sm));
+    if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
+    const int64_t need_ctas = (n_tpl + warps - 1) / warps;
+    const int ctas = (int)std::min<int64_t>((int64_t)c->n_sm * per_sm, need_ctas);
+    CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
+    a.out_scale = scale32;
+    CUDA_TRY(c, launch_eval_mixed(a, g.n_chan, c->opt.pixel, warps, ctas, s));
+    c->launches += 1;
+  } else if (path == TFS_PATH_PLAIN) {
+    prof_record(c, 2, s);
+    a.out_scale = scale32;
+    CUDA_TRY(c, launch_eval_plain(a, s));
+    c->launches += 1;
+  } else {
+    prof_record(c, 2, s);
+    a.out_scale = 4.0 * g.df;
+    CUDA_TRY(c, launch_eval_fp64(a, s));
+    c->launches += 1;
+  }
+  prof_record(c, 3, s);
+  if (!dev_stat)
+    CUDA_TRY(c, cudaMemcpyAsync(out_stat, o_stat, (size_t)n_levels * n_tpl * 8,
+                                cudaMemcpyDeviceToHost, s));
+  if (!dev_neff)
+    CUDA_TRY(c, cudaMemcpyAsync(out_neff, o_neff, (size_t)n_levels * n_tpl * 4,
+                                cudaMemcpyDeviceToHost, s));
+  if (!dev_diag)
+    CUDA_TRY(c, cudaMemcpyAsync(out_diag, o_diag, (size_t)2 * n_tpl * 4, cudaMemcpyDeviceToHost, s));
+  prof_record(c, 4, s);
+  if (!dev_stat || !dev_neff || !dev_diag || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (c->opt.profile) {
+    float ms;
+    for (int i = 0; i < 4; ++i) {
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      c->prof[i] = ms;
+    }
+    c->prof_valid = true;
+  }
+  return TFS_OK;
+}
+
+int tfs_eval_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32_t* n_seg,
+                       int n_levels, int per_template, double* out_stat, int32_t* out_neff,
+                       int32_t* out_diag, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (!c->has_data || !c->has_weights)
+    return fail(c, TFS_ERR_STATE, "load_tf_data and set_noise_weights must be called first");
+  if (n_tpl < 0 || n_tpl > INT32_MAX) return fail(c, TFS_ERR_ARG, "n_tpl must be in [0, 2^31)");
+  if (n_tpl > 0 && (!theta || !out_stat))
+    return fail(c, TFS_ERR_ARG, "theta and out_stat must not be null");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  return eval_impl(c, theta, n_tpl, n_seg, n_levels, per_template, out_stat, out_neff, out_diag,
+                   (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Ladder selection and gradient-ascent step
+// ---------------------------------------------------------------------------------
+extern "C" {
+
+int tfs_select_top(tfs_ctx* c, const double* stat, int64_t n, int64_t k, int64_t* out_index,
+                   void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (n < 0 || n > INT32_MAX || k < 0 || k > n) return fail(c, TFS_ERR_ARG, "need 0 <= k <= n < 2^31");
+  if (k == 0) return TFS_OK;
+  if (!stat || !out_index) return fail(c, TFS_ERR_ARG, "stat and out_index must not be null");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->launches = 0;
+  int r;
+  const void* sv = nullptr;
+  if ((r = device_view(c, stat, (size_t)n * 8, c->stat, s, &sv))) return r;
+  if ((r = buf_ensure(c, c->sortbuf, topk_scratch_bytes(n)))) return r;
+  const bool dev_out = is_device_ptr(out_index);
+  int64_t* o = out_index;
+  if (!dev_out) {
+    if ((r = buf_ensure(c, c->idx64, (size_t)k * 8))) return r;
+    o = (int64_t*)c->idx64.p;
+  }
+  int nl = 0;
+  CUDA_TRY(c, select_top((const double*)sv, n, k, o, c->sortbuf.p, s, &nl));
+  c->launches += nl;
+  if (!dev_out) {
+    CUDA_TRY(c, cudaMemcpyAsync(out_index, o, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+  }
+  return TFS_OK;
+}
+
+int tfs_ascent_step(tfs_ctx* c, double* theta, const double* grad, int64_t n, const double* step,
+                    const double* lo, const double* hi, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (n < 0) return fail(c, TFS_ERR_ARG, "n must be >= 0");
+  if (n == 0) return TFS_OK;
+  if (!theta || !grad || !step || !lo || !hi) return fail(c, TFS_ERR_ARG, "null argument");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  AscentParams p;
+  for (int i = 0; i < 8; ++i) {
+    p.step[i] = step[i];
+    p.lo[i] = lo[i];
+    p.hi[i] = hi[i];
+  }
+  int r;
+  const bool dev_theta = is_device_ptr(theta);
+  double* th = theta;
+  if (!dev_theta) {
+    if ((r = buf_ensure(c, c->theta, (size_t)n * 64))) return r;
+    th = (double*)c->theta.p;
+    CUDA_TRY(c, cudaMemcpyAsync(th, theta, (size_t)n * 64, cudaMemcpyHostToDevice, s));
+  }
+  const void* gv = nullptr;
+  if ((r = device_view(c, grad, (size_t)n * 64, c->grad, s, &gv))) return r;
+  c->launches = 0;
+  CUDA_TRY(c, launch_ascent(th, (const double*)gv, n, p, s));
+  c->launches = 1;
+  if (!dev_theta) {
+    CUDA_TRY(c, cudaMemcpyAsync(theta, th, (size_t)n * 64, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+  }
+  return TFS_OK;
+}
+
+int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n_seg,
+                       double* out_stat, double* out_grad, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  (void)theta; (void)n_tpl; (void)n_seg; (void)out_stat; (void)out_grad; (void)stream;
+  return fail(c, TFS_ERR_STATE, "gradient kernel not built in this library version");
+}
+
+}  // extern "C"

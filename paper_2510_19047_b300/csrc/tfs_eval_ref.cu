@@ -1,0 +1,390 @@
+// One-thread-per-template evaluation kernels (the paper's GPU mapping: "devoting one
+// GPU thread to each set of source parameters", Sec. "Hardware acceleration and
+// computational cost"), each updating Upsilon tranche by tranche without storing
+// the waveform:
+//
+//   k_eval_fp64  - FP64 throughout, the Fresnel-kernel transform in the
+//                  phase-cancelled form (see below), phase accumulated per tranche
+//                  with compensated summation. The parity path.
+//   k_eval_plain - the printed Eq. fresnel-ft evaluated bin by bin: Fresnel C, S of
+//                  v_1, v_2 and the factor exp(i(phi - pi fdot zeta^2)), with FP32
+//                  pixels and FP32 Fresnel/trig; the large trig arguments are reduced
+//                  in FP64 first, the phase track is FP64.
+//
+// Phase-cancelled form. With C + iS = sgn(v) [(1+i)/2 - G(|v|) e^{i pi v^2/2}],
+// G = g + i f (the paper's auxiliary functions), v_1 = sqrt(2 fdot) zeta and
+// pi v_1^2/2 = pi fdot zeta^2, Eq. fresnel-ft becomes
+//   h~_k = A/sqrt(2 fdot) e^{i phi} W_k,
+//   W_k  = s_1 G(|v_1|) - s_2 G(|v_2|) e^{i Psi} + [s_1 != s_2] (1+i) e^{-i pi v_1^2/2},
+//   Psi  = pi (v_2^2 - v_1^2)/2 = 2 pi (f_nm - f_k) dT + pi fdot dT^2,
+// and e^{i Psi} = e^{i(2 pi a + pi fdot dT^2)} (a = f_nm/df - k_c) is the same for all
+// bins of a tranche: the two ~1e5-rad arguments cancel exactly instead of numerically.
+#include <math.h>
+
+#include "tfs_internal.cuh"
+#include "tfs_kernels.cuh"
+
+namespace tfs {
+
+namespace {
+
+struct TrackD {
+  double tp, d0, f, fdot, fsrc;
+};
+
+// Retarded time, frequency and its derivative at the start of tranche m (FP64).
+__device__ __forceinline__ TrackD track_fp64(const TplConst& c, const TrancheD& tr, int resp) {
+  TrackD r;
+  double d1 = 0.0, d2 = 0.0;
+  r.d0 = 0.0;
+  if (resp) {
+    r.d0 = c.dop_c * tr.ca + c.dop_s * tr.sa;
+    d1 = kOmega * (c.dop_s * tr.ca - c.dop_c * tr.sa);
+    d2 = -kOmega * kOmega * r.d0;
+  }
+  r.tp = tr.t + r.d0;
+  const double u = 1.0 - r.tp / c.tc;
+  const double y = pow(u, -0.125), y2 = y * y, y3 = y2 * y;
+  r.fsrc = c.F0 * y3 * (1.0 + c.C2 * y2);
+  const double fdsrc = c.F0 * y3 * y3 * y3 * y2 * (3.0 + 5.0 * c.C2 * y2) / (8.0 * c.tc);
+  r.f = r.fsrc * (1.0 + d1);
+  r.fdot = fdsrc * (1.0 + d1) * (1.0 + d1) + r.fsrc * d2;
+  return r;
+}
+
+// Phase advanced, in cycles, from barycentre time ta to ta + dt (both before t_c):
+// [P5 (ua^(5/8) - ub^(5/8)) + P3 (ua^(3/8) - ub^(3/8))] / 2 pi with ub = ua (1 + rho),
+// rho = -dt / (t_c - ta), written with log1p/expm1 so that it keeps full relative
+// precision for small steps.
+__device__ __forceinline__ double phase_step_cycles(const TplConst& c, double ta, double dt) {
+  const double ua = 1.0 - ta / c.tc;
+  const double rho = -dt / (c.tc - ta);
+  const double l = log1p(rho);
+  const double q = pow(ua, 0.125), q2 = q * q, q3 = q2 * q, q5 = q3 * q2;
+  const double s = c.P5 * q5 * (-expm1(0.625 * l)) + c.P3 * q3 * (-expm1(0.375 * l));
+  return s * (0.5 / kPi);
+}
+
+__device__ __forceinline__ void kahan_add(double& acc, double& comp, double x) {
+  const double y = x - comp;
+  const double t = acc + y;
+  comp = (t - acc) - y;
+  acc = t;
+}
+
+// Segment levels of one template.
+struct LevelState {
+  int n;
+  int seg_len[kMaxLevels];
+  int anchor;
+};
+
+__device__ __forceinline__ LevelState levels_of(const EvalArgs& a, int64_t i) {
+  LevelState L;
+  if (a.nseg_pt) {
+    L.n = 1;
+    L.seg_len[0] = a.g.n_tranche / a.nseg_pt[i];
+    L.anchor = L.seg_len[0];
+  } else {
+    L.n = a.lv.n;
+    for (int l = 0; l < kMaxLevels; ++l) L.seg_len[l] = a.lv.seg_len[l];
+    L.anchor = a.lv.anchor_len;
+  }
+  return L;
+}
+
+// Response factors T_alpha = F+ A+ - i Fx Ax (Eq. tdi2, long-wavelength limit).
+template <class T>
+__device__ __forceinline__ void response_factors(const TplConst& c, const double* DA,
+                                                 const double* DE, int resp, T Tr[2], T Ti[2]) {
+  if (!resp) {
+    Tr[0] = Tr[1] = T(1);
+    Ti[0] = Ti[1] = T(0);
+    return;
+  }
+  double fpA = 0, fxA = 0, fpE = 0, fxE = 0;
+  for (int p = 0; p < 6; ++p) {
+    fpA += DA[p] * c.pp[p];
+    fxA += DA[p] * c.px[p];
+    fpE += DE[p] * c.pp[p];
+    fxE += DE[p] * c.px[p];
+  }
+  Tr[0] = T(fpA);
+  Ti[0] = T(-fxA);
+  Tr[1] = T(fpE);
+  Ti[1] = T(-fxE);
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------------------------
+// FP64 parity kernel
+// -------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n_tpl) return;
+  const TplConst c = a.tpl[i];
+  const LevelState L = levels_of(a, i);
+  const GridDesc g = a.g;
+  const int nch = g.n_chan;
+  double zr[kMaxLevels], zi[kMaxLevels], nn[kMaxLevels], ups[kMaxLevels];
+  int neff[kMaxLevels], cur[kMaxLevels];
+  for (int l = 0; l < kMaxLevels; ++l) {
+    zr[l] = zi[l] = nn[l] = ups[l] = 0.0;
+    neff[l] = 0;
+    cur[l] = -1;
+  }
+  int nact = 0, nnc = 0;
+  int blk = -1, m_prev = 0;
+  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0;
+  for (int m = c.m_lo; m < c.m_hi; ++m) {
+    for (int l = 0; l < L.n; ++l) {
+      const int s = m / L.seg_len[l];
+      if (s != cur[l]) {
+        if (nn[l] > 0.0) {
+          ups[l] += (zr[l] * zr[l] + zi[l] * zi[l]) / nn[l];
+          ++neff[l];
+        }
+        zr[l] = zi[l] = nn[l] = 0.0;
+        cur[l] = s;
+      }
+    }
+    if (!a.mask[m]) continue;
+    const TrancheD tr = a.tabD[m];
+    const TrackD tk = track_fp64(c, tr, a.response);
+    if (!(tk.tp < c.tc)) break;  // t' grows with t: every later tranche is past t_c
+    if (!(tk.fdot > 0.0)) continue;
+    const double x = tk.f * g.dT;  // f / df
+    const double kcd = ceil(x);
+    const int kc = (int)kcd;
+    if (kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) continue;
+    // phase in cycles since the start of this anchor block (a block holds whole
+    // segments of every level, so a constant offset per block is maximised away)
+    const int b = m / L.anchor;
+    if (b != blk) {
+      blk = b;
+      m_prev = b * L.anchor;
+      const TrancheD ta = a.tabD[m_prev];
+      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
+      tp_prev = ta.t + d0_prev;
+      acc = comp = 0.0;
+    }
+    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
+    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
+    tp_prev = tk.tp;
+    d0_prev = tk.d0;
+    m_prev = m;
+    const double cyc = (acc - floor(acc)) - comp;
+    ++nact;
+    if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
+
+    double Tr[2], Ti[2];
+    response_factors<double>(c, tr.DA, tr.DE, a.response, Tr, Ti);
+    const double aa = x - kcd;                    // in (-1, 0]
+    const double sig = g.df * sqrt(2.0 / tk.fdot);  // v = sig * (f_nm - f_k)/df
+    const double e2 = sqrt(2.0 * tk.fdot) * g.dT;   // v_2 - v_1
+    double spsi, cpsi;
+    sincospi(2.0 * aa + tk.fdot * g.dT * g.dT, &spsi, &cpsi);
+    double zcr[2] = {0, 0}, zci[2] = {0, 0}, ncc[2] = {0, 0};
+    for (int j = 0; j < kNF; ++j) {
+      const int k = kc - kNFHalf + j;
+      const double v1 = (aa - (double)(j - kNFHalf)) * sig;
+      const double v2 = v1 + e2;
+      double f1, g1, f2, g2;
+      fresnel_fg<double>(fabs(v1), f1, g1);
+      fresnel_fg<double>(fabs(v2), f2, g2);
+      const double s1 = v1 < 0.0 ? -1.0 : 1.0, s2 = v2 < 0.0 ? -1.0 : 1.0;
+      double wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
+      double wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
+      if (s1 != s2) {
+        double sp, cp;
+        sincospi(0.5 * v1 * v1, &sp, &cp);
+        wr += cp + sp;  // (1+i) e^{-i pi v1^2/2}
+        wi += cp - sp;
+      }
+      const double ww = wr * wr + wi * wi;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
+        const double2 u = a.u64[px];
+        zcr[ch] += u.x * wr + u.y * wi;  // conj(u) W
+        zci[ch] += u.x * wi - u.y * wr;
+        ncc[ch] += a.w64[px] * ww;
+      }
+    }
+    const double amp = pow(tk.fsrc / c.F0, 2.0 / 3.0);
+    const double P = amp / sqrt(2.0 * tk.fdot);
+    double sph, cph;
+    sincospi(2.0 * cyc, &sph, &cph);
+    double Zr = 0.0, Zi = 0.0, N = 0.0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const double ar = Tr[ch] * zcr[ch] - Ti[ch] * zci[ch];
+      const double ai = Tr[ch] * zci[ch] + Ti[ch] * zcr[ch];
+      Zr += ar * cph - ai * sph;
+      Zi += ar * sph + ai * cph;
+      N += (Tr[ch] * Tr[ch] + Ti[ch] * Ti[ch]) * ncc[ch];
+    }
+    for (int l = 0; l < L.n; ++l) {
+      zr[l] += P * Zr;
+      zi[l] += P * Zi;
+      nn[l] += P * P * N;
+    }
+  }
+  for (int l = 0; l < L.n; ++l) {
+    if (nn[l] > 0.0) {
+      ups[l] += (zr[l] * zr[l] + zi[l] * zi[l]) / nn[l];
+      ++neff[l];
+    }
+    a.out_stat[(int64_t)l * a.n_tpl + i] = ups[l] * a.out_scale;
+    if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + i] = neff[l];
+  }
+  if (a.out_diag) {
+    a.out_diag[i] = nact;
+    a.out_diag[a.n_tpl + i] = nnc;
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// Plain FP32 kernel: Eq. fresnel-ft as printed, bin by bin.
+// -------------------------------------------------------------------------------------
+
+// x - 2 round(x/2) in FP64, returned as FP32 in [-1, 1]: sin(pi x), cos(pi x) of the
+// result equal those of x.
+__device__ __forceinline__ float reduce_mod2(double x) { return (float)(x - 2.0 * rint(0.5 * x)); }
+
+// Paper's Fresnel C(v), S(v) with the trig argument pi v^2/2 reduced in FP64.
+__device__ __forceinline__ void fresnel_cs_plain(double v, float& C, float& S) {
+  const float a = fabsf((float)v);
+  float f, gg;
+  fresnel_fg<float>(a, f, gg);
+  float sn, cs;
+  sincospif(reduce_mod2(0.5 * v * v), &sn, &cs);
+  C = 0.5f + f * sn - gg * cs;
+  S = 0.5f - f * cs - gg * sn;
+  if (v < 0.0) {
+    C = -C;
+    S = -S;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n_tpl) return;
+  const TplConst c = a.tpl[i];
+  const LevelState L = levels_of(a, i);
+  const GridDesc g = a.g;
+  const int nch = g.n_chan;
+  float zr[kMaxLevels], zi[kMaxLevels], nn[kMaxLevels];
+  double ups[kMaxLevels];
+  int neff[kMaxLevels], cur[kMaxLevels];
+  for (int l = 0; l < kMaxLevels; ++l) {
+    zr[l] = zi[l] = nn[l] = 0.0f;
+    ups[l] = 0.0;
+    neff[l] = 0;
+    cur[l] = -1;
+  }
+  int nact = 0, nnc = 0;
+  int blk = -1, m_prev = 0;
+  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0;
+  for (int m = c.m_lo; m < c.m_hi; ++m) {
+    for (int l = 0; l < L.n; ++l) {
+      const int s = m / L.seg_len[l];
+      if (s != cur[l]) {
+        if (nn[l] > 0.0f) {
+          ups[l] += ((double)zr[l] * zr[l] + (double)zi[l] * zi[l]) / (double)nn[l];
+          ++neff[l];
+        }
+        zr[l] = zi[l] = nn[l] = 0.0f;
+        cur[l] = s;
+      }
+    }
+    if (!a.mask[m]) continue;
+    const TrancheD tr = a.tabD[m];
+    const TrackD tk = track_fp64(c, tr, a.response);
+    if (!(tk.tp < c.tc)) break;
+    if (!(tk.fdot > 0.0)) continue;
+    const int kc = (int)ceil(tk.f * g.dT);
+    if (kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) continue;
+    const int b = m / L.anchor;
+    if (b != blk) {
+      blk = b;
+      m_prev = b * L.anchor;
+      const TrancheD ta = a.tabD[m_prev];
+      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
+      tp_prev = ta.t + d0_prev;
+      acc = comp = 0.0;
+    }
+    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
+    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
+    tp_prev = tk.tp;
+    d0_prev = tk.d0;
+    m_prev = m;
+    const double cyc = (acc - floor(acc)) - comp;
+    ++nact;
+    if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
+
+    float Tr[2], Ti[2];
+    response_factors<float>(c, tr.DA, tr.DE, a.response, Tr, Ti);
+    const double s2d = sqrt(2.0 * tk.fdot);
+    const double inv_fdot = 1.0 / tk.fdot;
+    const float P = (float)(pow(tk.fsrc / c.F0, 2.0 / 3.0) / s2d);
+    float zcr[2] = {0, 0}, zci[2] = {0, 0}, ncc[2] = {0, 0};
+    for (int j = 0; j < kNF; ++j) {
+      const int k = kc - kNFHalf + j;
+      const double zeta = (tk.f - (double)k * g.df) * inv_fdot;
+      const double v1 = s2d * zeta, v2 = s2d * (g.dT + zeta);
+      float C1, S1, C2, S2;
+      fresnel_cs_plain(v1, C1, S1);
+      fresnel_cs_plain(v2, C2, S2);
+      // exp(i (phi - pi fdot zeta^2)), argument in cycles reduced in FP64
+      float sn, cs;
+      sincospif(reduce_mod2(2.0 * cyc - tk.fdot * zeta * zeta), &sn, &cs);
+      const float Fr = C2 - C1, Fi = S2 - S1;
+      const float hr = P * (cs * Fr - sn * Fi);
+      const float hi = P * (cs * Fi + sn * Fr);
+      const float hh = hr * hr + hi * hi;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
+        const float2 u = a.u32[px];
+        zcr[ch] += u.x * hr + u.y * hi;
+        zci[ch] += u.x * hi - u.y * hr;
+        ncc[ch] += a.w32[px] * hh;
+      }
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+      const float ar = Tr[ch] * zcr[ch] - Ti[ch] * zci[ch];
+      const float ai = Tr[ch] * zci[ch] + Ti[ch] * zcr[ch];
+      const float n = (Tr[ch] * Tr[ch] + Ti[ch] * Ti[ch]) * ncc[ch];
+      for (int l = 0; l < L.n; ++l) {
+        zr[l] += ar;
+        zi[l] += ai;
+        nn[l] += n;
+      }
+    }
+  }
+  for (int l = 0; l < L.n; ++l) {
+    if (nn[l] > 0.0f) {
+      ups[l] += ((double)zr[l] * zr[l] + (double)zi[l] * zi[l]) / (double)nn[l];
+      ++neff[l];
+    }
+    a.out_stat[(int64_t)l * a.n_tpl + i] = ups[l] * a.out_scale;
+    if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + i] = neff[l];
+  }
+  if (a.out_diag) {
+    a.out_diag[i] = nact;
+    a.out_diag[a.n_tpl + i] = nnc;
+  }
+}
+
+cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s) {
+  if (a.n_tpl <= 0) return cudaSuccess;
+  k_eval_fp64<<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s) {
+  if (a.n_tpl <= 0) return cudaSuccess;
+  k_eval_plain<<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tfs

@@ -1,0 +1,146 @@
+// Internal declarations of libtfs: data layouts, per-template constants, double-float
+// arithmetic and the Fresnel auxiliary functions shared by the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tfs.h"
+
+namespace tfs {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double kGMsunS = 4.925490947e-6;  // G M_sun / c^3 [s]
+constexpr double kAuS = 499.004784;         // 1 AU / c [s]
+constexpr double kYearS = 31557600.0;       // Julian year [s]
+constexpr double kOmega = 2.0 * kPi / kYearS;
+constexpr int kNF = 21;      // N_F bins per tranche
+constexpr int kNFHalf = 10;  // window k_c - 10 .. k_c + 10
+constexpr int kMaxLevels = 4;
+
+// Grid geometry.
+struct GridDesc {
+  int n_chan, n_tranche, n_bins;
+  double dT, df, t0;
+};
+
+// Segment levels of one call. seg_len[l] = N_t / N_seg[l]; anchor = lcm of the
+// segment lengths (every segment of every level lies inside one anchor block);
+// fine = gcd of the segment lengths (every segment is a union of fine segments).
+struct Levels {
+  int n;
+  int seg_len[kMaxLevels];
+  int anchor_len;
+  int fine_len;
+  int n_fine;
+};
+
+// Per-tranche geometry (FP64): start time, orbital phase and the long-wavelength
+// detector tensors of A and E in packed form (xx, yy, zz, 2xy, 2xz, 2yz).
+struct TrancheD {
+  double t, ca, sa;
+  double DA[6], DE[6];
+  double pad;
+};
+// Same for the mixed path: double-float time and orbital cos/sin, FP32 tensors.
+struct __align__(16) TrancheF {
+  float t_hi, t_lo, ca_hi, ca_lo;
+  float sa_hi, sa_lo, pad0, pad1;
+  float DA[6], DE[6];
+};
+
+// Per-template constants, computed once in FP64 by the set-up kernel.
+struct __align__(16) TplConst {
+  double tc;          // coalescence time at the barycentre [s]
+  double F0, C2;      // f(t') = F0 y^3 (1 + C2 y^2), y = (1 - t'/t_c)^(-1/8)
+  double P5, P3;      // Phi(t') = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u = 1 - t'/t_c
+  double phi0;
+  double dop_c, dop_s;  // (R/c) cos(beta) cos(lambda), (R/c) cos(beta) sin(lambda)
+  double pp[6], px[6];  // A+ e+ and Ax ex, packed (xx, yy, zz, 2xy, 2xz, 2yz)
+  int m_lo, m_hi;       // tranche range that can be active: [m_lo, m_hi)
+  uint32_t key;         // sort key (longer tracks first, then start frequency)
+  int kc_lo;            // window centre bin at m_lo
+};
+
+// ---------------------------------------------------------------------------------
+// Paper's Fresnel auxiliary functions: C + iS = sgn(z) [(1+i)/2 - (g + i f) e^{i pi z^2/2}]
+// with f, g rational for |z| <= 6 and f = 1/(pi z), g = 0 for |z| > 6 (the printed
+// asymptotic form), evaluated at a = |z|.
+// ---------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void fresnel_fg(T a, T& f, T& g) {
+  if (a > T(6)) {
+    f = T(1) / (T(kPi) * a);
+    g = T(0);
+  } else {
+    f = (T(1) + T(0.926) * a) / (T(2) + a * (T(1.792) + T(3.104) * a));
+    g = T(1) / (T(2) + a * (T(4.142) + a * (T(3.492) + T(6.670) * a)));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Double-float ("df") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, giving
+// ~48 significant bits from FP32 operations. Error-free transformations after Knuth
+// (two-sum) and Dekker (two-product, here with an FMA). The intrinsics keep the
+// compiler from contracting or reassociating the exact steps.
+// ---------------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_make(double x) {
+  df r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  df r;
+  r.hi = __fadd_rn(a, b);
+  r.lo = __fsub_rn(b, __fsub_rn(r.hi, a));
+  return r;
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  df r;
+  r.hi = __fadd_rn(a, b);
+  float bb = __fsub_rn(r.hi, a);
+  r.lo = __fadd_rn(__fsub_rn(a, __fsub_rn(r.hi, bb)), __fsub_rn(b, bb));
+  return r;
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ df df_add_f(df x, float b) {
+  df s = two_sum(x.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+  float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df x, float b) {
+  float p = __fmul_rn(x.hi, b);
+  float e = __fmaf_rn(x.hi, b, -p);
+  e = __fmaf_rn(x.lo, b, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sqr(df x) {
+  float p = __fmul_rn(x.hi, x.hi);
+  float e = __fmaf_rn(x.hi, x.hi, -p);
+  e = __fmaf_rn(2.0f * x.hi, x.lo, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ float df_to_f(df x) { return __fadd_rn(x.hi, x.lo); }
+
+// Host/device status word written by checked kernels.
+enum DeviceErr : int { kDevOk = 0, kDevBadIndex = 1 };
+
+}  // namespace tfs

@@ -1,0 +1,63 @@
+// Kernel argument blocks and host-side launchers of libtfs.
+#pragma once
+
+#include "tfs_internal.cuh"
+
+namespace tfs {
+
+// Everything an evaluation kernel needs, passed by value.
+struct EvalArgs {
+  GridDesc g;
+  int response;
+  int pitch;                    // m-dimension pitch of the mixed planes
+  const TrancheD* tabD;         // [N_t]
+  const TrancheF* tabF;         // [N_t]
+  const double2* u64;           // [c][m][k] FP64 u = d~ w
+  const double* w64;            // [c][m][k] FP64 w
+  const float2* u32;            // [c][m][k] scaled FP32 u
+  const float* w32;             // [c][m][k] scaled FP32 w
+  const void* Umix;             // [k][pitch] mixed planes
+  const void* Wmix;
+  const uint8_t* mask;          // [N_t]
+  const TplConst* tpl;          // [n_tpl]
+  const int32_t* perm;          // processing order (mixed path), may be null
+  int64_t n_tpl;
+  Levels lv;                    // global levels (per-template mode: lv.n == 0)
+  const int32_t* nseg_pt;       // per-template N_seg or null
+  int fine_cap;                 // smem fine-segment slots per warp (mixed path)
+  double* out_stat;             // [levels][n_tpl]
+  int32_t* out_neff;            // [levels][n_tpl] or null
+  int32_t* out_diag;            // [2][n_tpl] or null
+  double out_scale;             // Upsilon = out_scale * sum |Z|^2 / N
+  int* counter;                 // work ticket of the persistent launch
+  int* dev_err;                 // checked-mode status word
+  int checked;
+};
+
+cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, cudaStream_t s);
+cudaError_t launch_absmax(int64_t n, const double* d_re, const double* d_im, const double* w,
+                          unsigned long long* umax, unsigned long long* wmax, int* bad,
+                          int n_sm, cudaStream_t s);
+cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, const double* w,
+                            double su, double sw, double2* u64, double* w64, float2* u32,
+                            float* w32, int n_sm, cudaStream_t s);
+cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
+                              const double* d_im, const double* w, double su, double sw, void* U,
+                              void* W, int n_sm, cudaStream_t s);
+cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
+                         TplConst* out, cudaStream_t s);
+
+cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s);
+// Persistent mixed-precision launch; grid = ctas, block = 32 * warps.
+cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
+                              cudaStream_t s);
+cudaError_t mixed_occupancy(int n_chan, int pix, int warps, int fine_cap, int* ctas_per_sm);
+
+struct AscentParams {
+  double step[8], lo[8], hi[8];
+};
+cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const AscentParams& p,
+                          cudaStream_t s);
+
+}  // namespace tfs

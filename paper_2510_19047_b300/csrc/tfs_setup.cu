@@ -1,0 +1,377 @@
+// Set-up kernels of libtfs: per-tranche geometry, packing of the weighted data
+// u = d~ / S and weights w = 1/S into each evaluation path's layout, and the
+// per-template constants (FP64, once per template per call).
+#include <math.h>
+
+#include <algorithm>
+
+#include "tfs_internal.cuh"
+#include "tfs_kernels.cuh"
+
+namespace tfs {
+
+// Long-wavelength detector tensors of A and E at detector time t (FP64), packed
+// (xx, yy, zz, xy, xz, yz). The constellation's guiding centre moves on a circular
+// 1 AU orbit, r = (cos a, sin a, 0), a = 2 pi t / yr; the constellation plane is
+// inclined by 60 degrees (normal -r/2 + (sqrt3/2) z) and the spacecraft sit at
+// angles -a + 2 pi i / 3 in that plane. X = (l01 l01 - l02 l02)/2 and cyclic,
+// A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6.
+__device__ void lw_tensors(double t, double DA[6], double DE[6], double* ca_out,
+                           double* sa_out) {
+  const double tt = fmod(t, kYearS);
+  double sa, ca;
+  sincospi(2.0 * tt / kYearS, &sa, &ca);
+  *ca_out = ca;
+  *sa_out = sa;
+  const double h3 = 0.5 * sqrt(3.0);
+  const double e1[3] = {h3 * ca, h3 * sa, 0.5};
+  const double e2[3] = {-sa, ca, 0.0};
+  double q[3][3];
+  for (int i = 0; i < 3; ++i) {
+    double s, c;
+    sincos(-2.0 * kPi * tt / kYearS + 2.0 * kPi * i / 3.0, &s, &c);
+    for (int k = 0; k < 3; ++k) q[i][k] = c * e1[k] + s * e2[k];
+  }
+  double D[3][6];
+  for (int c = 0; c < 3; ++c) {
+    double l1[3], l2[3], n1 = 0, n2 = 0;
+    const int i1 = (c + 1) % 3, i2 = (c + 2) % 3;
+    for (int k = 0; k < 3; ++k) {
+      l1[k] = q[i1][k] - q[c][k];
+      l2[k] = q[i2][k] - q[c][k];
+      n1 += l1[k] * l1[k];
+      n2 += l2[k] * l2[k];
+    }
+    n1 = rsqrt(n1);
+    n2 = rsqrt(n2);
+    for (int k = 0; k < 3; ++k) {
+      l1[k] *= n1;
+      l2[k] *= n2;
+    }
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int p = 0; p < 6; ++p) D[c][p] = 0.5 * (l1[ia[p]] * l1[ib[p]] - l2[ia[p]] * l2[ib[p]]);
+  }
+  for (int p = 0; p < 6; ++p) {
+    DA[p] = (D[2][p] - D[0][p]) * (1.0 / sqrt(2.0));
+    DE[p] = (D[0][p] - 2.0 * D[1][p] + D[2][p]) * (1.0 / sqrt(6.0));
+  }
+}
+
+__global__ void k_tranche_table(GridDesc g, TrancheD* td, TrancheF* tf) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.n_tranche) return;
+  const double t = g.t0 + (double)m * g.dT;
+  TrancheD d;
+  d.t = t;
+  lw_tensors(t, d.DA, d.DE, &d.ca, &d.sa);
+  d.pad = 0.0;
+  td[m] = d;
+  TrancheF f;
+  f.t_hi = (float)t;
+  f.t_lo = (float)(t - (double)f.t_hi);
+  f.ca_hi = (float)d.ca;
+  f.ca_lo = (float)(d.ca - (double)f.ca_hi);
+  f.sa_hi = (float)d.sa;
+  f.sa_lo = (float)(d.sa - (double)f.sa_hi);
+  f.pad0 = f.pad1 = 0.0f;
+  for (int p = 0; p < 6; ++p) {
+    f.DA[p] = (float)d.DA[p];
+    f.DE[p] = (float)d.DE[p];
+  }
+  tf[m] = f;
+}
+
+// Largest |Re u|, |Im u| and w over the grid, and a count of invalid weights
+// (negative, NaN or infinite) or non-finite data under a positive weight.
+__global__ void k_absmax(int64_t n, const double* d_re, const double* d_im, const double* w,
+                         unsigned long long* umax, unsigned long long* wmax, int* bad) {
+  double lu = 0.0, lw = 0.0;
+  int lbad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (!(wi >= 0.0) || isinf(wi)) {
+      ++lbad;
+      continue;
+    }
+    if (wi == 0.0) continue;
+    const double ur = d_re[i] * wi, ui = d_im[i] * wi;
+    if (!isfinite(ur) || !isfinite(ui)) {
+      ++lbad;
+      continue;
+    }
+    lu = fmax(lu, fmax(fabs(ur), fabs(ui)));
+    lw = fmax(lw, wi);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lu = fmax(lu, __shfl_down_sync(0xffffffffu, lu, o));
+    lw = fmax(lw, __shfl_down_sync(0xffffffffu, lw, o));
+    lbad += __shfl_down_sync(0xffffffffu, lbad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(umax, (unsigned long long)__double_as_longlong(lu));
+    atomicMax(wmax, (unsigned long long)__double_as_longlong(lw));
+    if (lbad) atomicAdd(bad, lbad);
+  }
+}
+
+// [c][m][k] layouts of the FP64 path (unscaled) and of the plain FP32 path (scaled by
+// su, sw so that FP32 sums cannot overflow for any physical units of d and S).
+__global__ void k_pack_ref(int64_t n, const double* d_re, const double* d_im, const double* w,
+                           double su, double sw, double2* u64, double* w64, float2* u32,
+                           float* w32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    double ur = 0.0, ui = 0.0;
+    if (wi > 0.0) {
+      ur = d_re[i] * wi;
+      ui = d_im[i] * wi;
+    }
+    u64[i] = make_double2(ur, ui);
+    w64[i] = wi > 0.0 ? wi : 0.0;
+    u32[i] = make_float2((float)(ur * su), (float)(ui * su));
+    w32[i] = (float)((wi > 0.0 ? wi : 0.0) * sw);
+  }
+}
+
+template <int PIX>
+struct PixStore;
+template <>
+struct PixStore<TFS_PIX_F32> {
+  using U = float4;
+  using W = float2;
+  __device__ static U u(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+  __device__ static W w(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct PixStore<TFS_PIX_F16> {
+  using U = uint2;
+  using W = uint32_t;
+  __device__ static uint32_t h2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __device__ static U u(float a, float b, float c, float d) { return make_uint2(h2(a, b), h2(c, d)); }
+  __device__ static W w(float a, float b) { return h2(a, b); }
+};
+template <>
+struct PixStore<TFS_PIX_BF16> {
+  using U = uint2;
+  using W = uint32_t;
+  __device__ static uint32_t h2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __device__ static U u(float a, float b, float c, float d) { return make_uint2(h2(a, b), h2(c, d)); }
+  __device__ static W w(float a, float b) { return h2(a, b); }
+};
+
+// Mixed-path layout: frequency-major planes U[k][m] (both channels' u per pixel) and
+// W[k][m] (both channels' w), m padded to `pitch`, so that the 32 lanes of a warp,
+// which handle 32 consecutive tranches of one template, read consecutive words.
+template <int PIX>
+__global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const double* d_im,
+                             const double* w, double su, double sw,
+                             typename PixStore<PIX>::U* U, typename PixStore<PIX>::W* W) {
+  const int64_t npix = (int64_t)g.n_bins * pitch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / pitch), m = (int)(i % pitch);
+    float v[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (m < g.n_tranche) {
+      for (int c = 0; c < g.n_chan; ++c) {
+        const int64_t s = ((int64_t)c * g.n_tranche + m) * g.n_bins + k;
+        const double wi = w[s];
+        if (wi > 0.0) {
+          v[c][0] = (float)(d_re[s] * wi * su);
+          v[c][1] = (float)(d_im[s] * wi * su);
+          v[c][2] = (float)(wi * sw);
+        }
+      }
+    }
+    U[i] = PixStore<PIX>::u(v[0][0], v[0][1], v[1][0], v[1][1]);
+    W[i] = PixStore<PIX>::w(v[0][2], v[1][2]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Per-template constants.
+// ---------------------------------------------------------------------------------
+
+// Barycentre time t' at which the source-frame frequency equals f_target:
+// F0 (y^3 + C2 y^5) = f_target with y = (1 - t'/t_c)^(-1/8), by Newton's method.
+__device__ double time_at_frequency(double tc, double F0, double C2, double f_target) {
+  double y = cbrt(f_target / F0);
+  for (int it = 0; it < 30; ++it) {
+    const double y2 = y * y;
+    const double g = F0 * y * y2 * (1.0 + C2 * y2) - f_target;
+    const double gp = F0 * y2 * (3.0 + 5.0 * C2 * y2);
+    const double dy = g / gp;
+    y -= dy;
+    if (fabs(dy) < 1e-15 * y) break;
+  }
+  const double y2 = y * y, y4 = y2 * y2;
+  return tc * (1.0 - 1.0 / (y4 * y4));
+}
+
+__global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_order,
+                        GridDesc g, TplConst* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double th[8];
+  for (int p = 0; p < 8; ++p) th[p] = theta[(int64_t)p * n + i];
+  TplConst c;
+  const double Mc = th[0] * kGMsunS, eta = th[1], f0 = th[2];
+  const bool ok = isfinite(th[0]) && isfinite(eta) && isfinite(f0) && isfinite(th[3]) &&
+                  isfinite(th[4]) && isfinite(th[5]) && isfinite(th[6]) && isfinite(th[7]) &&
+                  Mc > 0.0 && f0 > 0.0 && (pn_order == 0 || (eta > 0.0 && eta <= 0.25));
+  if (!ok) {
+    c = TplConst{};
+    c.tc = 1.0;
+    c.F0 = 1.0;
+    c.key = 0xffffffffu;
+    out[i] = c;
+    return;
+  }
+  if (pn_order == 0) {
+    // Newtonian: tau0 = (5/256) (pi f0)^(-8/3) Mc^(-5/3); f = f0 u^(-3/8);
+    // Phi = phi0 + (16 pi / 5) f0 tau0 (1 - u^(5/8)), u = 1 - t/tau0
+    const double tau0 = (5.0 / 256.0) * pow(kPi * f0, -8.0 / 3.0) * pow(Mc, -5.0 / 3.0);
+    c.tc = tau0;
+    c.F0 = f0;
+    c.C2 = 0.0;
+    c.P5 = (16.0 * kPi / 5.0) * f0 * tau0;
+    c.P3 = 0.0;
+  } else {
+    // 1PN TaylorT3 with x = Theta^(-1/8), Theta = eta (t_c - t) / (5 M):
+    // f = x^3 (1 + (743/2688 + 11 eta/32) x^2) / (8 pi M),
+    // Phi = phi_c - (2/eta) (Theta^(5/8) + (3715/8064 + 55 eta/96) Theta^(3/8))
+    const double M = Mc * pow(eta, -0.6);
+    const double cf = 743.0 / 2688.0 + 11.0 * eta / 32.0;
+    const double cp = 3715.0 / 8064.0 + 55.0 * eta / 96.0;
+    const double yv = 8.0 * kPi * M * f0;
+    double x = cbrt(yv);
+    for (int it = 0; it < 50; ++it) {
+      const double x2 = x * x;
+      const double dx = (x * x2 * (1.0 + cf * x2) - yv) / (x2 * (3.0 + 5.0 * cf * x2));
+      x -= dx;
+      if (fabs(dx) < 1e-16 * x) break;
+    }
+    const double x2 = x * x, x4 = x2 * x2;
+    const double Theta0 = 1.0 / (x4 * x4);
+    c.tc = 5.0 * M * Theta0 / eta;
+    c.F0 = x * x2 / (8.0 * kPi * M);
+    c.C2 = cf * x2;
+    c.P5 = (2.0 / eta) * pow(Theta0, 0.625);
+    c.P3 = (2.0 / eta) * cp * pow(Theta0, 0.375);
+  }
+  c.phi0 = th[3];
+  // polarisation tensors: p0 = (sin l, -cos l, 0), q0 = n x p0, rotated by psi
+  double sl, cl, sb, cb, sps, cps;
+  sincos(th[4], &sl, &cl);
+  sincos(th[5], &sb, &cb);
+  sincos(th[6], &sps, &cps);
+  const double p0[3] = {sl, -cl, 0.0}, q0[3] = {sb * cl, sb * sl, -cb};
+  double p[3], q[3];
+  for (int k = 0; k < 3; ++k) {
+    p[k] = cps * p0[k] + sps * q0[k];
+    q[k] = -sps * p0[k] + cps * q0[k];
+  }
+  const double ci = cos(th[7]);
+  const double Ap = 0.5 * (1.0 + ci * ci), Ax = ci;
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int k = 0; k < 6; ++k) {
+    const double two = k < 3 ? 1.0 : 2.0;  // off-diagonal terms appear twice in D:e
+    c.pp[k] = two * Ap * (p[ia[k]] * p[ib[k]] - q[ia[k]] * q[ib[k]]);
+    c.px[k] = two * Ax * (p[ia[k]] * q[ib[k]] + q[ia[k]] * p[ib[k]]);
+  }
+  c.dop_c = kAuS * cb * cl;
+  c.dop_s = kAuS * cb * sl;
+  // Tranches that can be active: the window k_c +- 10 must lie in [1, N_bins - 1],
+  // i.e. 10 df < f_nm <= (N_bins - 11) df, and t' < t_c. The Doppler factor moves
+  // f by at most 1.1e-4 relative and t' by at most 1 AU/c; a margin covers both.
+  const double dop_f = 1.5e-4, dop_t = kAuS + 1.0;
+  const double f_lo = 10.0 * g.df / (1.0 + dop_f);
+  const double f_hi = (g.n_bins - 11) * g.df / (1.0 - dop_f);
+  const double tp_lo = time_at_frequency(c.tc, c.F0, c.C2, f_lo);
+  const double tp_hi = fmin(time_at_frequency(c.tc, c.F0, c.C2, f_hi), c.tc);
+  const double T_end = g.t0 + g.n_tranche * g.dT;
+  double m_lo = floor((tp_lo - dop_t - g.t0) / g.dT);
+  double m_hi = floor((tp_hi + dop_t - g.t0) / g.dT) + 1.0;
+  m_lo = fmax(0.0, fmin(m_lo, (double)g.n_tranche));
+  m_hi = fmax(m_lo, fmin(m_hi, (double)g.n_tranche));
+  if (tp_hi + dop_t < g.t0 || tp_lo - dop_t > T_end) m_hi = m_lo;
+  c.m_lo = (int)m_lo;
+  c.m_hi = (int)m_hi;
+  // sort key: longer ranges first (in 32-tranche blocks), then by start frequency
+  const int blocks = (c.m_hi - c.m_lo + 31) >> 5;
+  const double tp0 = g.t0 + c.m_lo * g.dT;
+  double f_start = c.F0;
+  if (tp0 < c.tc) {
+    const double u = 1.0 - tp0 / c.tc;
+    const double y = pow(u, -0.125), y2 = y * y;
+    f_start = c.F0 * y * y2 * (1.0 + c.C2 * y2);
+  }
+  const int kc_lo = (int)fmin(65535.0, fmax(0.0, ceil(f_start / g.df)));
+  c.kc_lo = kc_lo;
+  c.key = ((uint32_t)(0xffff - min(blocks, 0xffff)) << 16) | (uint32_t)kc_lo;
+  out[i] = c;
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------
+cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, cudaStream_t s) {
+  k_tranche_table<<<(g.n_tranche + 127) / 128, 128, 0, s>>>(g, td, tf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(int64_t n, const double* d_re, const double* d_im, const double* w,
+                          unsigned long long* umax, unsigned long long* wmax, int* bad,
+                          int n_sm, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8);
+  k_absmax<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(n, d_re, d_im, w, umax, wmax, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, const double* w,
+                            double su, double sw, double2* u64, double* w64, float2* u32,
+                            float* w32, int n_sm, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16);
+  k_pack_ref<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(n, d_re, d_im, w, su, sw, u64, w64, u32,
+                                                     w32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
+                              const double* d_im, const double* w, double su, double sw, void* U,
+                              void* W, int n_sm, cudaStream_t s) {
+  const int64_t npix = (int64_t)g.n_bins * pitch;
+  const int blocks = (int)std::min<int64_t>((npix + 255) / 256, (int64_t)n_sm * 16);
+  switch (pix) {
+    case TFS_PIX_F32:
+      k_pack_mixed<TFS_PIX_F32><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
+                                                        (float4*)U, (float2*)W);
+      break;
+    case TFS_PIX_F16:
+      k_pack_mixed<TFS_PIX_F16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
+                                                        (uint2*)U, (uint32_t*)W);
+      break;
+    default:
+      k_pack_mixed<TFS_PIX_BF16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
+                                                         (uint2*)U, (uint32_t*)W);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
+                         TplConst* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, n, pn_order, g, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tfs

@@ -1,0 +1,237 @@
+"""CUDA paths against the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (relative error of Upsilon per template and level):
+  FP64 path          1e-10
+  plain FP32 path    1e-4
+  mixed, FP32 pixels 1e-4
+  mixed, FP16 pixels max 1.5e-3, p99 1e-3   (3x and 2x the FP16 unit roundoff 2^-11)
+  mixed, BF16 pixels max 1.2e-2, p99 8e-3   (3x and 2x the BF16 unit roundoff 2^-8)
+The reduced-precision bounds follow from rounding u = d~/S and w = 1/S once to the
+storage type: each pixel carries an independent relative error below the unit
+roundoff, so |Z_n| and N_n move by a random fraction of it and Upsilon by about twice
+that.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_19047_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {("fp64", "f16"): (1e-10, 1e-10), ("plain", "f16"): (1e-4, 1e-4),
+       ("mixed", "f32"): (1e-4, 1e-4), ("mixed", "f16"): (1.5e-3, 1e-3),
+       ("mixed", "bf16"): (1.2e-2, 8e-3)}
+CASES = list(TOL)
+
+
+def rel_err(got, ref):
+    got, ref = np.asarray(got, float), np.asarray(ref, float)
+    assert np.all(np.isfinite(got))
+    zero = ref == 0
+    assert np.all(got[zero] == 0)
+    r = np.abs(got[~zero] - ref[~zero]) / ref[~zero]
+    return (r.max(), np.percentile(r, 99)) if r.size else (0.0, 0.0)
+
+
+def ctx_for(D, path, pixel, **kw):
+    from paper_2510_19047_b300.binding import TFS
+    c = TFS(0, path=path, pixel=pixel, pn_order=D.pn_order, response=D.response, **kw)
+    c.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    c.set_noise_weights(D.w, D.mask)
+    return c
+
+
+@pytest.fixture(scope="module")
+def week():
+    return synth.week_one_channel(seed=0)
+
+
+@pytest.fixture(scope="module")
+def ae45():
+    return synth.two_year_two_channel(seed=77, n_inj=3, n_tranche=384, L=2048)
+
+
+@pytest.fixture(scope="module")
+def ae45_bank(ae45):
+    th = synth.two_year_bank(253, seed=5)  # ragged: not a multiple of 32 or 128
+    th[:, :3] = ae45.injections
+    return th
+
+
+@pytest.mark.parametrize("path,pixel", CASES)
+def test_week_one_channel(week, path, pixel):
+    th = synth.week_bank(1024, 0)
+    ref, rneff, rnact, rnnc = oracle.statistic(week.d, week.w, week.mask, th, 8, week.dT)
+    c = ctx_for(week, path, pixel)
+    got, neff, diag = c.eval_statistic(th, 8, diag=True)
+    mx, p99 = rel_err(got, ref)
+    assert mx < TOL[(path, pixel)][0] and p99 < TOL[(path, pixel)][1], (mx, p99)
+    assert np.array_equal(neff, rneff)
+    assert np.array_equal(diag[0], rnact) and np.array_equal(diag[1], rnnc)
+
+
+@pytest.mark.parametrize("path,pixel", CASES)
+def test_two_channel_response_gaps_levels(ae45, ae45_bank, path, pixel):
+    lev = [128, 32, 8]
+    refs = [oracle.statistic(ae45.d, ae45.w, ae45.mask, ae45_bank, L, ae45.dT, pn_order=1,
+                             response=1) for L in lev]
+    c = ctx_for(ae45, path, pixel)
+    got, neff, diag = c.eval_statistic(ae45_bank, lev, diag=True)
+    for i, (ref, rneff, rnact, _) in enumerate(refs):
+        mx, p99 = rel_err(got[i], ref)
+        assert mx < TOL[(path, pixel)][0] and p99 < TOL[(path, pixel)][1], (lev[i], mx, p99)
+        assert np.array_equal(neff[i], rneff)
+    # the double-float track decides the window like the FP64 oracle
+    assert np.abs(diag[0] - refs[0][2]).max() <= (0 if path != "mixed" else 1)
+
+
+@pytest.mark.parametrize("path", ["fp64", "plain", "mixed"])
+def test_per_template_segment_counts(ae45, ae45_bank, path):
+    th = ae45_bank[:, :96]
+    choices = np.array([128, 32, 8, 1], np.int32)
+    ns = choices[np.arange(th.shape[1]) % 4]
+    c = ctx_for(ae45, path, "f32")
+    got, neff, _ = c.eval_statistic(th, ns, per_template=True)
+    tol = {"fp64": 1e-10, "plain": 1e-4, "mixed": 1e-4}[path]
+    for L in choices:
+        sel = ns == L
+        ref, rneff, _, _ = oracle.statistic(ae45.d, ae45.w, ae45.mask, th[:, sel], int(L), ae45.dT,
+                                            pn_order=1, response=1)
+        assert rel_err(got[sel], ref)[0] < tol
+        assert np.array_equal(neff[sel], rneff)
+
+
+def test_device_and_host_pointers_agree(ae45, ae45_bank):
+    import torch
+    c = ctx_for(ae45, "mixed", "f16")
+    host, _, _ = c.eval_statistic(ae45_bank, [64, 8])
+    dev, _, _ = c.eval_statistic(torch.from_numpy(ae45_bank).cuda(), [64, 8])
+    torch.cuda.synchronize()
+    assert np.array_equal(host, dev.cpu().numpy())  # deterministic, bit for bit
+    again, _, _ = c.eval_statistic(ae45_bank, [64, 8])
+    assert np.array_equal(host, again)
+
+
+def test_edge_cases(ae45):
+    from paper_2510_19047_b300.binding import TFS, TFSError
+    for path in ("fp64", "plain", "mixed"):
+        c = ctx_for(ae45, path, "f16")
+        # empty batch
+        s, n, _ = c.eval_statistic(np.zeros((8, 0)), 8)
+        assert s.shape == (0,)
+        # out of band (above the top bin), non-physical, and one ordinary template
+        th = synth.two_year_bank(3, seed=1)
+        th[2, 0] = 0.3       # f_0 above (N_bins - 11) df
+        th[0, 1] = -5.0      # M_c < 0
+        s, n, d = c.eval_statistic(th, [16, 4], diag=True)
+        assert np.all(s[:, :2] == 0) and np.all(n[:, :2] == 0) and np.all(d[:, :2] == 0)
+        assert np.all(s[:, 2] > 0)
+        # N_seg must divide N_t
+        with pytest.raises(TFSError, match="NSEG"):
+            c.eval_statistic(th, 7)
+        with pytest.raises(TFSError, match="ARG"):
+            c.eval_statistic(th, [1, 2, 4, 8, 16])
+    # a grid whose tranches are all gapped
+    D = synth.TFData(d=ae45.d, w=ae45.w, mask=np.zeros_like(ae45.mask), dt=ae45.dt, dT=ae45.dT,
+                     pn_order=1, response=1)
+    c = ctx_for(D, "mixed", "f16")
+    s, n, _ = c.eval_statistic(synth.two_year_bank(40, seed=3), 16)
+    assert np.all(s == 0) and np.all(n == 0)
+    # the mixed path folds at most 1024 finest segments; the FP64 path has no such limit
+    big = synth.TFData(d=np.zeros((1, 2048, 64), complex), w=np.ones((1, 2048, 64)),
+                       mask=np.ones(2048, np.uint8), dt=5.0, dT=640.0)
+    c = ctx_for(big, "mixed", "f16")
+    with pytest.raises(TFSError, match="ARG"):
+        c.eval_statistic(synth.week_bank(4), 2048)
+    c.set_options(path="fp64")
+    c.eval_statistic(synth.week_bank(4), 2048)
+    # calls before data is loaded
+    c = TFS(0)
+    with pytest.raises(TFSError, match="STATE"):
+        c.eval_statistic(synth.week_bank(4), 1)
+    with pytest.raises(TFSError, match="STATE"):
+        c.set_noise_weights(np.ones((1, 4, 64)))
+    # invalid weights are rejected
+    c.load_tf_data(week_like(), 5.0, 1280.0)
+    w = np.ones((1, 16, 64))
+    w[0, 3, 5] = -1.0
+    with pytest.raises(TFSError, match="ARG"):
+        c.set_noise_weights(w)
+
+
+def week_like():
+    return np.zeros((1, 16, 64), complex)
+
+
+def test_select_top_matches_stable_sort():
+    from paper_2510_19047_b300.binding import TFS
+    rng = np.random.default_rng(3)
+    c = TFS(0)
+    for n, k in ((1, 1), (1000, 10), (100_003, 1000)):
+        x = np.round(rng.normal(size=n), 2)  # many ties
+        idx = c.select_top(x, k)
+        ref = np.lexsort((np.arange(n), -x))[:k]
+        assert np.array_equal(idx, ref)
+    x = rng.normal(size=5000)
+    x[7] = np.nan
+    idx = c.select_top(x, 5000)
+    assert idx[-1] == 7
+
+
+def test_ascent_step_update():
+    from paper_2510_19047_b300.binding import TFS
+    rng = np.random.default_rng(4)
+    th = synth.two_year_bank(300, seed=8)
+    g = rng.normal(size=th.shape)
+    step = np.array([1e-3, 1e-4, 1e-6, 0.1, 0.1, 0.1, 0.1, 0.1])
+    lo = np.array([5, 0.05, 1e-4, 0, 0, -np.pi / 2, 0, 0])
+    hi = np.array([100, 0.25, 0.1, 2 * np.pi, 2 * np.pi, np.pi / 2, np.pi, np.pi])
+    ref = th + step[:, None] * g
+    for p in (0, 1, 2, 5, 7):
+        ref[p] = np.clip(ref[p], lo[p], hi[p])
+    ref[3] = np.mod(ref[3], 2 * np.pi)
+    ref[4] = np.mod(ref[4], 2 * np.pi)
+    ref[6] = np.mod(ref[6], np.pi)
+    c = TFS(0)
+    out = th.copy()
+    c.ascent_step(out, g, step, lo, hi)
+    np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.fixture(scope="module")
+def two_year():
+    return synth.cached(synth.two_year_two_channel)
+
+
+def test_two_year_full_bank_sampled(two_year):
+    """The bench workload (1e6 templates, N_seg 256/64/16 in one mixed launch): sampled
+    templates against the oracle, and properties that hold for every template."""
+    import torch
+    D = two_year
+    lev = [256, 64, 16]
+    th = synth.two_year_bank(1_000_000, seed=2002)
+    c = ctx_for(D, "mixed", "f16")
+    st, ne, dg = c.eval_statistic(torch.from_numpy(th).cuda(), lev, diag=True)
+    st, ne, dg = st.cpu().numpy(), ne.cpu().numpy(), dg.cpu().numpy()
+    assert np.all(np.isfinite(st)) and np.all(st >= 0)
+    assert np.all(ne <= np.array(lev)[:, None])
+    # nested segmentations (Cauchy-Schwarz), up to the mixed-precision error
+    assert np.all(st[0] >= st[1] * (1 - 3e-3)) and np.all(st[1] >= st[2] * (1 - 3e-3))
+    # noise-dominated bank: Upsilon ~ chi^2 with 2 N_eff dof on average
+    act = ne[0] > 0
+    assert abs(np.mean(st[0][act]) / np.mean(2 * ne[0][act]) - 1) < 0.02
+    idx = np.linspace(0, th.shape[1] - 1, 12).astype(int)
+    for i, L in enumerate(lev):
+        ref, rneff, rnact, _ = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT,
+                                                pn_order=1, response=1)
+        mx, _ = rel_err(st[i, idx], ref)
+        assert mx < TOL[("mixed", "f16")][0], (L, mx)
+        assert np.array_equal(ne[i, idx], rneff)
+    # FP64 and plain paths on the sampled templates
+    for path, tol in (("fp64", 1e-10), ("plain", 1e-4)):
+        c2 = ctx_for(D, path, "f16")
+        got, _, _ = c2.eval_statistic(th[:, idx], lev)
+        for i, L in enumerate(lev):
+            ref = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT, pn_order=1, response=1)[0]
+            assert rel_err(got[i], ref)[0] < tol, (path, L)
