@@ -625,8 +625,59 @@ int tfs_ascent_step(tfs_ctx* c, double* theta, const double* grad, int64_t n, co
 int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream) {
   if (!c) return TFS_ERR_ARG;
-  (void)theta; (void)n_tpl; (void)n_seg; (void)out_stat; (void)out_grad; (void)stream;
-  return fail(c, TFS_ERR_STATE, "gradient kernel not built in this library version");
+  c->err.clear();
+  if (!c->has_data || !c->has_weights)
+    return fail(c, TFS_ERR_STATE, "load_tf_data and set_noise_weights must be called first");
+  if (n_tpl < 0 || n_tpl > INT32_MAX) return fail(c, TFS_ERR_ARG, "n_tpl must be in [0, 2^31)");
+  if (n_seg < 1) return fail(c, TFS_ERR_ARG, "N_seg must be >= 1");
+  if (c->g.n_tranche % n_seg != 0)
+    return fail(c, TFS_ERR_NSEG, "N_t = " + std::to_string(c->g.n_tranche) +
+                                     " is not divisible by N_seg = " + std::to_string(n_seg));
+  if (n_seg > kMixedMaxFine) return fail(c, TFS_ERR_ARG, "the gradient kernel supports N_seg <= 1024");
+  if (n_tpl == 0) return TFS_OK;
+  if (!theta || !out_stat || !out_grad) return fail(c, TFS_ERR_ARG, "null argument");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  int r;
+  const void* th = nullptr;
+  if ((r = device_view(c, theta, (size_t)n_tpl * 64, c->theta, s, &th))) return r;
+  if ((r = buf_ensure(c, c->tpl, (size_t)n_tpl * sizeof(TplConst)))) return r;
+  const bool dev_stat = is_device_ptr(out_stat), dev_grad = is_device_ptr(out_grad);
+  double* os = out_stat;
+  double* og = out_grad;
+  if (!dev_stat) {
+    if ((r = buf_ensure(c, c->stat, (size_t)n_tpl * 8))) return r;
+    os = (double*)c->stat.p;
+  }
+  if (!dev_grad) {
+    if ((r = buf_ensure(c, c->grad, (size_t)n_tpl * 64))) return r;
+    og = (double*)c->grad.p;
+  }
+  c->launches = 0;
+  prof_record(c, 0, s);
+  CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, c->g, (TplConst*)c->tpl.p, s));
+  prof_record(c, 1, s);
+  prof_record(c, 2, s);
+  const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);
+  CUDA_TRY(c, launch_grad(c->g, c->opt.response, c->opt.pn_order, (const TrancheD*)c->tabD.p,
+                          (const float2*)c->u32.p, (const float*)c->w32.p,
+                          (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
+                          n_tpl, n_seg, scale, os, og, s));
+  c->launches = 2;
+  prof_record(c, 3, s);
+  if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
+  if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));
+  prof_record(c, 4, s);
+  if (!dev_stat || !dev_grad || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (c->opt.profile) {
+    float ms;
+    for (int i = 0; i < 4; ++i) {
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      c->prof[i] = ms;
+    }
+    c->prof_valid = true;
+  }
+  return TFS_OK;
 }
 
 }  // extern "C"

@@ -59,5 +59,10 @@ struct AscentParams {
 };
 cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const AscentParams& p,
                           cudaStream_t s);
+// Adjoint gradient at one N_seg: out_stat [n], out_grad [8][n] (device pointers).
+cudaError_t launch_grad(const GridDesc& g, int response, int pn_order, const TrancheD* tabD,
+                        const float2* u32, const float* w32, const uint8_t* mask,
+                        const double* theta, const TplConst* tpl, int64_t n, int n_seg,
+                        double scale, double* out_stat, double* out_grad, cudaStream_t s);
 
 }  // namespace tfs

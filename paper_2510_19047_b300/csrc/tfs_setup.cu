@@ -7,6 +7,7 @@
 
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
+#include "tfs_source.cuh"
 
 namespace tfs {
 
@@ -235,60 +236,19 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
     out[i] = c;
     return;
   }
-  if (pn_order == 0) {
-    // Newtonian: tau0 = (5/256) (pi f0)^(-8/3) Mc^(-5/3); f = f0 u^(-3/8);
-    // Phi = phi0 + (16 pi / 5) f0 tau0 (1 - u^(5/8)), u = 1 - t/tau0
-    const double tau0 = (5.0 / 256.0) * pow(kPi * f0, -8.0 / 3.0) * pow(Mc, -5.0 / 3.0);
-    c.tc = tau0;
-    c.F0 = f0;
-    c.C2 = 0.0;
-    c.P5 = (16.0 * kPi / 5.0) * f0 * tau0;
-    c.P3 = 0.0;
-  } else {
-    // 1PN TaylorT3 with x = Theta^(-1/8), Theta = eta (t_c - t) / (5 M):
-    // f = x^3 (1 + (743/2688 + 11 eta/32) x^2) / (8 pi M),
-    // Phi = phi_c - (2/eta) (Theta^(5/8) + (3715/8064 + 55 eta/96) Theta^(3/8))
-    const double M = Mc * pow(eta, -0.6);
-    const double cf = 743.0 / 2688.0 + 11.0 * eta / 32.0;
-    const double cp = 3715.0 / 8064.0 + 55.0 * eta / 96.0;
-    const double yv = 8.0 * kPi * M * f0;
-    double x = cbrt(yv);
-    for (int it = 0; it < 50; ++it) {
-      const double x2 = x * x;
-      const double dx = (x * x2 * (1.0 + cf * x2) - yv) / (x2 * (3.0 + 5.0 * cf * x2));
-      x -= dx;
-      if (fabs(dx) < 1e-16 * x) break;
-    }
-    const double x2 = x * x, x4 = x2 * x2;
-    const double Theta0 = 1.0 / (x4 * x4);
-    c.tc = 5.0 * M * Theta0 / eta;
-    c.F0 = x * x2 / (8.0 * kPi * M);
-    c.C2 = cf * x2;
-    c.P5 = (2.0 / eta) * pow(Theta0, 0.625);
-    c.P3 = (2.0 / eta) * cp * pow(Theta0, 0.375);
-  }
-  c.phi0 = th[3];
-  // polarisation tensors: p0 = (sin l, -cos l, 0), q0 = n x p0, rotated by psi
-  double sl, cl, sb, cb, sps, cps;
-  sincos(th[4], &sl, &cl);
-  sincos(th[5], &sb, &cb);
-  sincos(th[6], &sps, &cps);
-  const double p0[3] = {sl, -cl, 0.0}, q0[3] = {sb * cl, sb * sl, -cb};
-  double p[3], q[3];
-  for (int k = 0; k < 3; ++k) {
-    p[k] = cps * p0[k] + sps * q0[k];
-    q[k] = -sps * p0[k] + cps * q0[k];
-  }
-  const double ci = cos(th[7]);
-  const double Ap = 0.5 * (1.0 + ci * ci), Ax = ci;
-  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  const SrcT<double> src = source_of<double>(th, pn_order);
+  c.tc = src.tc;
+  c.F0 = src.F0;
+  c.C2 = src.C2;
+  c.P5 = src.P5;
+  c.P3 = src.P3;
+  c.phi0 = src.phi0;
   for (int k = 0; k < 6; ++k) {
-    const double two = k < 3 ? 1.0 : 2.0;  // off-diagonal terms appear twice in D:e
-    c.pp[k] = two * Ap * (p[ia[k]] * p[ib[k]] - q[ia[k]] * q[ib[k]]);
-    c.px[k] = two * Ax * (p[ia[k]] * q[ib[k]] + q[ia[k]] * p[ib[k]]);
+    c.pp[k] = src.pp[k];
+    c.px[k] = src.px[k];
   }
-  c.dop_c = kAuS * cb * cl;
-  c.dop_s = kAuS * cb * sl;
+  c.dop_c = src.dop_c;
+  c.dop_s = src.dop_s;
   // Tranches that can be active: the window k_c +- 10 must lie in [1, N_bins - 1],
   // i.e. 10 df < f_nm <= (N_bins - 11) df, and t' < t_c. The Doppler factor moves
   // f by at most 1.1e-4 relative and t' by at most 1 AU/c; a margin covers both.

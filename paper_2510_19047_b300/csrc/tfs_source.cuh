@@ -1,0 +1,203 @@
+// Source model of a template and its track at a tranche start, written once over the
+// scalar type R: R = double for values, R = D1 (value and one directional derivative,
+// forward mode) for the gradient kernel.
+//
+// Chirp (Sec. "Time-frequency waveform representation" expands the GW phase about
+// the tranche start; the chirp model itself is the reading stated in the header):
+//   Newtonian: t_c = tau0 = (5/256) (pi f0)^(-8/3) Mc^(-5/3),
+//              f = f0 u^(-3/8), Phi = phi0 + (16 pi/5) f0 tau0 (1 - u^(5/8)), u = 1 - t'/t_c
+//   1PN TaylorT3 in x = Theta^(-1/8), Theta = eta (t_c - t')/(5 M), M = Mc eta^(-3/5):
+//              f = x^3 (1 + (743/2688 + 11 eta/32) x^2) / (8 pi M)
+//              Phi = phi_c - (2/eta) (Theta^(5/8) + (3715/8064 + 55 eta/96) Theta^(3/8))
+//   Both as f = F0 y^3 (1 + C2 y^2), y = u^(-1/8), Phi = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)).
+// Response (Eq. tdi2 in the long-wavelength limit): T_alpha = D_alpha : (A+ e+) - i D_alpha : (Ax ex),
+// with the barycentre delay t' = t + n.r(t)/c.
+#pragma once
+
+#include <math.h>
+
+#include "tfs_internal.cuh"
+
+namespace tfs {
+
+struct D1 {
+  double v, d;
+};
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ D1 operator/(D1 a, D1 b) {
+  const double q = a.v / b.v;
+  return {q, (a.d - q * b.d) / b.v};
+}
+__device__ __forceinline__ D1 operator+(D1 a, double b) { return {a.v + b, a.d}; }
+__device__ __forceinline__ D1 operator+(double b, D1 a) { return {a.v + b, a.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, double b) { return {a.v - b, a.d}; }
+__device__ __forceinline__ D1 operator-(double b, D1 a) { return {b - a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, double b) { return {a.v * b, a.d * b}; }
+__device__ __forceinline__ D1 operator*(double b, D1 a) { return {a.v * b, a.d * b}; }
+__device__ __forceinline__ D1 operator/(D1 a, double b) { return {a.v / b, a.d / b}; }
+__device__ __forceinline__ D1 operator/(double a, D1 b) {
+  const double q = a / b.v;
+  return {q, -q * b.d / b.v};
+}
+
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(D1 x) { return x.v; }
+__device__ __forceinline__ D1 mk(double v, double d) { return {v, d}; }
+
+__device__ __forceinline__ double r_pow(double x, double p) { return pow(x, p); }
+__device__ __forceinline__ D1 r_pow(D1 x, double p) {
+  const double y = pow(x.v, p);
+  return {y, p * y / x.v * x.d};
+}
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ D1 r_sqrt(D1 x) {
+  const double s = sqrt(x.v);
+  return {s, 0.5 * x.d / s};
+}
+__device__ __forceinline__ double r_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ D1 r_log1p(D1 x) { return {log1p(x.v), x.d / (1.0 + x.v)}; }
+__device__ __forceinline__ double r_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ D1 r_expm1(D1 x) { return {expm1(x.v), exp(x.v) * x.d}; }
+__device__ __forceinline__ void r_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void r_sincos(D1 x, D1* s, D1* c) {
+  double sv, cv;
+  sincos(x.v, &sv, &cv);
+  *s = {sv, cv * x.d};
+  *c = {cv, -sv * x.d};
+}
+__device__ __forceinline__ double r_cos(double x) { return cos(x); }
+__device__ __forceinline__ D1 r_cos(D1 x) { return {cos(x.v), -sin(x.v) * x.d}; }
+
+template <class R>
+struct SrcT {
+  R tc, F0, C2, P5, P3, phi0, dop_c, dop_s;
+  R pp[6], px[6];  // A+ e+ and Ax ex packed (xx, yy, zz, 2xy, 2xz, 2yz)
+};
+
+// Template constants from theta = (Mc, eta, f0, phi0, lambda, beta, psi, iota).
+template <class R>
+__device__ SrcT<R> source_of(const R th[8], int pn_order) {
+  SrcT<R> s;
+  const R Mc = th[0] * kGMsunS;
+  const R eta = th[1];
+  const R f0 = th[2];
+  if (pn_order == 0) {
+    const R tau0 = (5.0 / 256.0) * r_pow(kPi * f0, -8.0 / 3.0) * r_pow(Mc, -5.0 / 3.0);
+    s.tc = tau0;
+    s.F0 = f0;
+    s.C2 = f0 * 0.0;
+    s.P5 = (16.0 * kPi / 5.0) * f0 * tau0;
+    s.P3 = f0 * 0.0;
+  } else {
+    const R M = Mc * r_pow(eta, -0.6);
+    const R cf = 743.0 / 2688.0 + (11.0 / 32.0) * eta;
+    const R cp = 3715.0 / 8064.0 + (55.0 / 96.0) * eta;
+    const R yv = 8.0 * kPi * M * f0;
+    // x^3 (1 + cf x^2) = yv: Newton on the value, then two steps in R so that the
+    // derivative follows the implicit function theorem
+    double x = cbrt(val(yv));
+    for (int it = 0; it < 50; ++it) {
+      const double x2 = x * x;
+      const double dx = (x * x2 * (1.0 + val(cf) * x2) - val(yv)) / (x2 * (3.0 + 5.0 * val(cf) * x2));
+      x -= dx;
+      if (fabs(dx) < 1e-16 * x) break;
+    }
+    R xr = yv * 0.0 + x;
+    for (int it = 0; it < 2; ++it) {
+      const R x2 = xr * xr;
+      xr = xr - (xr * x2 * (1.0 + cf * x2) - yv) / (x2 * (3.0 + 5.0 * cf * x2));
+    }
+    const R x2 = xr * xr, x4 = x2 * x2;
+    const R Theta0 = 1.0 / (x4 * x4);
+    s.tc = 5.0 * M * Theta0 / eta;
+    s.F0 = xr * x2 / (8.0 * kPi * M);
+    s.C2 = cf * x2;
+    s.P5 = (2.0 / eta) * r_pow(Theta0, 0.625);
+    s.P3 = (2.0 / eta) * cp * r_pow(Theta0, 0.375);
+  }
+  s.phi0 = th[3];
+  R sl, cl, sb, cb, sps, cps;
+  r_sincos(th[4], &sl, &cl);
+  r_sincos(th[5], &sb, &cb);
+  r_sincos(th[6], &sps, &cps);
+  const R zero = th[0] * 0.0;
+  const R p0[3] = {sl, -cl, zero}, q0[3] = {sb * cl, sb * sl, -cb};
+  R p[3], q[3];
+  for (int k = 0; k < 3; ++k) {
+    p[k] = cps * p0[k] + sps * q0[k];
+    q[k] = (-sps) * p0[k] + cps * q0[k];
+  }
+  const R ci = r_cos(th[7]);
+  const R Ap = 0.5 * (1.0 + ci * ci), Ax = ci;
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int k = 0; k < 6; ++k) {
+    const double two = k < 3 ? 1.0 : 2.0;  // off-diagonal terms appear twice in D:e
+    s.pp[k] = two * Ap * (p[ia[k]] * p[ib[k]] - q[ia[k]] * q[ib[k]]);
+    s.px[k] = two * Ax * (p[ia[k]] * q[ib[k]] + q[ia[k]] * p[ib[k]]);
+  }
+  s.dop_c = kAuS * cb * cl;
+  s.dop_s = kAuS * cb * sl;
+  return s;
+}
+
+template <class R>
+struct TrkT {
+  R f, fdot, dphi, amp;  // detector-frame f, fdot; phase since the anchor [rad]; (f/F0)^(2/3)
+  R Tr[2], Ti[2];
+  bool alive;
+};
+
+// Track at the start of tranche `tr` with the phase measured from the start of
+// tranche `ta` (the anchor, m_a <= m); dm_dT = (m - m_a) dT exactly.
+template <class R>
+__device__ TrkT<R> track_of(const SrcT<R>& s, const TrancheD& tr, const TrancheD& ta, double dm_dT,
+                            int resp) {
+  TrkT<R> k;
+  const R zero = s.tc * 0.0;
+  R d0 = zero, d1 = zero, d2 = zero, a0 = zero;
+  if (resp) {
+    d0 = s.dop_c * tr.ca + s.dop_s * tr.sa;
+    d1 = kOmega * (s.dop_s * tr.ca - s.dop_c * tr.sa);
+    d2 = (-kOmega * kOmega) * d0;
+    a0 = s.dop_c * ta.ca + s.dop_s * ta.sa;
+  }
+  const R tp = d0 + tr.t;
+  const R tpa = a0 + ta.t;
+  k.alive = val(tp) < val(s.tc) && val(tpa) < val(s.tc);
+  if (!k.alive) return k;
+  const R u = 1.0 - tp / s.tc;
+  const R y = r_pow(u, -0.125), y2 = y * y, y3 = y2 * y;
+  const R onec = 1.0 + s.C2 * y2;
+  const R fsrc = s.F0 * y3 * onec;
+  const R fdsrc = s.F0 * (y3 * y3 * y3 * y2) * (3.0 + 5.0 * s.C2 * y2) / (8.0 * s.tc);
+  k.f = fsrc * (1.0 + d1);
+  k.fdot = fdsrc * (1.0 + d1) * (1.0 + d1) + fsrc * d2;
+  k.amp = r_pow(y3 * onec, 2.0 / 3.0);
+  const R delta = (d0 - a0) + dm_dT;
+  const R ua = 1.0 - tpa / s.tc;
+  const R l = r_log1p((-delta) / (s.tc - tpa));
+  k.dphi = s.P5 * r_pow(ua, 0.625) * (-r_expm1(0.625 * l)) +
+           s.P3 * r_pow(ua, 0.375) * (-r_expm1(0.375 * l));
+  if (resp) {
+    R fpA = zero, fxA = zero, fpE = zero, fxE = zero;
+    for (int q = 0; q < 6; ++q) {
+      fpA = fpA + s.pp[q] * tr.DA[q];
+      fxA = fxA + s.px[q] * tr.DA[q];
+      fpE = fpE + s.pp[q] * tr.DE[q];
+      fxE = fxE + s.px[q] * tr.DE[q];
+    }
+    k.Tr[0] = fpA;
+    k.Ti[0] = -fxA;
+    k.Tr[1] = fpE;
+    k.Ti[1] = -fxE;
+  } else {
+    k.Tr[0] = k.Tr[1] = zero + 1.0;
+    k.Ti[0] = k.Ti[1] = zero;
+  }
+  return k;
+}
+
+}  // namespace tfs

@@ -1,7 +1,10 @@
 """CUDA paths against the FP64 oracle, element by element on the same seeded inputs.
 
 Tolerances (relative error of Upsilon per template and level):
-  FP64 path          1e-10
+  FP64 path          max(1e-10, 2 eps64 Phi_seg): Upsilon's sensitivity to a relative
+                     error in the phase constants is about Phi_seg, the largest phase a
+                     template advances inside one segment (2 pi f_max T_seg rad), so FP64
+                     agreement with the extended-precision oracle is floored there
   plain FP32 path    1e-4
   mixed, FP32 pixels 1e-4
   mixed, FP16 pixels max 1.5e-3, p99 1e-3   (3x and 2x the FP16 unit roundoff 2^-11)
@@ -23,6 +26,14 @@ TOL = {("fp64", "f16"): (1e-10, 1e-10), ("plain", "f16"): (1e-4, 1e-4),
        ("mixed", "f32"): (1e-4, 1e-4), ("mixed", "f16"): (1.5e-3, 1e-3),
        ("mixed", "bf16"): (1.2e-2, 8e-3)}
 CASES = list(TOL)
+EPS64 = 2.0 ** -53
+
+
+def fp64_tol(D, n_seg):
+    """1e-10, or the FP64 conditioning floor 2 eps64 Phi_seg for long segments."""
+    f_max = D.n_bins / D.dT
+    phi_seg = 2 * np.pi * f_max * (D.n_tranche // int(np.min(n_seg))) * D.dT
+    return max(1e-10, 2 * EPS64 * phi_seg)
 
 
 def rel_err(got, ref):
@@ -66,7 +77,8 @@ def test_week_one_channel(week, path, pixel):
     c = ctx_for(week, path, pixel)
     got, neff, diag = c.eval_statistic(th, 8, diag=True)
     mx, p99 = rel_err(got, ref)
-    assert mx < TOL[(path, pixel)][0] and p99 < TOL[(path, pixel)][1], (mx, p99)
+    tol = fp64_tol(week, 8) if path == "fp64" else TOL[(path, pixel)][0]
+    assert mx < tol and p99 < max(tol, TOL[(path, pixel)][1]), (mx, p99)
     assert np.array_equal(neff, rneff)
     assert np.array_equal(diag[0], rnact) and np.array_equal(diag[1], rnnc)
 
@@ -80,7 +92,8 @@ def test_two_channel_response_gaps_levels(ae45, ae45_bank, path, pixel):
     got, neff, diag = c.eval_statistic(ae45_bank, lev, diag=True)
     for i, (ref, rneff, rnact, _) in enumerate(refs):
         mx, p99 = rel_err(got[i], ref)
-        assert mx < TOL[(path, pixel)][0] and p99 < TOL[(path, pixel)][1], (lev[i], mx, p99)
+        tol = fp64_tol(ae45, lev[i]) if path == "fp64" else TOL[(path, pixel)][0]
+        assert mx < tol and p99 < max(tol, TOL[(path, pixel)][1]), (lev[i], mx, p99)
         assert np.array_equal(neff[i], rneff)
     # the double-float track decides the window like the FP64 oracle
     assert np.abs(diag[0] - refs[0][2]).max() <= (0 if path != "mixed" else 1)
@@ -93,8 +106,8 @@ def test_per_template_segment_counts(ae45, ae45_bank, path):
     ns = choices[np.arange(th.shape[1]) % 4]
     c = ctx_for(ae45, path, "f32")
     got, neff, _ = c.eval_statistic(th, ns, per_template=True)
-    tol = {"fp64": 1e-10, "plain": 1e-4, "mixed": 1e-4}[path]
     for L in choices:
+        tol = {"fp64": fp64_tol(ae45, L), "plain": 1e-4, "mixed": 1e-4}[path]
         sel = ns == L
         ref, rneff, _, _ = oracle.statistic(ae45.d, ae45.w, ae45.mask, th[:, sel], int(L), ae45.dT,
                                             pn_order=1, response=1)
@@ -229,9 +242,10 @@ def test_two_year_full_bank_sampled(two_year):
         assert mx < TOL[("mixed", "f16")][0], (L, mx)
         assert np.array_equal(ne[i, idx], rneff)
     # FP64 and plain paths on the sampled templates
-    for path, tol in (("fp64", 1e-10), ("plain", 1e-4)):
+    for path in ("fp64", "plain"):
         c2 = ctx_for(D, path, "f16")
         got, _, _ = c2.eval_statistic(th[:, idx], lev)
         for i, L in enumerate(lev):
+            tol = fp64_tol(D, L) if path == "fp64" else 1e-4
             ref = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT, pn_order=1, response=1)[0]
             assert rel_err(got[i], ref)[0] < tol, (path, L)
