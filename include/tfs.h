@@ -149,6 +149,25 @@ int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t
 int tfs_select_top(tfs_ctx* ctx, const double* stat, int64_t n, int64_t k, int64_t* out_index,
                    void* stream);
 
+/* Same selection as tfs_select_top, for callers that cannot allocate device memory:
+ * code between the launches of a pipeline that must not synchronise the device
+ * (cudaMalloc/cudaFree synchronise it), or a framework that owns all device memory
+ * through its own pool under a fixed budget. This function has no counterpart in the
+ * paper; it is a deployment variant. It calls no allocator and needs no context: the
+ * radix-sort scratch is a static device array of about 1.6 MB (room for
+ * n <= 65536 values) that every GPU loading this library keeps until the process
+ * exits.
+ *   stat: double [n] and out_index: int64 [k], both device pointers of the current
+ *   device; n > 65536, host pointers or k outside [0, n] return TFS_ERR_ARG; a CUDA
+ *   failure returns TFS_ERR_CUDA (no message: there is no context).
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture. Every
+ * call reuses the same array and overwrites every byte it reads, so nothing carries
+ * over from the previous call, but calls whose GPU work overlaps (two streams, or two
+ * host threads on one device) race on it: serialise them. Asynchronous on `stream`. */
+int tfs_select_top_noalloc(const double* stat, int64_t n, int64_t k, int64_t* out_index,
+                           void* stream);
+
 /* One projected gradient-ascent step on a batch of templates, in place:
  *   theta[p][i] += step[p] * grad[p][i], then clamped to [lo[p], hi[p]];
  *   phi_0, lambda, psi are wrapped to [0, 2 pi) / [0, pi) instead of clamped.

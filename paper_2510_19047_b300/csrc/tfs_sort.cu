@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tfs_sort.cuh"
 
@@ -207,3 +208,68 @@ cudaError_t select_top(const double* stat, int64_t n, int64_t k, int64_t* out_id
 }
 
 }  // namespace tfs
+
+// ---------------------------------------------------------------------------------
+// Top-k selection that allocates nothing, for callers that cannot call cudaMalloc:
+// code running between the launches of a pipeline that must not synchronise the
+// device (cudaMalloc and cudaFree synchronise), or inside a framework whose memory
+// is owned by its own pool under a fixed budget. The radix-sort scratch lives in a
+// file-scope device array that every GPU loading this library keeps until exit.
+// ---------------------------------------------------------------------------------
+namespace tfs {
+namespace {
+
+constexpr int64_t kStaticTopMax = 1 << 16;  // largest n the static scratch holds
+constexpr size_t kStaticTopBytes =
+    (size_t)kStaticTopMax * (8 + 8 + 4 + 4) +
+    (size_t)kDigits * ((kStaticTopMax + kTile - 1) / kTile) * 4 + 256;
+
+static __device__ __align__(256) unsigned char g_top_scratch[kStaticTopBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_top_mutex;
+void* g_top_ptr[kMaxDevices] = {};
+
+// Device address of g_top_scratch on the current device (looked up once per device).
+cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_top_mutex);
+  if (!g_top_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_top_scratch);
+    if (e != cudaSuccess) return e;
+    g_top_ptr[dev] = p;
+  }
+  *out = g_top_ptr[dev];
+  return cudaSuccess;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace tfs
+
+extern "C" int tfs_select_top_noalloc(const double* stat, int64_t n, int64_t k,
+                                      int64_t* out_index, void* stream) {
+  using namespace tfs;
+  if (n < 0 || k < 0 || k > n) return TFS_ERR_ARG;
+  if (n > kStaticTopMax) return TFS_ERR_ARG;  // beyond the static scratch
+  if (k == 0) return TFS_OK;
+  if (!stat || !out_index || !on_device(stat) || !on_device(out_index)) return TFS_ERR_ARG;
+  void* scratch = nullptr;
+  if (static_scratch(&scratch) != cudaSuccess) return TFS_ERR_CUDA;
+  int launches = 0;
+  if (select_top(stat, n, k, out_index, scratch, (cudaStream_t)stream, &launches) != cudaSuccess)
+    return TFS_ERR_CUDA;
+  return TFS_OK;
+}
