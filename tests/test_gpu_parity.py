@@ -1,9 +1,10 @@
 """CUDA paths against the FP64 oracle, element by element on the same seeded inputs.
 
 Tolerances (relative error of Upsilon per template and level):
-  FP64 path          max(1e-10, 2 eps64 Phi_seg): Upsilon's sensitivity to a relative
+  FP64 path          max(1e-10, 4 eps64 Phi_seg): Upsilon's sensitivity to a relative
                      error in the phase constants is about Phi_seg, the largest phase a
-                     template advances inside one segment (2 pi f_max T_seg rad), so FP64
+                     template advances inside one segment (2 pi f_max T_seg rad); the
+                     FP64 constants t_c, F0, P5, P3 each carry ~eps64 of rounding, so FP64
                      agreement with the extended-precision oracle is floored there
   plain FP32 path    1e-4
   mixed, FP32 pixels 1e-4
@@ -30,10 +31,10 @@ EPS64 = 2.0 ** -53
 
 
 def fp64_tol(D, n_seg):
-    """1e-10, or the FP64 conditioning floor 2 eps64 Phi_seg for long segments."""
+    """1e-10, or the FP64 conditioning floor 4 eps64 Phi_seg for long segments."""
     f_max = D.n_bins / D.dT
     phi_seg = 2 * np.pi * f_max * (D.n_tranche // int(np.min(n_seg))) * D.dT
-    return max(1e-10, 2 * EPS64 * phi_seg)
+    return max(1e-10, 4 * EPS64 * phi_seg)
 
 
 def rel_err(got, ref):
