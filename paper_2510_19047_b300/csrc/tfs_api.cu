@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <numeric>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -47,12 +49,18 @@ struct tfs_ctx {
   int pix_built = -1;
   double su = 1.0, sw = 1.0;
   // per-call scratch
-  DevBuf theta, tpl, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
+  DevBuf theta, tpl, tplm, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
   // profiling
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double prof[4] = {0, 0, 0, 0};
   bool prof_valid = false;
   int mixed_warps = 0;
+  // autotuned mixed launch shapes: (n_chan, pixel, fine_cap, per_template) -> (warps, ctas)
+  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tuned;
+  // CUDA graph of the mixed evaluation, replayed while its key is unchanged
+  cudaStream_t cstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<long long> gkey;
 };
 
 namespace {
@@ -175,6 +183,84 @@ void prof_record(tfs_ctx* c, int i, cudaStream_t s) {
   if (c->opt.profile) cudaEventRecord(c->ev[i], s);
 }
 
+
+// The launches of one mixed evaluation after the per-template set-up: optional
+// length/frequency sort, counter reset, persistent statistic kernel.
+int issue_mixed(tfs_ctx* c, EvalArgs& a, int64_t n_tpl, int warps, int ctas, cudaStream_t s) {
+  if (c->opt.sort) {
+    int nl = 0;
+    CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
+                               c->n_sm, s, &nl));
+    c->launches += nl;
+    a.perm = (const int32_t*)c->perm.p;
+  } else {
+    a.perm = nullptr;
+  }
+  prof_record(c, 2, s);
+  CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
+  CUDA_TRY(c, launch_eval_mixed(a, c->g.n_chan, c->opt.pixel, warps, ctas, s));
+  c->launches += 1;
+  return TFS_OK;
+}
+
+// Launch shape of the mixed kernel: the options' warps per CTA if set, otherwise the
+// fastest of {4, 8} warps x {full, full - 1} CTAs per SM, timed once per
+// (channels, pixel type, segment slots, per-template mode) on up to 24576 templates of
+// the current (already sorted) queue.
+int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_template,
+                cudaStream_t s, int* warps_out, int* ctas_out) {
+  const int n_chan = c->g.n_chan, pix = c->opt.pixel;
+  auto shape_for = [&](int warps, int per_sm, int* ctas) {
+    const int64_t need = (n_tpl + warps - 1) / warps;
+    *ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->n_sm * per_sm, need));
+  };
+  if (c->opt.warps_per_cta) {
+    int per_sm = 0;
+    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->opt.warps_per_cta, fine_cap, &per_sm));
+    if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
+    *warps_out = c->opt.warps_per_cta;
+    shape_for(*warps_out, per_sm, ctas_out);
+    return TFS_OK;
+  }
+  const auto key = std::make_tuple(n_chan, pix, fine_cap, per_template);
+  auto it = c->tuned.find(key);
+  if (it == c->tuned.end()) {
+    a.n_work = std::min<int64_t>(n_tpl, 24576);
+    float best = 1e30f;
+    std::pair<int, int> pick{8, 1};
+    cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
+    for (int warps : {4, 8}) {
+      int occ = 0;
+      CUDA_TRY(c, mixed_occupancy(n_chan, pix, warps, fine_cap, &occ));
+      for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
+        int ctas;
+        shape_for(warps, per_sm, &ctas);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
+          CUDA_TRY(c, cudaEventRecord(e0, s));
+          CUDA_TRY(c, launch_eval_mixed(a, n_chan, pix, warps, ctas, s));
+          CUDA_TRY(c, cudaEventRecord(e1, s));
+          CUDA_TRY(c, cudaEventSynchronize(e1));
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
+        }
+        if (ms < best) {
+          best = ms;
+          pick = {warps, per_sm};
+        }
+      }
+    }
+    it = c->tuned.emplace(key, pick).first;
+  }
+  int occ = 0;
+  CUDA_TRY(c, mixed_occupancy(n_chan, pix, it->second.first, fine_cap, &occ));
+  *warps_out = it->second.first;
+  shape_for(*warps_out, std::min(occ, it->second.second), ctas_out);
+  return TFS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -236,6 +322,7 @@ int tfs_create(tfs_ctx** out, int device, const tfs_options* opt) {
   }
   c->device = device;
   for (int i = 0; i < 5; ++i) cudaEventCreate(&c->ev[i]);
+  cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking);
   *out = c;
   return TFS_OK;
 }
@@ -244,12 +331,14 @@ int tfs_destroy(tfs_ctx* c) {
   if (!c) return TFS_OK;
   cudaSetDevice(c->device);
   DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
-                   &c->w64, &c->u32, &c->w32, &c->Umix, &c->Wmix, &c->theta, &c->tpl,
+                   &c->w64, &c->u32, &c->w32, &c->Umix, &c->Wmix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
                    &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ};
   for (DevBuf* b : all) buf_free(c, *b);
   for (int i = 0; i < 5; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cstream) cudaStreamDestroy(c->cstream);
   delete c;
   return TFS_OK;
 }
@@ -422,14 +511,25 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   c->launches = 0;
   c->prof_valid = false;
   if (n_tpl == 0) return TFS_OK;
-  // inputs
+  const bool graph = path == TFS_PATH_MIXED && c->opt.use_graph;
+  // inputs: device theta is read in place, host theta is copied; a graph always reads
+  // the context's own copy so that its pointers stay fixed between replays
   const void* th = nullptr;
-  if ((r = device_view(c, theta, (size_t)n_tpl * 8 * 8, c->theta, s, &th))) return r;
+  if (graph) {
+    if ((r = buf_ensure(c, c->theta, (size_t)n_tpl * 64))) return r;
+    CUDA_TRY(c, cudaMemcpyAsync(c->theta.p, theta, (size_t)n_tpl * 64,
+                                is_device_ptr(theta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                s));
+    th = c->theta.p;
+  } else if ((r = device_view(c, theta, (size_t)n_tpl * 8 * 8, c->theta, s, &th))) {
+    return r;
+  }
   if ((r = buf_ensure(c, c->tpl, (size_t)n_tpl * sizeof(TplConst)))) return r;
-  // outputs: device pointers are written directly, host ones through scratch
-  const bool dev_stat = is_device_ptr(out_stat);
-  const bool dev_neff = !out_neff || is_device_ptr(out_neff);
-  const bool dev_diag = !out_diag || is_device_ptr(out_diag);
+  // outputs: device pointers are written directly, host ones (and graph replays) go
+  // through the context's scratch
+  const bool dev_stat = !graph && is_device_ptr(out_stat);
+  const bool dev_neff = !graph && (!out_neff || is_device_ptr(out_neff));
+  const bool dev_diag = !graph && (!out_diag || is_device_ptr(out_diag));
   double* o_stat = out_stat;
   int32_t* o_neff = out_neff;
   int32_t* o_diag = out_diag;
@@ -446,11 +546,15 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     o_diag = (int32_t*)c->diag.p;
   }
   if ((r = buf_ensure(c, c->counter, 64))) return r;
-
-  prof_record(c, 0, s);
-  CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, g, (TplConst*)c->tpl.p, s));
-  c->launches++;
-  prof_record(c, 1, s);
+  TplMix* mix = nullptr;
+  if (path == TFS_PATH_MIXED) {
+    if ((r = buf_ensure(c, c->tplm, (size_t)n_tpl * sizeof(TplMix)))) return r;
+    mix = (TplMix*)c->tplm.p;
+    if (c->pix_built != c->opt.pixel && (r = pack_mixed(c, s))) return r;
+    if (c->opt.sort && ((r = buf_ensure(c, c->perm, (size_t)n_tpl * 4)) ||
+                        (r = buf_ensure(c, c->sortbuf, sort_scratch_bytes(n_tpl)))))
+      return r;
+  }
 
   EvalArgs a{};
   a.g = g;
@@ -466,8 +570,10 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.Wmix = c->Wmix.p;
   a.mask = (const uint8_t*)c->mask.p;
   a.tpl = (const TplConst*)c->tpl.p;
+  a.tplm = mix;
   a.perm = nullptr;
   a.n_tpl = n_tpl;
+  a.n_work = n_tpl;
   a.lv = lv;
   a.nseg_pt = nseg_dev;
   a.fine_cap = fine_cap;
@@ -477,53 +583,101 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.counter = (int*)c->counter.p;
   a.dev_err = (int*)c->counter.p + 8;
   a.checked = c->opt.checked;
-  const double scale32 = 4.0 * g.df * c->sw / (c->su * c->su);
+  a.out_scale = path == TFS_PATH_FP64 ? 4.0 * g.df : 4.0 * g.df * c->sw / (c->su * c->su);
+
+  auto setup = [&](cudaStream_t st) -> int {
+    prof_record(c, 0, st);
+    CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, g, (TplConst*)c->tpl.p, mix, st));
+    c->launches++;
+    prof_record(c, 1, st);
+    return TFS_OK;
+  };
+
+  if (c->opt.checked) {
+    // range check of the per-template constants before any kernel reads pixels
+    if ((r = setup(s))) return r;
+    CUDA_TRY(c, cudaMemsetAsync(a.dev_err, 0, 4, s));
+    CUDA_TRY(c, launch_check_tpl((const TplConst*)c->tpl.p, n_tpl, g.n_tranche, a.dev_err, s));
+    int herr = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&herr, a.dev_err, 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (herr) return fail(c, TFS_ERR_DEVICE_CHECK, "a template's tranche range lies outside the grid");
+  }
 
   if (path == TFS_PATH_MIXED) {
-    if (c->pix_built != c->opt.pixel && (r = pack_mixed(c, s))) return r;
-    if (c->opt.sort) {
-      if ((r = buf_ensure(c, c->perm, (size_t)n_tpl * 4)) ||
-          (r = buf_ensure(c, c->sortbuf, sort_scratch_bytes(n_tpl))))
-        return r;
+    if (!c->opt.checked && (r = setup(s))) return r;
+    int warps = 8, ctas = 1;
+    const bool must_time = !c->opt.warps_per_cta &&
+                           !c->tuned.count(std::make_tuple(g.n_chan, c->opt.pixel, fine_cap, per_template));
+    if (c->opt.sort && must_time) {
+      // the autotuner times the sorted queue, so sort once before choosing
+      EvalArgs t = a;
       int nl = 0;
-      CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p,
-                                 c->sortbuf.p, c->n_sm, s, &nl));
-      c->launches += nl;
-      a.perm = (const int32_t*)c->perm.p;
+      CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
+                                 c->n_sm, s, &nl));
+      t.perm = (const int32_t*)c->perm.p;
+      if ((r = mixed_shape(c, t, n_tpl, fine_cap, per_template, s, &warps, &ctas))) return r;
+    } else if ((r = mixed_shape(c, a, n_tpl, fine_cap, per_template, s, &warps, &ctas))) {
+      return r;
     }
-    prof_record(c, 2, s);
-    const int warps = c->opt.warps_per_cta ? c->opt.warps_per_cta : 8;
-    int per_sm = 0;
-    CUDA_TRY(c, mixed_occupancy(g.n_chan, c->opt.pixel, warps, fine_cap, &per_sm));
-    if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
-    const int64_t need_ctas = (n_tpl + warps - 1) / warps;
-    const int ctas = (int)std::min<int64_t>((int64_t)c->n_sm * per_sm, need_ctas);
-    CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
-    a.out_scale = scale32;
-    CUDA_TRY(c, launch_eval_mixed(a, g.n_chan, c->opt.pixel, warps, ctas, s));
-    c->launches += 1;
-  } else if (path == TFS_PATH_PLAIN) {
-    prof_record(c, 2, s);
-    a.out_scale = scale32;
-    CUDA_TRY(c, launch_eval_plain(a, s));
-    c->launches += 1;
+    c->launches = 0;
+    if (!graph) {
+      c->launches = 1;  // set-up
+      if ((r = issue_mixed(c, a, n_tpl, warps, ctas, s))) return r;
+    } else {
+      std::vector<long long> key = {n_tpl, n_levels, per_template, fine_cap, warps, ctas,
+                                    c->opt.pixel, c->opt.sort, c->opt.profile, c->opt.pn_order,
+                                    c->opt.response, (long long)th, (long long)o_stat,
+                                    (long long)o_neff, (long long)o_diag, (long long)c->tpl.p,
+                                    (long long)c->tplm.p, (long long)c->perm.p,
+                                    (long long)c->sortbuf.p, (long long)c->Umix.p,
+                                    (long long)c->nseg.p, lv.seg_len[0], lv.seg_len[1],
+                                    lv.seg_len[2], lv.seg_len[3]};
+      if (!c->gexec || key != c->gkey) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+        cudaGraph_t gr = nullptr;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->cstream, cudaStreamCaptureModeThreadLocal));
+        int rr = setup(c->cstream);
+        if (!rr) rr = issue_mixed(c, a, n_tpl, warps, ctas, c->cstream);
+        prof_record(c, 3, c->cstream);
+        const cudaError_t ce = cudaStreamEndCapture(c->cstream, &gr);
+        if (rr) {
+          if (gr) cudaGraphDestroy(gr);
+          return rr;
+        }
+        CUDA_TRY(c, ce);
+        const cudaError_t ie = cudaGraphInstantiate(&c->gexec, gr, 0);
+        cudaGraphDestroy(gr);
+        CUDA_TRY(c, ie);
+        c->gkey = key;
+      }
+      // the replay follows the work already queued on the caller's stream
+      CUDA_TRY(c, cudaGraphLaunch(c->gexec, s));
+      c->launches = 1 + (c->opt.sort ? 1 + 4 * 3 : 0) + 1;
+    }
   } else {
+    if (!c->opt.checked && (r = setup(s))) return r;
     prof_record(c, 2, s);
-    a.out_scale = 4.0 * g.df;
-    CUDA_TRY(c, launch_eval_fp64(a, s));
+    CUDA_TRY(c, path == TFS_PATH_PLAIN ? launch_eval_plain(a, s) : launch_eval_fp64(a, s));
     c->launches += 1;
   }
-  prof_record(c, 3, s);
+  if (!graph) prof_record(c, 3, s);
   if (!dev_stat)
     CUDA_TRY(c, cudaMemcpyAsync(out_stat, o_stat, (size_t)n_levels * n_tpl * 8,
-                                cudaMemcpyDeviceToHost, s));
-  if (!dev_neff)
+                                is_device_ptr(out_stat) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!dev_neff && out_neff)
     CUDA_TRY(c, cudaMemcpyAsync(out_neff, o_neff, (size_t)n_levels * n_tpl * 4,
-                                cudaMemcpyDeviceToHost, s));
-  if (!dev_diag)
-    CUDA_TRY(c, cudaMemcpyAsync(out_diag, o_diag, (size_t)2 * n_tpl * 4, cudaMemcpyDeviceToHost, s));
+                                is_device_ptr(out_neff) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!dev_diag && out_diag)
+    CUDA_TRY(c, cudaMemcpyAsync(out_diag, o_diag, (size_t)2 * n_tpl * 4,
+                                is_device_ptr(out_diag) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   prof_record(c, 4, s);
-  if (!dev_stat || !dev_neff || !dev_diag || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
+  const bool host_out = !is_device_ptr(out_stat) || (out_neff && !is_device_ptr(out_neff)) ||
+                        (out_diag && !is_device_ptr(out_diag));
+  if (host_out || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
   if (c->opt.profile) {
     float ms;
     for (int i = 0; i < 4; ++i) {
@@ -655,7 +809,8 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   }
   c->launches = 0;
   prof_record(c, 0, s);
-  CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, c->g, (TplConst*)c->tpl.p, s));
+  CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, c->g, (TplConst*)c->tpl.p,
+                           nullptr, s));
   prof_record(c, 1, s);
   prof_record(c, 2, s);
   const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);

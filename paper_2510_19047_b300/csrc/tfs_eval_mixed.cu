@@ -32,24 +32,19 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Pixel loads: ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E).
 template <int PIX>
 struct PixLoad;
 template <>
 struct PixLoad<TFS_PIX_F32> {
   using U = float4;
   using W = float2;
-  __device__ static void u(const U* p, float& a, float& b, float& c, float& d) {
+  __device__ static void u(const U* p, float2& ur, float2& ui) {
     const float4 v = __ldg(p);
-    a = v.x;
-    b = v.y;
-    c = v.z;
-    d = v.w;
+    ur = make_float2(v.x, v.y);
+    ui = make_float2(v.z, v.w);
   }
-  __device__ static void w(const W* p, float& a, float& b) {
-    const float2 v = __ldg(p);
-    a = v.x;
-    b = v.y;
-  }
+  __device__ static float2 w(const W* p) { return __ldg(p); }
 };
 template <>
 struct PixLoad<TFS_PIX_F16> {
@@ -59,19 +54,12 @@ struct PixLoad<TFS_PIX_F16> {
     __half2 h = *reinterpret_cast<__half2*>(&x);
     return __half22float2(h);
   }
-  __device__ static void u(const U* p, float& a, float& b, float& c, float& d) {
+  __device__ static void u(const U* p, float2& ur, float2& ui) {
     const uint2 v = __ldg(p);
-    const float2 x = cv(v.x), y = cv(v.y);
-    a = x.x;
-    b = x.y;
-    c = y.x;
-    d = y.y;
+    ur = cv(v.x);
+    ui = cv(v.y);
   }
-  __device__ static void w(const W* p, float& a, float& b) {
-    const float2 x = cv(__ldg(p));
-    a = x.x;
-    b = x.y;
-  }
+  __device__ static float2 w(const W* p) { return cv(__ldg(p)); }
 };
 template <>
 struct PixLoad<TFS_PIX_BF16> {
@@ -81,19 +69,12 @@ struct PixLoad<TFS_PIX_BF16> {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&x);
     return __bfloat1622float2(h);
   }
-  __device__ static void u(const U* p, float& a, float& b, float& c, float& d) {
+  __device__ static void u(const U* p, float2& ur, float2& ui) {
     const uint2 v = __ldg(p);
-    const float2 x = cv(v.x), y = cv(v.y);
-    a = x.x;
-    b = x.y;
-    c = y.x;
-    d = y.y;
+    ur = cv(v.x);
+    ui = cv(v.y);
   }
-  __device__ static void w(const W* p, float& a, float& b) {
-    const float2 x = cv(__ldg(p));
-    a = x.x;
-    b = x.y;
-  }
+  __device__ static float2 w(const W* p) { return cv(__ldg(p)); }
 };
 
 __device__ __forceinline__ df two_prod(float a, float b) {
@@ -114,15 +95,18 @@ __device__ __forceinline__ void fg_fast(float a, float& f, float& g) {
   }
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-
 }  // namespace
 
+#ifndef TFS_MIXED_UNROLL
+#define TFS_MIXED_UNROLL 3
+#endif
+#ifndef TFS_MIXED_MINB
+#define TFS_MIXED_MINB 4
+#endif
+constexpr int kBinUnroll = TFS_MIXED_UNROLL;
+
 template <int NCH, int PIX>
-__global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
+__global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
   const int lane = threadIdx.x & 31;
@@ -142,9 +126,9 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
     int t = 0;
     if (lane == 0) t = atomicAdd(a.counter, 1);
     t = __shfl_sync(kFull, t, 0);
-    if (t >= a.n_tpl) break;
+    if (t >= a.n_work) break;
     const int idx = a.perm ? a.perm[t] : t;
-    const TplConst c = a.tpl[idx];
+    const TplMix c = a.tplm[idx];
 
     int nl, fine_len;
     int seg_len[kMaxLevels];
@@ -161,21 +145,14 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
     const int n_fine = g.n_tranche / fine_len;
     for (int q = lane; q < n_fine; q += 32) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    const df tc_inv = df_make(1.0 / c.tc);
-    const df F0 = df_make(c.F0);
-    const float C2 = (float)c.C2;
-    const float fd_k = (float)(c.F0 / (8.0 * c.tc));  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
-    const df P5 = df_make(c.P5 * (0.5 / kPi));        // phase coefficients in cycles
-    const df P3 = df_make(c.P3 * (0.5 / kPi));
-    const double ph0c = c.phi0 * (0.5 / kPi);
-    const df ph0 = df_make(ph0c - floor(ph0c));
-    const df dopc = df_make(c.dop_c), dops = df_make(c.dop_s);
-    float pp[6], px[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      pp[q] = (float)c.pp[q];
-      px[q] = (float)c.px[q];
-    }
+    const df tc_inv = {c.tcinv_hi, c.tcinv_lo};
+    const df F0 = {c.F0_hi, c.F0_lo};
+    const float C2 = c.C2;
+    const float fd_k = c.fd_k;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
+    const df P5 = {c.P5_hi, c.P5_lo};  // phase coefficients in cycles
+    const df P3 = {c.P3_hi, c.P3_lo};
+    const df ph0 = {c.ph0_hi, c.ph0_lo};
+    const df dopc = {c.dopc_hi, c.dopc_lo}, dops = {c.dops_hi, c.dops_lo};
     int nact = 0, nnc = 0;
     __syncwarp();
 
@@ -235,8 +212,9 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
             const df ph = df_add(ph0, df_add(df_mul(P5, df_sub(one, u58)),
                                              df_mul(P3, df_sub(one, u38))));
             const float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
+            // cyc is in [-1/2, 1/2]: the hardware sine/cosine are accurate to ~4e-7 there
             float sph, cph;
-            sincospif(2.0f * cyc, &sph, &cph);
+            __sincosf(6.283185307f * cyc, &sph, &cph);
             // amplitude (f/F0)^(2/3) = y^2 (1 + C2 y^2)^(2/3), series to O(e^4)
             const float amp =
                 y2f * fmaf(c2y2, fmaf(c2y2, fmaf(c2y2, 4.0f / 81.0f, -1.0f / 9.0f), 2.0f / 3.0f),
@@ -245,15 +223,16 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
             amp_s = amp * sph;
             sig = sig_k * rsqrtf(fdot);
             eps = fdot * dTf * dTf;  // fdot dT / df: sweep width in bins
-            sincospif(fmaf(2.0f, aa, eps), &spsi, &cpsi);
+            const float psi = fmaf(2.0f, aa, eps);  // Psi / pi, reduced to [-1, 1]
+            __sincosf(3.141592654f * (psi - 2.0f * rintf(0.5f * psi)), &spsi, &cpsi);
             if (a.response) {
               float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
 #pragma unroll
               for (int q = 0; q < 6; ++q) {
-                fpA = fmaf(tr.DA[q], pp[q], fpA);
-                fxA = fmaf(tr.DA[q], px[q], fxA);
-                fpE = fmaf(tr.DE[q], pp[q], fpE);
-                fxE = fmaf(tr.DE[q], px[q], fxE);
+                fpA = fmaf(tr.DA[q], c.pp[q], fpA);
+                fxA = fmaf(tr.DA[q], c.px[q], fxA);
+                fpE = fmaf(tr.DE[q], c.pp[q], fpE);
+                fxE = fmaf(tr.DE[q], c.px[q], fxE);
               }
               Tr0 = fpA;
               Ti0 = -fxA;
@@ -275,11 +254,22 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
       if (act) {
         const typename Ld::U* Up = U + (int64_t)(kc - kNFHalf) * pitch + m;
         const typename Ld::W* Wp = W + (int64_t)(kc - kNFHalf) * pitch + m;
-        float zr0 = 0.f, zi0 = 0.f, n0 = 0.f, zr1 = 0.f, zi1 = 0.f, n1 = 0.f;
+        float2 zr = make_float2(0.f, 0.f), zi = zr, nn = zr;  // (channel A, channel E)
         const float spi = sig * (float)kPi;
-#pragma unroll
+        // pixel loads run one bin ahead of the arithmetic
+        float2 cur_r, cur_i, cur_w;
+        Ld::u(Up, cur_r, cur_i);
+        cur_w = Ld::w(Wp);
+#pragma unroll kBinUnroll
         for (int j = 0; j < kNF; ++j) {
+          float2 nxt_r, nxt_i, nxt_w;
+          if (j + 1 < kNF) {
+            Ld::u(Up + (int64_t)(j + 1) * pitch, nxt_r, nxt_i);
+            nxt_w = Ld::w(Wp + (int64_t)(j + 1) * pitch);
+          }
           const int jp = j - kNFHalf;
+          // x1 = (f_nm - f_k)/df, formed directly from aa: aa + 10 - j would round aa
+          // to ulp(10) and ruin 1/x1 for the bins next to f_nm
           const float x1 = aa - (float)jp;
           const float x2 = x1 + eps;
           float wr, wi;
@@ -305,18 +295,19 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
             wi = fmaf(-cpsi, q2, q1);
           }
           const float ww = fmaf(wr, wr, wi * wi);
-          float ur0, ui0, ur1, ui1, w0, w1;
-          Ld::u(Up + (int64_t)j * pitch, ur0, ui0, ur1, ui1);
-          Ld::w(Wp + (int64_t)j * pitch, w0, w1);
-          zr0 = fmaf(ur0, wr, fmaf(ui0, wi, zr0));
-          zi0 = fmaf(ur0, wi, fmaf(-ui0, wr, zi0));
-          n0 = fmaf(w0, ww, n0);
-          if (NCH == 2) {
-            zr1 = fmaf(ur1, wr, fmaf(ui1, wi, zr1));
-            zi1 = fmaf(ur1, wi, fmaf(-ui1, wr, zi1));
-            n1 = fmaf(w1, ww, n1);
+          const float2 wr2 = make_float2(wr, wr), wi2 = make_float2(wi, wi);
+          const float2 nwr2 = make_float2(-wr, -wr), ww2 = make_float2(ww, ww);
+          // conj(u) W for both channels at once
+          zr = __ffma2_rn(cur_r, wr2, __ffma2_rn(cur_i, wi2, zr));
+          zi = __ffma2_rn(cur_r, wi2, __ffma2_rn(cur_i, nwr2, zi));
+          nn = __ffma2_rn(cur_w, ww2, nn);
+          if (j + 1 < kNF) {
+            cur_r = nxt_r;
+            cur_i = nxt_i;
+            cur_w = nxt_w;
           }
         }
+        const float zr0 = zr.x, zi0 = zi.x, n0 = nn.x, zr1 = zr.y, zi1 = zi.y, n1 = nn.y;
         float ar = Tr0 * zr0 - Ti0 * zi0, ai = Tr0 * zi0 + Ti0 * zr0;
         float nt = (Tr0 * Tr0 + Ti0 * Ti0) * n0;
         if (NCH == 2) {
@@ -356,7 +347,7 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
     for (int l = 0; l < nl; ++l) {
       const int r = seg_len[l] / fine_len;
       const int ns = g.n_tranche / seg_len[l];
-      double ups = 0.0;
+      float ups = 0.f;
       int ne = 0;
       for (int n = lane; n < ns; n += 32) {
         float zr = 0.f, zi = 0.f, nn = 0.f;
@@ -367,14 +358,14 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
           nn += v.z;
         }
         if (nn > 0.f) {
-          ups += ((double)zr * zr + (double)zi * zi) / (double)nn;
+          ups += __fdividef(fmaf(zr, zr, zi * zi), nn);
           ++ne;
         }
       }
-      ups = warp_sum_d(ups);
+      for (int o = 16; o > 0; o >>= 1) ups += __shfl_xor_sync(kFull, ups, o);
       ne = __reduce_add_sync(kFull, ne);
       if (lane == 0) {
-        a.out_stat[(int64_t)l * a.n_tpl + idx] = ups * a.out_scale;
+        a.out_stat[(int64_t)l * a.n_tpl + idx] = (double)ups * a.out_scale;
         if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + idx] = ne;
       }
     }
@@ -391,13 +382,12 @@ __global__ void __launch_bounds__(256) k_eval_mixed(EvalArgs a) {
 template <int NCH, int PIX>
 static cudaError_t launch_one(const EvalArgs& a, int warps, int ctas, cudaStream_t s) {
   const size_t smem = (size_t)warps * a.fine_cap * sizeof(float4);
-  auto kern = k_eval_mixed<NCH, PIX>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<ctas, warps * 32, smem, s>>>(a);
+  k_eval_mixed<NCH, PIX><<<ctas, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
+// Launch only (no attribute calls, so it can be captured into a CUDA graph);
+// mixed_occupancy() must have been called for the same shape first.
 cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
                               cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
@@ -411,6 +401,8 @@ cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps,
   return launch_one<2, TFS_PIX_BF16>(a, warps, ctas, s);
 }
 
+// Sets the dynamic shared-memory limit of the instantiation and returns how many CTAs
+// of this shape fit on one SM.
 template <int NCH, int PIX>
 static cudaError_t occ_one(int warps, int fine_cap, int* n) {
   const size_t smem = (size_t)warps * fine_cap * sizeof(float4);

@@ -64,6 +64,20 @@ struct __align__(16) TplConst {
   int kc_lo;            // window centre bin at m_lo
 };
 
+// The same constants split for the mixed path's double-float / FP32 arithmetic
+// (hi + lo pairs), so that kernel needs no FP64 instruction.
+struct __align__(16) TplMix {
+  float tcinv_hi, tcinv_lo;  // 1 / t_c
+  float F0_hi, F0_lo;
+  float P5_hi, P5_lo;        // P5 / 2 pi (cycles)
+  float P3_hi, P3_lo;        // P3 / 2 pi
+  float ph0_hi, ph0_lo;      // frac(phi0 / 2 pi)
+  float dopc_hi, dopc_lo, dops_hi, dops_lo;
+  float C2, fd_k;            // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
+  float pp[6], px[6];
+  int m_lo, m_hi;
+};
+
 // ---------------------------------------------------------------------------------
 // Paper's Fresnel auxiliary functions: C + iS = sgn(z) [(1+i)/2 - (g + i f) e^{i pi z^2/2}]
 // with f, g rational for |z| <= 6 and f = 1/(pi z), g = 0 for |z| > 6 (the printed

@@ -20,8 +20,10 @@ struct EvalArgs {
   const void* Wmix;
   const uint8_t* mask;          // [N_t]
   const TplConst* tpl;          // [n_tpl]
+  const TplMix* tplm;           // [n_tpl] (mixed path)
   const int32_t* perm;          // processing order (mixed path), may be null
   int64_t n_tpl;
+  int64_t n_work;               // queue entries the mixed launch processes (<= n_tpl)
   Levels lv;                    // global levels (per-template mode: lv.n == 0)
   const int32_t* nseg_pt;       // per-template N_seg or null
   int fine_cap;                 // smem fine-segment slots per warp (mixed path)
@@ -44,9 +46,11 @@ cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, c
 cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
                               const double* d_im, const double* w, double su, double sw, void* U,
                               void* W, int n_sm, cudaStream_t s);
+// mix may be null (only the mixed path reads it).
 cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
-                         TplConst* out, cudaStream_t s);
+                         TplConst* out, TplMix* mix, cudaStream_t s);
 
+cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int* err, cudaStream_t s);
 cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s);
 // Persistent mixed-precision launch; grid = ctas, block = 32 * warps.

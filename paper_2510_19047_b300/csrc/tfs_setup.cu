@@ -169,9 +169,11 @@ struct PixStore<TFS_PIX_BF16> {
   __device__ static W w(float a, float b) { return h2(a, b); }
 };
 
-// Mixed-path layout: frequency-major planes U[k][m] (both channels' u per pixel) and
-// W[k][m] (both channels' w), m padded to `pitch`, so that the 32 lanes of a warp,
-// which handle 32 consecutive tranches of one template, read consecutive words.
+// Mixed-path layout: frequency-major planes U[k][m] and W[k][m], m padded to `pitch`,
+// so that the 32 lanes of a warp, which handle 32 consecutive tranches of one template,
+// read consecutive words. Channels are paired inside each element,
+// U = (Re u_A, Re u_E, Im u_A, Im u_E) and W = (w_A, w_E), so that one conversion yields
+// both channels and one packed f32x2 operation updates both channels' sums.
 template <int PIX>
 __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const double* d_im,
                              const double* w, double su, double sw,
@@ -192,7 +194,7 @@ __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const do
         }
       }
     }
-    U[i] = PixStore<PIX>::u(v[0][0], v[0][1], v[1][0], v[1][1]);
+    U[i] = PixStore<PIX>::u(v[0][0], v[1][0], v[0][1], v[1][1]);
     W[i] = PixStore<PIX>::w(v[0][2], v[1][2]);
   }
 }
@@ -217,8 +219,34 @@ __device__ double time_at_frequency(double tc, double F0, double C2, double f_ta
   return tc * (1.0 - 1.0 / (y4 * y4));
 }
 
+__device__ __forceinline__ void split(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+__device__ TplMix mix_of(const TplConst& c) {
+  TplMix t;
+  split(1.0 / c.tc, t.tcinv_hi, t.tcinv_lo);
+  split(c.F0, t.F0_hi, t.F0_lo);
+  split(c.P5 * (0.5 / kPi), t.P5_hi, t.P5_lo);
+  split(c.P3 * (0.5 / kPi), t.P3_hi, t.P3_lo);
+  const double ph = c.phi0 * (0.5 / kPi);
+  split(ph - floor(ph), t.ph0_hi, t.ph0_lo);
+  split(c.dop_c, t.dopc_hi, t.dopc_lo);
+  split(c.dop_s, t.dops_hi, t.dops_lo);
+  t.C2 = (float)c.C2;
+  t.fd_k = (float)(c.F0 / (8.0 * c.tc));
+  for (int k = 0; k < 6; ++k) {
+    t.pp[k] = (float)c.pp[k];
+    t.px[k] = (float)c.px[k];
+  }
+  t.m_lo = c.m_lo;
+  t.m_hi = c.m_hi;
+  return t;
+}
+
 __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_order,
-                        GridDesc g, TplConst* __restrict__ out) {
+                        GridDesc g, TplConst* __restrict__ out, TplMix* __restrict__ mix) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double th[8];
@@ -234,6 +262,7 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
     c.F0 = 1.0;
     c.key = 0xffffffffu;
     out[i] = c;
+    if (mix) mix[i] = mix_of(c);
     return;
   }
   const SrcT<double> src = source_of<double>(th, pn_order);
@@ -278,6 +307,15 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
   c.kc_lo = kc_lo;
   c.key = ((uint32_t)(0xffff - min(blocks, 0xffff)) << 16) | (uint32_t)kc_lo;
   out[i] = c;
+  if (mix) mix[i] = mix_of(c);
+}
+
+// Checked mode: every template's tranche range must lie inside the grid.
+__global__ void k_check_tpl(const TplConst* __restrict__ tpl, int64_t n, int n_tranche, int* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const TplConst c = tpl[i];
+  if (c.m_lo < 0 || c.m_hi < c.m_lo || c.m_hi > n_tranche) atomicOr(err, kDevBadIndex);
 }
 
 // ---------------------------------------------------------------------------------
@@ -327,10 +365,16 @@ cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
-                         TplConst* out, cudaStream_t s) {
+cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int* err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, n, pn_order, g, out);
+  k_check_tpl<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tpl, n, n_tranche, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
+                         TplConst* out, TplMix* mix, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, n, pn_order, g, out, mix);
   return cudaGetLastError();
 }
 

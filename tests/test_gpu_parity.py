@@ -250,3 +250,26 @@ def test_two_year_full_bank_sampled(two_year):
             tol = fp64_tol(D, L) if path == "fp64" else 1e-4
             ref = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT, pn_order=1, response=1)[0]
             assert rel_err(got[i], ref)[0] < tol, (path, L)
+
+
+def test_graph_replay_checked_mode_and_launch_shapes(ae45, ae45_bank):
+    """CUDA-graph replay, checked mode and every launch shape give the direct path's
+    result bit for bit (templates are independent and the fold is deterministic)."""
+    import torch
+    lev = [64, 16, 4]
+    base = ctx_for(ae45, "mixed", "f16")
+    ref, rneff, _ = base.eval_statistic(ae45_bank, lev)
+    for kw in ({"use_graph": 1}, {"checked": 1}, {"warps_per_cta": 4}, {"warps_per_cta": 8},
+               {"sort": 0}):
+        c = ctx_for(ae45, "mixed", "f16", **kw)
+        for _ in range(2):  # second call replays the captured graph
+            got, neff, _ = c.eval_statistic(ae45_bank, lev)
+            assert np.array_equal(got, ref) and np.array_equal(neff, rneff), kw
+    # a graph re-captures when the batch shape changes, and works on device arrays
+    c = ctx_for(ae45, "mixed", "f16", use_graph=1)
+    sub = ae45_bank[:, :100]
+    got, _, _ = c.eval_statistic(torch.from_numpy(sub).cuda(), lev)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), ref[:, :100])
+    got, _, _ = c.eval_statistic(ae45_bank, lev)
+    assert np.array_equal(got, ref)
