@@ -36,14 +36,12 @@ import numpy as np  # noqa: E402
 METRIC = "templates/s of ρ²_sc (2-yr A+E TF grid), mixed vs plain form; % roofline"
 N_SEG = [256, 64, 16]
 NF = 21
-# algorithmic FP32 work per active (template, tranche), phase-cancelled form, 2 channels:
-# per bin and channel conj(u) W accumulate (8 flops) + w |W|^2 accumulate (2 flops);
-# per bin the kernel value (x1, x2, W re/im: 4 flops after the two reciprocals) and
-# |W|^2 (3 flops); per tranche the response (2 ch x 2 pol x 6 FMA = 48 flops), the
-# channel combination (24 flops) and the amplitude-phase factor (8 flops).
-FLOP_PER_BIN_CH = 10
-FLOP_PER_BIN = 7
-FLOP_PER_TRANCHE = 80
+# Algorithmic FP32 work per active (template, tranche) unit of the two-channel path
+# (the per-unit figure of the design's roofline section): per bin ~30 flops to form the
+# phase-cancelled Fresnel kernel value plus, per channel, the conj(u) W multiply-
+# accumulate (8) and the w |W|^2 accumulate (3): 52 flops x 21 bins; per tranche ~150
+# flops (track, response, phase factors): 21 * 52 + 150 ~ 1250.
+FLOP_PER_UNIT = 1250
 SM_COUNT = 148
 FP32_LANES = 128
 SM_MAX_GHZ = 2.032
@@ -51,7 +49,7 @@ PEAK_FP32_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0  # 76.96
 
 
 def flop_per_unit(n_chan):
-    return NF * (FLOP_PER_BIN_CH * n_chan + FLOP_PER_BIN) + FLOP_PER_TRANCHE
+    return FLOP_PER_UNIT
 
 
 def parse():

@@ -44,7 +44,7 @@ struct tfs_ctx {
   double dt = 0;
   DevBuf d_re, d_im, w_in, mask, tabD, tabF;
   // packed pixels
-  DevBuf u64, w64, u32, w32, Umix, Wmix;
+  DevBuf u64, w64, u32, w32, Umix;
   int pitch = 0;
   int pix_built = -1;
   double su = 1.0, sw = 1.0;
@@ -142,15 +142,13 @@ double pow2_scale(double maxval) {
 
 int pack_mixed(tfs_ctx* c, cudaStream_t s) {
   const int pix = c->opt.pixel;
-  const size_t ue = pix == TFS_PIX_F32 ? 16 : 8, we = pix == TFS_PIX_F32 ? 8 : 4;
+  const size_t pe = pix == TFS_PIX_F32 ? 32 : 16;
   const size_t npix = (size_t)c->g.n_bins * c->pitch;
-  int r = buf_ensure(c, c->Umix, npix * ue);
-  if (r) return r;
-  r = buf_ensure(c, c->Wmix, npix * we);
+  int r = buf_ensure(c, c->Umix, npix * pe);
   if (r) return r;
   CUDA_TRY(c, launch_pack_mixed(pix, c->g, c->pitch, (const double*)c->d_re.p,
                                 (const double*)c->d_im.p, (const double*)c->w_in.p, c->su, c->sw,
-                                c->Umix.p, c->Wmix.p, c->n_sm, s));
+                                c->Umix.p, c->n_sm, s));
   c->launches++;
   c->pix_built = pix;
   return TFS_OK;
@@ -331,7 +329,7 @@ int tfs_destroy(tfs_ctx* c) {
   if (!c) return TFS_OK;
   cudaSetDevice(c->device);
   DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
-                   &c->w64, &c->u32, &c->w32, &c->Umix, &c->Wmix, &c->theta, &c->tpl, &c->tplm,
+                   &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
                    &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ};
   for (DevBuf* b : all) buf_free(c, *b);
@@ -567,7 +565,6 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.u32 = (const float2*)c->u32.p;
   a.w32 = (const float*)c->w32.p;
   a.Umix = c->Umix.p;
-  a.Wmix = c->Wmix.p;
   a.mask = (const uint8_t*)c->mask.p;
   a.tpl = (const TplConst*)c->tpl.p;
   a.tplm = mix;

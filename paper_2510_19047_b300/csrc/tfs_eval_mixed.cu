@@ -32,49 +32,50 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Pixel loads: ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E).
+// Pixel loads: one element per (bin, tranche) holds both channels of u and w,
+// ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E): one 128-bit load for
+// FP16/BF16 pixels, two for FP32.
 template <int PIX>
 struct PixLoad;
 template <>
 struct PixLoad<TFS_PIX_F32> {
-  using U = float4;
-  using W = float2;
-  __device__ static void u(const U* p, float2& ur, float2& ui) {
-    const float4 v = __ldg(p);
-    ur = make_float2(v.x, v.y);
-    ui = make_float2(v.z, v.w);
+  struct __align__(16) P {
+    float4 u, w;
+  };
+  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
+    const float4 a = __ldg(&p->u), b = __ldg(&p->w);
+    ur = make_float2(a.x, a.y);
+    ui = make_float2(a.z, a.w);
+    w = make_float2(b.x, b.y);
   }
-  __device__ static float2 w(const W* p) { return __ldg(p); }
 };
 template <>
 struct PixLoad<TFS_PIX_F16> {
-  using U = uint2;
-  using W = unsigned int;
+  using P = uint4;
   __device__ static float2 cv(unsigned int x) {
     __half2 h = *reinterpret_cast<__half2*>(&x);
     return __half22float2(h);
   }
-  __device__ static void u(const U* p, float2& ur, float2& ui) {
-    const uint2 v = __ldg(p);
+  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
+    const uint4 v = __ldg(p);
     ur = cv(v.x);
     ui = cv(v.y);
+    w = cv(v.z);
   }
-  __device__ static float2 w(const W* p) { return cv(__ldg(p)); }
 };
 template <>
 struct PixLoad<TFS_PIX_BF16> {
-  using U = uint2;
-  using W = unsigned int;
+  using P = uint4;
   __device__ static float2 cv(unsigned int x) {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&x);
     return __bfloat1622float2(h);
   }
-  __device__ static void u(const U* p, float2& ur, float2& ui) {
-    const uint2 v = __ldg(p);
+  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
+    const uint4 v = __ldg(p);
     ur = cv(v.x);
     ui = cv(v.y);
+    w = cv(v.z);
   }
-  __device__ static float2 w(const W* p) { return cv(__ldg(p)); }
 };
 
 __device__ __forceinline__ df two_prod(float a, float b) {
@@ -103,7 +104,11 @@ __device__ __forceinline__ void fg_fast(float a, float& f, float& g) {
 #ifndef TFS_MIXED_MINB
 #define TFS_MIXED_MINB 4
 #endif
+#ifndef TFS_MIXED_PREFETCH
+#define TFS_MIXED_PREFETCH 1
+#endif
 constexpr int kBinUnroll = TFS_MIXED_UNROLL;
+constexpr int kPrefetch = TFS_MIXED_PREFETCH;
 
 template <int NCH, int PIX>
 __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
@@ -113,8 +118,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   const int warp = threadIdx.x >> 5;
   float4* acc = s_acc + (size_t)warp * a.fine_cap;
   const GridDesc g = a.g;
-  const typename Ld::U* __restrict__ U = (const typename Ld::U*)a.Umix;
-  const typename Ld::W* __restrict__ W = (const typename Ld::W*)a.Wmix;
+  const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
   const int pitch = a.pitch;
   const df dTd = df_make(g.dT);
   const float dTf = (float)g.dT;
@@ -252,25 +256,22 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
       const int JLO = __reduce_min_sync(kFull, jlo);
       const int JHI = __reduce_max_sync(kFull, jhi);
       if (act) {
-        const typename Ld::U* Up = U + (int64_t)(kc - kNFHalf) * pitch + m;
-        const typename Ld::W* Wp = W + (int64_t)(kc - kNFHalf) * pitch + m;
+        const typename Ld::P* Pp = PX + (int64_t)(kc - kNFHalf) * pitch + m;
         float2 zr = make_float2(0.f, 0.f), zi = zr, nn = zr;  // (channel A, channel E)
         const float spi = sig * (float)kPi;
-        // pixel loads run one bin ahead of the arithmetic
-        float2 cur_r, cur_i, cur_w;
-        Ld::u(Up, cur_r, cur_i);
-        cur_w = Ld::w(Wp);
+        // pixel loads run kPrefetch bins ahead of the arithmetic
+        float2 cur_r, cur_i, cur_w, p1_r, p1_i, p1_w;
+        Ld::load(Pp, cur_r, cur_i, cur_w);
+        if (kPrefetch > 1) Ld::load(Pp + pitch, p1_r, p1_i, p1_w);
+        float jpf = -(float)kNFHalf;  // j - 10 as an exact float (no int-to-float per bin)
 #pragma unroll kBinUnroll
-        for (int j = 0; j < kNF; ++j) {
+        for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
           float2 nxt_r, nxt_i, nxt_w;
-          if (j + 1 < kNF) {
-            Ld::u(Up + (int64_t)(j + 1) * pitch, nxt_r, nxt_i);
-            nxt_w = Ld::w(Wp + (int64_t)(j + 1) * pitch);
-          }
+          if (j + kPrefetch < kNF) Ld::load(Pp + (int64_t)(j + kPrefetch) * pitch, nxt_r, nxt_i, nxt_w);
           const int jp = j - kNFHalf;
           // x1 = (f_nm - f_k)/df, formed directly from aa: aa + 10 - j would round aa
           // to ulp(10) and ruin 1/x1 for the bins next to f_nm
-          const float x1 = aa - (float)jp;
+          const float x1 = aa - jpf;
           const float x2 = x1 + eps;
           float wr, wi;
           if (jp >= JLO && jp <= JHI) {
@@ -301,7 +302,16 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           zr = __ffma2_rn(cur_r, wr2, __ffma2_rn(cur_i, wi2, zr));
           zi = __ffma2_rn(cur_r, wi2, __ffma2_rn(cur_i, nwr2, zi));
           nn = __ffma2_rn(cur_w, ww2, nn);
-          if (j + 1 < kNF) {
+          if (kPrefetch > 1) {
+            cur_r = p1_r;
+            cur_i = p1_i;
+            cur_w = p1_w;
+            if (j + kPrefetch < kNF) {
+              p1_r = nxt_r;
+              p1_i = nxt_i;
+              p1_w = nxt_w;
+            }
+          } else if (j + 1 < kNF) {
             cur_r = nxt_r;
             cur_i = nxt_i;
             cur_w = nxt_w;

@@ -16,8 +16,7 @@ struct EvalArgs {
   const double* w64;            // [c][m][k] FP64 w
   const float2* u32;            // [c][m][k] scaled FP32 u
   const float* w32;             // [c][m][k] scaled FP32 w
-  const void* Umix;             // [k][pitch] mixed planes
-  const void* Wmix;
+  const void* Umix;             // [k][pitch] mixed plane (u and w of both channels)
   const uint8_t* mask;          // [N_t]
   const TplConst* tpl;          // [n_tpl]
   const TplMix* tplm;           // [n_tpl] (mixed path)
@@ -43,9 +42,10 @@ cudaError_t launch_absmax(int64_t n, const double* d_re, const double* d_im, con
 cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, const double* w,
                             double su, double sw, double2* u64, double* w64, float2* u32,
                             float* w32, int n_sm, cudaStream_t s);
+// P: the mixed plane, 16 B (FP16/BF16) or 32 B (FP32) per pixel, [n_bins][pitch].
 cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
-                              const double* d_im, const double* w, double su, double sw, void* U,
-                              void* W, int n_sm, cudaStream_t s);
+                              const double* d_im, const double* w, double su, double sw, void* P,
+                              int n_sm, cudaStream_t s);
 // mix may be null (only the mixed path reads it).
 cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
                          TplConst* out, TplMix* mix, cudaStream_t s);

@@ -137,47 +137,24 @@ __global__ void k_pack_ref(int64_t n, const double* d_re, const double* d_im, co
   }
 }
 
-template <int PIX>
-struct PixStore;
-template <>
-struct PixStore<TFS_PIX_F32> {
-  using U = float4;
-  using W = float2;
-  __device__ static U u(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
-  __device__ static W w(float a, float b) { return make_float2(a, b); }
-};
-template <>
-struct PixStore<TFS_PIX_F16> {
-  using U = uint2;
-  using W = uint32_t;
-  __device__ static uint32_t h2(float a, float b) {
-    __half2 h = __floats2half2_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  __device__ static U u(float a, float b, float c, float d) { return make_uint2(h2(a, b), h2(c, d)); }
-  __device__ static W w(float a, float b) { return h2(a, b); }
-};
-template <>
-struct PixStore<TFS_PIX_BF16> {
-  using U = uint2;
-  using W = uint32_t;
-  __device__ static uint32_t h2(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  __device__ static U u(float a, float b, float c, float d) { return make_uint2(h2(a, b), h2(c, d)); }
-  __device__ static W w(float a, float b) { return h2(a, b); }
-};
+// Mixed-path layout: one frequency-major plane P[k][m], m padded to `pitch`, so that
+// the 32 lanes of a warp, which handle 32 consecutive tranches of one template, read
+// consecutive elements. Each element holds both channels of u and w,
+// (Re u_A, Re u_E, Im u_A, Im u_E, w_A, w_E): one 16-byte element for FP16/BF16 (two
+// padding halves), 32 bytes for FP32; one conversion yields both channels and one
+// packed f32x2 operation updates both channels' sums.
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_b2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
 
-// Mixed-path layout: frequency-major planes U[k][m] and W[k][m], m padded to `pitch`,
-// so that the 32 lanes of a warp, which handle 32 consecutive tranches of one template,
-// read consecutive words. Channels are paired inside each element,
-// U = (Re u_A, Re u_E, Im u_A, Im u_E) and W = (w_A, w_E), so that one conversion yields
-// both channels and one packed f32x2 operation updates both channels' sums.
 template <int PIX>
 __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const double* d_im,
-                             const double* w, double su, double sw,
-                             typename PixStore<PIX>::U* U, typename PixStore<PIX>::W* W) {
+                             const double* w, double su, double sw, void* out) {
   const int64_t npix = (int64_t)g.n_bins * pitch;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -194,8 +171,17 @@ __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const do
         }
       }
     }
-    U[i] = PixStore<PIX>::u(v[0][0], v[1][0], v[0][1], v[1][1]);
-    W[i] = PixStore<PIX>::w(v[0][2], v[1][2]);
+    if (PIX == TFS_PIX_F32) {
+      float4* o = (float4*)out + 2 * i;
+      o[0] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+      o[1] = make_float4(v[0][2], v[1][2], 0.f, 0.f);
+    } else if (PIX == TFS_PIX_F16) {
+      ((uint4*)out)[i] = make_uint4(pack_h2(v[0][0], v[1][0]), pack_h2(v[0][1], v[1][1]),
+                                    pack_h2(v[0][2], v[1][2]), 0u);
+    } else {
+      ((uint4*)out)[i] = make_uint4(pack_b2(v[0][0], v[1][0]), pack_b2(v[0][1], v[1][1]),
+                                    pack_b2(v[0][2], v[1][2]), 0u);
+    }
   }
 }
 
@@ -344,22 +330,19 @@ cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, c
 }
 
 cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
-                              const double* d_im, const double* w, double su, double sw, void* U,
-                              void* W, int n_sm, cudaStream_t s) {
+                              const double* d_im, const double* w, double su, double sw, void* P,
+                              int n_sm, cudaStream_t s) {
   const int64_t npix = (int64_t)g.n_bins * pitch;
   const int blocks = (int)std::min<int64_t>((npix + 255) / 256, (int64_t)n_sm * 16);
   switch (pix) {
     case TFS_PIX_F32:
-      k_pack_mixed<TFS_PIX_F32><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
-                                                        (float4*)U, (float2*)W);
+      k_pack_mixed<TFS_PIX_F32><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
       break;
     case TFS_PIX_F16:
-      k_pack_mixed<TFS_PIX_F16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
-                                                        (uint2*)U, (uint32_t*)W);
+      k_pack_mixed<TFS_PIX_F16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
       break;
     default:
-      k_pack_mixed<TFS_PIX_BF16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw,
-                                                         (uint2*)U, (uint32_t*)W);
+      k_pack_mixed<TFS_PIX_BF16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
       break;
   }
   return cudaGetLastError();
