@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--study", default=None, choices=["precision", "ladder", "refine"],
+                   help="run one of the workload studies instead of the headline step")
     return p.parse_args()
 
 
@@ -187,6 +189,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.study:
+        import bench_studies
+        print(json.dumps(getattr(bench_studies, args.study)(args)), flush=True)
         return
     rank, world, local = dist_env()
     import torch

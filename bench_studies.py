@@ -1,0 +1,139 @@
+"""Workload studies run by `bench.py --study <name>` (one JSON line each).
+
+precision : one-channel week grid; each storage/precision variant of the statistic
+            against the FP64 oracle (max, p99 relative error), and the shift in
+            detection probability at a fixed false-alarm probability (ROC) against the
+            FP64 path over seeded noise realisations with and without an injection.
+ladder    : 1e7 templates with uneven in-band durations (lognormal, 30 d to 2 yr) on the
+            two-year A/E grid, N_seg ladder 256 -> 64 -> 16 keeping the top 1 % per stage,
+            each stage one persistent launch replayed as a CUDA graph.
+refine    : 4096 candidates near the injections of the two-year grid at N_seg = 16: the
+            adjoint gradient against the oracle on a sample, then 200 batched
+            gradient-ascent steps.
+"""
+import statistics
+import time
+
+import numpy as np
+
+
+def _ctx(D, **kw):
+    from paper_2510_19047_b300.binding import TFS
+    c = TFS(0, pn_order=D.pn_order, response=D.response, **kw)
+    c.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    c.set_noise_weights(D.w, D.mask)
+    return c
+
+
+def _rel(a, b):
+    m = b > 0
+    r = np.abs(a[m] - b[m]) / b[m]
+    return float(r.max()), float(np.percentile(r, 99))
+
+
+def precision(args):
+    import oracle
+    from paper_2510_19047_b300 import synth
+    D = synth.week_one_channel(seed=0)
+    bank = synth.week_bank(1024, 0)
+    ref = oracle.statistic(D.d, D.w, D.mask, bank, 8, D.dT)[0]
+    variants = [("fp64", "f32"), ("plain", "f32"), ("mixed", "f32"), ("mixed", "f16"),
+                ("mixed", "bf16")]
+    errors = {}
+    ctxs = {}
+    for path, pix in variants:
+        c = _ctx(D, path=path, pixel=pix)
+        got = c.eval_statistic(bank, 8)[0]
+        mx, p99 = _rel(got, ref)
+        errors[f"{path}-{pix}"] = {"max": mx, "p99": p99}
+        ctxs[(path, pix)] = c
+    # ROC: threshold = (1 - FAP) quantile over noise-only realisations of the bank's
+    # largest Upsilon_8; detection = matched template above it in signal realisations
+    n_real, fap, snr = 200, 0.1, 7.0
+    inj = D.injections
+    sig = synth.week_one_channel(seed=0, noise=False, snr=snr)
+    noise_max = {v: [] for v in variants}
+    matched = {v: [] for v in variants}
+    for r in range(n_real):
+        n = synth.tf_noise_only(D.d.shape, D.w, D.df, seed=50_000 + r)
+        for v in variants:
+            c = ctxs[v]
+            c.load_tf_data(n, D.dt, D.dT)
+            c.set_noise_weights(D.w, D.mask)
+            noise_max[v].append(float(c.eval_statistic(bank, 8)[0].max()))
+            c.load_tf_data(n + sig.d, D.dt, D.dT)
+            c.set_noise_weights(D.w, D.mask)
+            matched[v].append(float(c.eval_statistic(inj, 8)[0][0]))
+    roc = {}
+    for v in variants:
+        thr = float(np.quantile(noise_max[v], 1 - fap))
+        roc[f"{v[0]}-{v[1]}"] = {"threshold": thr,
+                                 "p_detect": float(np.mean(np.array(matched[v]) > thr))}
+    base = roc["fp64-f32"]["p_detect"]
+    return {"study": "precision", "workload": "1ch-week-256x512, 1024 templates, N_seg 8",
+            "error_vs_oracle": errors, "roc": roc, "roc_fap": fap, "roc_snr": snr,
+            "roc_realisations": n_real,
+            "max_p_detect_shift_vs_fp64": max(abs(r["p_detect"] - base) for r in roc.values())}
+
+
+def ladder(args):
+    import torch
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.ladder import run_ladder
+    D = synth.cached(synth.two_year_two_channel)
+    n = 10_000_000
+    bank = synth.uneven_length_bank(n, seed=2004, dT=D.dT, n_bins=D.n_bins)
+    c = _ctx(D, use_graph=1)
+    th = torch.from_numpy(bank).cuda()
+    run_ladder(c, th[:, :200_000], stages=(256, 64, 16), keep=0.01)  # warm-up, tuning
+    times = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = run_ladder(c, th, stages=(256, 64, 16), keep=0.01, timings=times)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t0
+    return {"study": "ladder", "workload": "AE-2yr-2048x6144, 1e7 uneven-length templates",
+            "stages": times, "survivors": [len(r["index"]) for r in res],
+            "seconds": total, "templates_per_s": n / total}
+
+
+def refine(args):
+    import torch
+    import oracle
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.refine import refine as run_refine
+    D = synth.cached(synth.two_year_two_channel)
+    cand = synth.candidates_near(D.injections, 4096, seed=2005)
+    c = _ctx(D)
+    th = torch.from_numpy(cand).cuda()
+    u, g = c.grad_statistic(th, 16)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c.grad_statistic(th, 16)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    idx = np.linspace(0, cand.shape[1] - 1, 6).astype(int)
+    ru, rg = oracle.gradient(D.d, D.w, D.mask, cand[:, idx], 16, D.dT, pn_order=1, response=1)
+    gg = g.cpu().numpy()[:, idx]
+    comp = {}
+    for p, name in enumerate(("Mc", "eta", "f0", "phi0", "lam", "beta", "psi", "iota")):
+        if p == 3:
+            continue
+        scale = np.maximum(np.abs(rg[p]), 1e-3 * np.abs(rg[p]).max())
+        comp[name] = float(np.max(np.abs(gg[p] - rg[p]) / scale))
+    t0 = time.perf_counter()
+    best, hist, u0, u1 = run_refine(c, th, 16, steps=200)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    u0, u1 = u0.cpu().numpy(), u1.cpu().numpy()
+    return {"study": "refine", "workload": "AE-2yr-2048x6144, 4096 candidates near 20 injections, N_seg 16",
+            "grad_ms_per_call": statistics.median(ts),
+            "grad_rel_err_vs_oracle": comp,
+            "stat_rel_err_vs_oracle": _rel(u.cpu().numpy()[idx], ru)[0],
+            "ascent_steps": 200, "ascent_seconds": dt,
+            "mean_upsilon_start": float(u0.mean()), "mean_upsilon_end": float(u1.mean()),
+            "fraction_improved": float(np.mean(u1 > u0))}

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
     const float fd_k = c.fd_k;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
     const df P5 = {c.P5_hi, c.P5_lo};  // phase coefficients in cycles
     const df P3 = {c.P3_hi, c.P3_lo};
-    const df ph0 = {c.ph0_hi, c.ph0_lo};
+    const df Kc = {c.K_hi, c.K_lo};
     const df dopc = {c.dopc_hi, c.dopc_lo}, dops = {c.dops_hi, c.dops_lo};
     int nact = 0, nnc = 0;
     __syncwarp();
@@ -210,12 +210,14 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           } else {
             ++nact;
             if (fdot > ncomp) ++nnc;
-            // phase in cycles: phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u^(5/8) = u y^3
+            // phase in cycles: K - P5 u^(5/8) - P3 u^(3/8), with u^(5/8) = u y^3 and
+            // u^(3/8) = u y^5; the fractional part is taken in two steps because the hi
+            // word can be an integer-valued float (|Phi| > 2^23 cycles)
             const df u58 = df_mul(u, y3);
             const df u38 = df_mul(u58, y2);
-            const df ph = df_add(ph0, df_add(df_mul(P5, df_sub(one, u58)),
-                                             df_mul(P3, df_sub(one, u38))));
-            const float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
+            const df ph = df_sub(df_sub(Kc, df_mul(P5, u58)), df_mul(P3, u38));
+            float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
+            cyc = __fsub_rn(cyc, rintf(cyc));
             // cyc is in [-1/2, 1/2]: the hardware sine/cosine are accurate to ~4e-7 there
             float sph, cph;
             __sincosf(6.283185307f * cyc, &sph, &cph);

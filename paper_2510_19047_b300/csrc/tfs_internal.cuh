@@ -71,7 +71,7 @@ struct __align__(16) TplMix {
   float F0_hi, F0_lo;
   float P5_hi, P5_lo;        // P5 / 2 pi (cycles)
   float P3_hi, P3_lo;        // P3 / 2 pi
-  float ph0_hi, ph0_lo;      // frac(phi0 / 2 pi)
+  float K_hi, K_lo;          // frac(phi0 / 2 pi + P5 / 2 pi + P3 / 2 pi): Phi = K - P5 u^5/8 - P3 u^3/8
   float dopc_hi, dopc_lo, dops_hi, dops_lo;
   float C2, fd_k;            // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
   float pp[6], px[6];

@@ -216,8 +216,12 @@ __device__ TplMix mix_of(const TplConst& c) {
   split(c.F0, t.F0_hi, t.F0_lo);
   split(c.P5 * (0.5 / kPi), t.P5_hi, t.P5_lo);
   split(c.P3 * (0.5 / kPi), t.P3_hi, t.P3_lo);
+  // Phi/2pi = phi0/2pi + P5 (1 - u^5/8) + P3 (1 - u^3/8) = K - P5 u^5/8 - P3 u^3/8; the
+  // integer part of K is irrelevant
   const double ph = c.phi0 * (0.5 / kPi);
-  split(ph - floor(ph), t.ph0_hi, t.ph0_lo);
+  const double P5c = c.P5 * (0.5 / kPi), P3c = c.P3 * (0.5 / kPi);
+  const double K = (ph - floor(ph)) + (P5c - floor(P5c)) + (P3c - floor(P3c));
+  split(K - floor(K), t.K_hi, t.K_lo);
   split(c.dop_c, t.dopc_hi, t.dopc_lo);
   split(c.dop_s, t.dops_hi, t.dops_lo);
   t.C2 = (float)c.C2;
