@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--path", default="mixed", choices=["mixed", "plain", "fp64"])
     p.add_argument("--pixel", default="f16", choices=["f16", "bf16", "f32"])
     p.add_argument("--plain-templates", type=int, default=20_000)
+    p.add_argument("--fp64-templates", type=int, default=5_000)
     p.add_argument("--cpu-sample", type=int, default=1200)  # ~10-20 s of oracle work
     p.add_argument("--ref-sample", type=int, default=48)    # per reference-arm step
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -140,16 +141,19 @@ def oracle_sample_rate(D, theta, n_seg, threads=0):
     return theta.shape[1] / dt, dt
 
 
-def traffic_record():
-    """Per-launch DRAM bytes of the statistic kernel from a committed ncu summary, valid
-    only while the kernel source is unchanged."""
+def traffic_record(units):
+    """DRAM bytes (read + write) of one full-size statistic launch, from a committed
+    one-pass ncu capture of this bench's workload; valid only while the kernel source is
+    unchanged and the launch processes the same number of units. The traffic is not
+    proportional to the units (the grid is read about once per launch and then served
+    from L2), so a capture of another size is not rescaled."""
     src = os.path.join(ROOT, "paper_2510_19047_b300", "csrc", "tfs_eval_mixed.cu")
     path = os.path.join(ROOT, "profiles", "k_eval_mixed_dram.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    if rec.get("source_sha1") != h:
+    if rec.get("source_sha1") != h or int(rec.get("units_per_launch", -1)) != units:
         return None
     return rec
 
@@ -257,10 +261,10 @@ def main():
     kms = statistics.mean(kern_ms)
     flops = units * flop_per_unit(D.n_chan)
     achieved = flops / (kms / 1000.0) / 1e12
-    trec = traffic_record()
+    trec = traffic_record(units)
     roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / PEAK_FP32_TFLOPS,
-            "traffic": (trec["dram_bytes_per_unit"] * units) if trec else None,
+            "traffic": trec["dram_bytes_per_launch"] if trec else None,
             "kernel": "k_eval_mixed", "kernel_ms": kms, "units_per_launch": units,
             "flop_per_unit": flop_per_unit(D.n_chan),
             "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz"}
@@ -298,6 +302,23 @@ def main():
         result["plain"] = {"value": pv, "unit": "templates/s", "n_templates": sub.shape[1],
                            "ms_per_step": statistics.mean(pms), "dtype": "f32 pixels, f64 phase"}
         result["mixed_vs_plain"] = (n / (statistics.mean(step_ms) / 1000.0)) / pv
+        # the FP64 parity path on a subset of the same bank
+        ctx.set_options(path="fp64", profile=1)
+        sub = theta[:, : args.fp64_templates].contiguous()
+        ctx.eval_statistic(sub, N_SEG)
+        fms = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.eval_statistic(sub, N_SEG)
+            e1.record(stream)
+            e1.synchronize()
+            fms.append(e0.elapsed_time(e1))
+        result["fp64"] = {"value": sub.shape[1] / (statistics.mean(fms) / 1000.0),
+                          "unit": "templates/s", "n_templates": sub.shape[1],
+                          "ms_per_step": statistics.mean(fms), "dtype": "f64"}
         ctx.set_options(path=args.path, pixel=args.pixel, profile=1)
 
     if rank == 0 and not args.no_e2e:

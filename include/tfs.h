@@ -102,7 +102,7 @@ int tfs_set_options(tfs_ctx* ctx, const tfs_options* opt);
 int tfs_get_options(const tfs_ctx* ctx, tfs_options* opt);
 
 /* Load the time-frequency data grid d~_alpha,m[k] (Eq. inner-tranche-tf):
- *   n_chan 1 or 2 (A, E), n_tranche N_t >= 1, n_bins >= 22 complex bins per tranche
+ *   n_chan 1 or 2 (A, E), n_tranche N_t in [1, 65535], n_bins in [22, 2^21] complex bins per tranche
  *   (bin k at f_k = k / dT), dt the sample cadence (dT / dt >= 2 n_bins), dT the
  *   tranche length [s], t0 the start time of tranche 0 [s].
  *   d_re, d_im: double [n_chan][n_tranche][n_bins], host or device, copied.

@@ -372,8 +372,10 @@ int tfs_load_tf_data(tfs_ctx* c, int n_chan, int n_tranche, int n_bins, double d
   if (!c) return TFS_ERR_ARG;
   c->err.clear();
   if (n_chan < 1 || n_chan > 2) return fail(c, TFS_ERR_ARG, "n_chan must be 1 or 2");
-  if (n_tranche < 1) return fail(c, TFS_ERR_ARG, "n_tranche must be >= 1");
-  if (n_bins < 2 * kNFHalf + 2) return fail(c, TFS_ERR_ARG, "n_bins must be >= 22");
+  if (n_tranche < 1 || n_tranche > 65535)
+    return fail(c, TFS_ERR_ARG, "n_tranche must be in [1, 65535]");
+  if (n_bins < 2 * kNFHalf + 2 || n_bins > (1 << 21))
+    return fail(c, TFS_ERR_ARG, "n_bins must be in [22, 2^21]");
   if (!(dT > 0.0) || !(dt > 0.0) || !std::isfinite(dT) || !std::isfinite(t0))
     return fail(c, TFS_ERR_ARG, "dt and dT must be positive and finite");
   if (dT / dt + 1e-9 < 2.0 * n_bins)

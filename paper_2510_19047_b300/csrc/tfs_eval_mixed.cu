@@ -22,6 +22,7 @@
 // deterministic segmented shuffle reduction into shared memory, and at the end into
 // every requested N_seg (Eqs. overlap-n, Upsilon-seg).
 #include <math.h>
+#include <stddef.h>
 
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
@@ -34,7 +35,8 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Pixel loads: one element per (bin, tranche) holds both channels of u and w,
 // ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E): one 128-bit load for
-// FP16/BF16 pixels, two for FP32.
+// FP16/BF16 pixels, two for FP32. raw() loads, cvt() widens to FP32 at the point of use
+// (the prefetched element stays packed).
 template <int PIX>
 struct PixLoad;
 template <>
@@ -42,11 +44,11 @@ struct PixLoad<TFS_PIX_F32> {
   struct __align__(16) P {
     float4 u, w;
   };
-  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
-    const float4 a = __ldg(&p->u), b = __ldg(&p->w);
-    ur = make_float2(a.x, a.y);
-    ui = make_float2(a.z, a.w);
-    w = make_float2(b.x, b.y);
+  __device__ static P raw(const P* p) { return P{__ldg(&p->u), __ldg(&p->w)}; }
+  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
+    ur = make_float2(v.u.x, v.u.y);
+    ui = make_float2(v.u.z, v.u.w);
+    w = make_float2(v.w.x, v.w.y);
   }
 };
 template <>
@@ -56,8 +58,8 @@ struct PixLoad<TFS_PIX_F16> {
     __half2 h = *reinterpret_cast<__half2*>(&x);
     return __half22float2(h);
   }
-  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
-    const uint4 v = __ldg(p);
+  __device__ static P raw(const P* p) { return __ldg(p); }
+  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
     ur = cv(v.x);
     ui = cv(v.y);
     w = cv(v.z);
@@ -70,13 +72,47 @@ struct PixLoad<TFS_PIX_BF16> {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&x);
     return __bfloat1622float2(h);
   }
-  __device__ static void load(const P* p, float2& ur, float2& ui, float2& w) {
-    const uint4 v = __ldg(p);
+  __device__ static P raw(const P* p) { return __ldg(p); }
+  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
     ur = cv(v.x);
     ui = cv(v.y);
     w = cv(v.z);
   }
 };
+
+// Rounding to an integer on the FMA pipe (the conversion units are slow on this part):
+// exact round-half-even for |x| < 2^22, and the integer value of such a float.
+__device__ __forceinline__ float rint_small(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+__device__ __forceinline__ int int_small(float x) {
+  return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
+// Non-coherent 16-byte load kept in place (volatile: not hoisted out of the tranche
+// loop, so its result does not occupy registers across it).
+__device__ __forceinline__ float4 ldg_nc4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &&
+                  offsetof(TplMix, K_hi) == 32 && offsetof(TplMix, dops_hi) == 48 &&
+                  offsetof(TplMix, C2) == 56 && offsetof(TplMix, fd_k) == 60 &&
+                  offsetof(TplMix, pp) == 64 && offsetof(TplMix, px) == 88,
+              "TplMix layout assumed by the 16-byte loads of the mixed kernel");
+
+// x^(-1/8) to ~2^-21 relative from the hardware base-2 logarithm and exponential
+// (x > 0); the seed of a Newton step.
+__device__ __forceinline__ float pow_m18(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.125f * l));
+  return r;
+}
 
 __device__ __forceinline__ df two_prod(float a, float b) {
   df r;
@@ -85,15 +121,65 @@ __device__ __forceinline__ df two_prod(float a, float b) {
   return r;
 }
 
-// Paper's auxiliary Fresnel functions in FP32 with approximate division.
-__device__ __forceinline__ void fg_fast(float a, float& f, float& g) {
-  if (a > 6.0f) {
-    f = __fdividef(1.0f, (float)kPi * a);
-    g = 0.0f;
-  } else {
-    f = __fdividef(fmaf(0.926f, a, 1.0f), fmaf(a, fmaf(3.104f, a, 1.792f), 2.0f));
-    g = __fdividef(1.0f, fmaf(a, fmaf(a, fmaf(6.670f, a, 3.492f), 4.142f), 2.0f));
+// The paper's auxiliary Fresnel functions f, g in FP32 with approximate division,
+// branch-free: the rational forms for a <= 6 and the printed asymptotic form
+// f = 1/(pi a), g = 0 beyond (Sec. "Fresnel integrals").
+__device__ __forceinline__ void fg_sel(float a, float& f, float& g) {
+  const bool big = a > 6.0f;
+  const float num = big ? 1.0f : fmaf(0.926f, a, 1.0f);
+  const float den = big ? (float)kPi * a : fmaf(a, fmaf(3.104f, a, 1.792f), 2.0f);
+  f = __fdividef(num, den);
+  const float e = fmaf(a, fmaf(a, fmaf(6.670f, a, 3.492f), 4.142f), 2.0f);
+  g = big ? 0.0f : __fdividef(1.0f, e);
+}
+
+// General bin: W''_k = sigma pi W_k with W_k = s1 G(|v1|) - s2 G(|v2|) e^{i Psi}
+// + [s1 != s2] (1+i) e^{-i pi v1^2 / 2}, G = g + i f, v = sigma x.
+__device__ __forceinline__ void w_general(float x1, float x2, float sig, float spi, float cpsi,
+                                          float spsi, bool sweep, float& wr, float& wi) {
+  const float v1 = sig * x1, v2 = sig * x2;
+  float f1, g1, f2, g2;
+  fg_sel(fabsf(v1), f1, g1);
+  fg_sel(fabsf(v2), f2, g2);
+  const float s1 = v1 < 0.f ? -spi : spi, s2 = v2 < 0.f ? -spi : spi;
+  wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
+  wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
+  if (sweep && v1 < 0.f && v2 >= 0.f) {  // f_k inside this tranche's sweep
+    float sp, cp;
+    sincospif(0.5f * v1 * v1, &sp, &cp);
+    wr = fmaf(spi, cp + sp, wr);
+    wi = fmaf(spi, cp - sp, wi);
   }
+}
+
+// Per-tranche bin sums, channels A and E paired: with real weights q = 1/x the
+// asymptotic bins need only U1 = sum u q1 and U2 = sum u q2, since
+// sum conj(u) W'' = i conj(U1) - i e^{i Psi} conj(U2) for W'' = i q1 - i e^{i Psi} q2.
+// A general bin with complex W'' adds i u conj(W'') to U1, which the same formula maps
+// back to conj(u) W''. nn = sum w |W''|^2.
+struct BinAcc {
+  float2 u1r, u1i, u2r, u2i, nn;
+};
+
+__device__ __forceinline__ void acc_asym(BinAcc& s, float2 ur, float2 ui, float2 w, float x1,
+                                         float x2, float m2c) {
+  const float q1 = __fdividef(1.0f, x1), q2 = __fdividef(1.0f, x2);
+  const float2 Q1 = make_float2(q1, q1), Q2 = make_float2(q2, q2);
+  s.u1r = __ffma2_rn(ur, Q1, s.u1r);
+  s.u1i = __ffma2_rn(ui, Q1, s.u1i);
+  s.u2r = __ffma2_rn(ur, Q2, s.u2r);
+  s.u2i = __ffma2_rn(ui, Q2, s.u2i);
+  const float ww = fmaf(q1, fmaf(m2c, q2, q1), q2 * q2);  // |W''|^2 = q1^2 + q2^2 - 2 cos(Psi) q1 q2
+  s.nn = __ffma2_rn(w, make_float2(ww, ww), s.nn);
+}
+
+__device__ __forceinline__ void acc_general(BinAcc& s, float2 ur, float2 ui, float2 w, float wr,
+                                            float wi) {
+  const float2 WR = make_float2(wr, wr), WI = make_float2(wi, wi);
+  s.u1r = __ffma2_rn(ur, WI, __ffma2_rn(ui, make_float2(-wr, -wr), s.u1r));
+  s.u1i = __ffma2_rn(ur, WR, __ffma2_rn(ui, WI, s.u1i));
+  const float ww = fmaf(wr, wr, wi * wi);
+  s.nn = __ffma2_rn(w, make_float2(ww, ww), s.nn);
 }
 
 }  // namespace
@@ -104,11 +190,8 @@ __device__ __forceinline__ void fg_fast(float a, float& f, float& g) {
 #ifndef TFS_MIXED_MINB
 #define TFS_MIXED_MINB 4
 #endif
-#ifndef TFS_MIXED_PREFETCH
-#define TFS_MIXED_PREFETCH 1
-#endif
+
 constexpr int kBinUnroll = TFS_MIXED_UNROLL;
-constexpr int kPrefetch = TFS_MIXED_PREFETCH;
 
 template <int NCH, int PIX>
 __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
@@ -132,7 +215,8 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
     t = __shfl_sync(kFull, t, 0);
     if (t >= a.n_work) break;
     const int idx = a.perm ? a.perm[t] : t;
-    const TplMix c = a.tplm[idx];
+    const TplMix* __restrict__ cptr = a.tplm + idx;
+    const int m_lo = cptr->m_lo, m_hi = cptr->m_hi;
 
     int nl, fine_len;
     int seg_len[kMaxLevels];
@@ -147,28 +231,34 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
       fine_len = a.lv.fine_len;
     }
     const int n_fine = g.n_tranche / fine_len;
+    // m / fine_len = umulhi(m, ceil(2^32 / fine_len)), exact while m * fine_len < 2^32
+    // (n_tranche < 2^16, checked by the host)
+    const unsigned fmagic = fine_len > 1 ? 0xFFFFFFFFu / (unsigned)fine_len + 1u : 0u;
     for (int q = lane; q < n_fine; q += 32) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    const df tc_inv = {c.tcinv_hi, c.tcinv_lo};
-    const df F0 = {c.F0_hi, c.F0_lo};
-    const float C2 = c.C2;
-    const float fd_k = c.fd_k;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
-    const df P5 = {c.P5_hi, c.P5_lo};  // phase coefficients in cycles
-    const df P3 = {c.P3_hi, c.P3_lo};
-    const df Kc = {c.K_hi, c.K_lo};
-    const df dopc = {c.dopc_hi, c.dopc_lo}, dops = {c.dops_hi, c.dops_lo};
     int nact = 0, nnc = 0;
     __syncwarp();
 
-    for (int m0 = c.m_lo; m0 < c.m_hi; m0 += 32) {
+    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
       const int m = m0 + lane;
-      const bool inr = m < c.m_hi;
+      const bool inr = m < m_hi;
       bool act = inr && a.mask[m];
       float Zr = 0.f, Zi = 0.f, Nn = 0.f;
       int kc = 0;
-      float aa = 0.f, eps = 0.f, sig = 1.f, spsi = 0.f, cpsi = 1.f, amp_c = 0.f, amp_s = 0.f;
-      float Tr0 = 1.f, Ti0 = 0.f, Tr1 = 1.f, Ti1 = 0.f;
+      float aa = 0.f, eps = 0.f, sig = 1.f, spsi = 0.f, cpsi = 1.f;
+      // T_alpha A e^{i phi}: response times amplitude and phase factor, per channel
+      float Tr0 = 0.f, Ti0 = 0.f, Tr1 = 0.f, Ti1 = 0.f;
       if (act) {
+        // the template's constants are re-read per tranche (L1 hits) instead of being
+        // held in registers across the tranche loop
+        const float4* cq = reinterpret_cast<const float4*>(cptr);
+        const float4 c0 = ldg_nc4(cq), c1 = ldg_nc4(cq + 1), c2 = ldg_nc4(cq + 2),
+                     c3 = ldg_nc4(cq + 3);
+        const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
+        const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};  // phase coefficients in cycles
+        const df Kc = {c2.x, c2.y}, dopc = {c2.z, c2.w};
+        const df dops = {c3.x, c3.y};
+        const float C2 = c3.z, fd_k = c3.w;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
         const TrancheF tr = a.tabF[m];
         const df tt = {tr.t_hi, tr.t_lo};
         df d0 = {0.f, 0.f};
@@ -185,7 +275,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           act = false;
         } else {
           // y = u^(-1/8): FP32 seed, one Newton step with a double-float residual
-          const float y0 = rsqrtf(sqrtf(sqrtf(u.hi)));
+          const float y0 = pow_m18(u.hi);
           const df y02 = two_prod(y0, y0);
           const df y08 = df_sqr(df_sqr(y02));
           const df p = df_mul(u, y08);
@@ -201,23 +291,25 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
           const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
           const df x = df_mul(f, dTd);  // f_nm / df
-          float kcf = ceilf(x.hi);
-          if (kcf == x.hi && x.lo > 0.f) kcf += 1.0f;
-          kc = (int)kcf;
+          // the window test first on the float, so that x is small enough for the
+          // FMA-pipe ceiling below (n_bins < 2^22)
+          const bool inband = x.hi > (float)kNFHalf && x.hi < (float)(g.n_bins - kNFHalf);
+          float kcf = rint_small(inband ? x.hi : 0.0f);  // ceil(x) = rint(x) (+1 if below x)
+          if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
+          kc = int_small(kcf);
           aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);  // f_nm/df - k_c, in (-1, 0]
-          if (!(fdot > 0.f) || kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) {
+          if (!inband || !(fdot > 0.f) || kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) {
             act = false;
           } else {
             ++nact;
             if (fdot > ncomp) ++nnc;
-            // phase in cycles: K - P5 u^(5/8) - P3 u^(3/8), with u^(5/8) = u y^3 and
-            // u^(3/8) = u y^5; the fractional part is taken in two steps because the hi
-            // word can be an integer-valued float (|Phi| > 2^23 cycles)
+            // phase in cycles: K - P5 u^(5/8) - P3 u^(3/8) = K - u y^3 (P5 + P3 y^2)
+            // (u^(5/8) = u y^3, u^(3/8) = u y^5); the fractional part is taken in two
+            // steps because the hi word can be an integer-valued float (|Phi| > 2^23)
             const df u58 = df_mul(u, y3);
-            const df u38 = df_mul(u58, y2);
-            const df ph = df_sub(df_sub(Kc, df_mul(P5, u58)), df_mul(P3, u38));
+            const df ph = df_sub(Kc, df_mul(u58, df_add(P5, df_mul(P3, y2))));
             float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
-            cyc = __fsub_rn(cyc, rintf(cyc));
+            cyc = __fsub_rn(cyc, rint_small(cyc));
             // cyc is in [-1/2, 1/2]: the hardware sine/cosine are accurate to ~4e-7 there
             float sph, cph;
             __sincosf(6.283185307f * cyc, &sph, &cph);
@@ -225,101 +317,112 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             const float amp =
                 y2f * fmaf(c2y2, fmaf(c2y2, fmaf(c2y2, 4.0f / 81.0f, -1.0f / 9.0f), 2.0f / 3.0f),
                            1.0f);
-            amp_c = amp * cph;
-            amp_s = amp * sph;
+            const float amp_c = amp * cph, amp_s = amp * sph;
+            Tr0 = Tr1 = amp_c;
+            Ti0 = Ti1 = amp_s;
             sig = sig_k * rsqrtf(fdot);
             eps = fdot * dTf * dTf;  // fdot dT / df: sweep width in bins
             const float psi = fmaf(2.0f, aa, eps);  // Psi / pi, reduced to [-1, 1]
-            __sincosf(3.141592654f * (psi - 2.0f * rintf(0.5f * psi)), &spsi, &cpsi);
+            __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &spsi, &cpsi);
             if (a.response) {
               float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
+              // the polarisation tensors are read here, per tranche, from L1 rather than
+              // held in registers across the tranche loop
+              const float4* pq = reinterpret_cast<const float4*>(a.tplm[idx].pp);
+              const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
+              const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+              const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
 #pragma unroll
               for (int q = 0; q < 6; ++q) {
-                fpA = fmaf(tr.DA[q], c.pp[q], fpA);
-                fxA = fmaf(tr.DA[q], c.px[q], fxA);
-                fpE = fmaf(tr.DE[q], c.pp[q], fpE);
-                fxE = fmaf(tr.DE[q], c.px[q], fxE);
+                fpA = fmaf(tr.DA[q], pp[q], fpA);
+                fxA = fmaf(tr.DA[q], px[q], fxA);
+                fpE = fmaf(tr.DE[q], pp[q], fpE);
+                fxE = fmaf(tr.DE[q], px[q], fxE);
               }
-              Tr0 = fpA;
-              Ti0 = -fxA;
-              Tr1 = fpE;
-              Ti1 = -fxE;
+              // (F+ - i Fx)(amp_c + i amp_s)
+              Tr0 = fmaf(fpA, amp_c, fxA * amp_s);
+              Ti0 = fmaf(fpA, amp_s, -fxA * amp_c);
+              Tr1 = fmaf(fpE, amp_c, fxE * amp_s);
+              Ti1 = fmaf(fpE, amp_s, -fxE * amp_c);
             }
           }
         }
       }
-      // window-relative bins that need the exact (rational or in-sweep) branch
-      int jlo = 100, jhi = -100;
-      if (act) {
-        const float r6 = __fdividef(6.0f, sig);
-        jlo = (int)ceilf(aa - r6 - 0.01f);
-        jhi = (int)floorf(aa + eps + r6 + 0.01f);
+      // Window-relative bins jp = j - 10 that need the general (rational or in-sweep)
+      // form: |v| <= 6 for v1 or v2, or the sweep [x1, x2] contains 0. Joined over the
+      // warp so that every branch below is warp-uniform.
+      // jlo = ceil(aa - r6 - 0.01) and jhi = floor(aa + eps + r6 + 0.01), r6 = 6/sigma;
+      // the common case jlo >= -1, jhi <= 0 is tested on the floats
+      const float r6 = act ? __fdividef(6.0f, sig) : 0.0f;
+      const bool central = !act || (aa - r6 - 0.01f > -2.0f && aa + eps + r6 + 0.01f < 1.0f);
+      int JLO = -1, JHI = 0;
+      if (!__all_sync(kFull, central)) {
+        int jlo = 100, jhi = -100;
+        if (act) {
+          jlo = (int)ceilf(aa - r6 - 0.01f);
+          jhi = (int)floorf(aa + eps + r6 + 0.01f);
+        }
+        JLO = __reduce_min_sync(kFull, jlo);
+        JHI = __reduce_max_sync(kFull, jhi);
       }
-      const int JLO = __reduce_min_sync(kFull, jlo);
-      const int JHI = __reduce_max_sync(kFull, jhi);
       if (act) {
         const typename Ld::P* Pp = PX + (int64_t)(kc - kNFHalf) * pitch + m;
-        float2 zr = make_float2(0.f, 0.f), zi = zr, nn = zr;  // (channel A, channel E)
         const float spi = sig * (float)kPi;
-        // pixel loads run kPrefetch bins ahead of the arithmetic
-        float2 cur_r, cur_i, cur_w, p1_r, p1_i, p1_w;
-        Ld::load(Pp, cur_r, cur_i, cur_w);
-        if (kPrefetch > 1) Ld::load(Pp + pitch, p1_r, p1_i, p1_w);
-        float jpf = -(float)kNFHalf;  // j - 10 as an exact float (no int-to-float per bin)
-#pragma unroll kBinUnroll
-        for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
-          float2 nxt_r, nxt_i, nxt_w;
-          if (j + kPrefetch < kNF) Ld::load(Pp + (int64_t)(j + kPrefetch) * pitch, nxt_r, nxt_i, nxt_w);
-          const int jp = j - kNFHalf;
-          // x1 = (f_nm - f_k)/df, formed directly from aa: aa + 10 - j would round aa
-          // to ulp(10) and ruin 1/x1 for the bins next to f_nm
-          const float x1 = aa - jpf;
-          const float x2 = x1 + eps;
-          float wr, wi;
-          if (jp >= JLO && jp <= JHI) {
-            const float v1 = sig * x1, v2 = sig * x2;
-            float f1, g1, f2, g2;
-            fg_fast(fabsf(v1), f1, g1);
-            fg_fast(fabsf(v2), f2, g2);
-            const float s1 = v1 < 0.f ? -1.f : 1.f, s2 = v2 < 0.f ? -1.f : 1.f;
-            wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
-            wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
-            if (s1 != s2) {
-              float sp, cp;
-              sincospif(0.5f * v1 * v1, &sp, &cp);
-              wr += cp + sp;
-              wi += cp - sp;
+        const float ae = aa + eps;
+        const float m2c = -2.0f * cpsi;
+        BinAcc s;
+        s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
+        // pixel loads run one bin ahead of the arithmetic
+        typename Ld::P cur = Ld::raw(Pp);
+        if (JLO >= -1 && JHI <= 0) {
+          // Only the two bins next to f_nm (jp = -1, 0) can need the general form:
+          // fully unrolled, no per-bin branch. For jp >= 1, x2 < -r6 < 0; for jp <= -2,
+          // x1 > 1 > r6; and only jp = 0 can hold the sweep (x1 = aa <= 0 < x2).
+#pragma unroll
+          for (int j = 0; j < kNF; ++j) {
+            typename Ld::P nxt;
+            if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(cur, cur_r, cur_i, cur_w);
+            constexpr float kZero = 0.0f;
+            const float c = kZero + (float)(j - kNFHalf);
+            if (j == kNFHalf - 1 || j == kNFHalf) {
+              float wr, wi;
+              w_general(aa - c, ae - c, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
+              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+            } else {
+              acc_asym(s, cur_r, cur_i, cur_w, aa - c, ae - c, m2c);
             }
-            wr *= spi;
-            wi *= spi;
-          } else {
-            const float q1 = __fdividef(1.0f, x1), q2 = __fdividef(1.0f, x2);
-            wr = spsi * q2;
-            wi = fmaf(-cpsi, q2, q1);
+            if (j + 1 < kNF) cur = nxt;
           }
-          const float ww = fmaf(wr, wr, wi * wi);
-          const float2 wr2 = make_float2(wr, wr), wi2 = make_float2(wi, wi);
-          const float2 nwr2 = make_float2(-wr, -wr), ww2 = make_float2(ww, ww);
-          // conj(u) W for both channels at once
-          zr = __ffma2_rn(cur_r, wr2, __ffma2_rn(cur_i, wi2, zr));
-          zi = __ffma2_rn(cur_r, wi2, __ffma2_rn(cur_i, nwr2, zi));
-          nn = __ffma2_rn(cur_w, ww2, nn);
-          if (kPrefetch > 1) {
-            cur_r = p1_r;
-            cur_i = p1_i;
-            cur_w = p1_w;
-            if (j + kPrefetch < kNF) {
-              p1_r = nxt_r;
-              p1_i = nxt_i;
-              p1_w = nxt_w;
+        } else {
+          float jpf = -(float)kNFHalf;  // jp as an exact float (no int-to-float per bin)
+#pragma unroll kBinUnroll
+          for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
+            typename Ld::P nxt;
+            if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(cur, cur_r, cur_i, cur_w);
+            const int jp = j - kNFHalf;
+            // x1 = (f_nm - f_k)/df formed directly from aa: aa + 10 - j would round aa
+            // to ulp(10) and ruin 1/x1 for the bins next to f_nm
+            const float x1 = aa - jpf;
+            const float x2 = ae - jpf;
+            if (jp >= JLO && jp <= JHI) {
+              float wr, wi;
+              w_general(x1, x2, sig, spi, cpsi, spsi, true, wr, wi);
+              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+            } else {
+              acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
             }
-          } else if (j + 1 < kNF) {
-            cur_r = nxt_r;
-            cur_i = nxt_i;
-            cur_w = nxt_w;
+            if (j + 1 < kNF) cur = nxt;
           }
         }
-        const float zr0 = zr.x, zi0 = zi.x, n0 = nn.x, zr1 = zr.y, zi1 = zi.y, n1 = nn.y;
+        // Z = i conj(U1) - i e^{i Psi} conj(U2), both channels at once
+        const float2 ncp = make_float2(-cpsi, -cpsi);
+        const float2 zr = __ffma2_rn(make_float2(spsi, spsi), s.u2r, __ffma2_rn(ncp, s.u2i, s.u1i));
+        const float2 zi = __ffma2_rn(ncp, s.u2r, __ffma2_rn(make_float2(-spsi, -spsi), s.u2i, s.u1r));
+        const float zr0 = zr.x, zi0 = zi.x, n0 = s.nn.x, zr1 = zr.y, zi1 = zi.y, n1 = s.nn.y;
         float ar = Tr0 * zr0 - Ti0 * zi0, ai = Tr0 * zi0 + Ti0 * zr0;
         float nt = (Tr0 * Tr0 + Ti0 * Ti0) * n0;
         if (NCH == 2) {
@@ -327,13 +430,13 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           ai += Tr1 * zi1 + Ti1 * zr1;
           nt += (Tr1 * Tr1 + Ti1 * Ti1) * n1;
         }
-        Zr = ar * amp_c - ai * amp_s;
-        Zi = ar * amp_s + ai * amp_c;
-        Nn = (amp_c * amp_c + amp_s * amp_s) * nt;
+        Zr = ar;
+        Zi = ai;
+        Nn = nt;
       }
       // segmented (by finest segment) suffix sums across the warp; the first lane
       // of each run adds its segment's sum to shared memory
-      const int key = inr ? m / fine_len : 0x7fffffff;
+      const int key = inr ? (fine_len > 1 ? (int)__umulhi((unsigned)m, fmagic) : m) : 0x7fffffff;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const float zr2 = __shfl_down_sync(kFull, Zr, o);

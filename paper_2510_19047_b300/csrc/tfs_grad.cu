@@ -41,10 +41,13 @@ cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const As
 // (s folds the constant 4 delta f and the storage scales of u and w). One warp per
 // template, one lane per tranche. Pass A forms Z_n, N_n in shared memory; pass B
 // recomputes the track (it is never stored), the per-bin sums of the Fresnel-kernel
-// derivatives with respect to v_1, v_2 and Psi, turns them into the tranche's
-// sensitivities to (f, fdot, phi, A, T_alpha), and chains those to theta through
-// forward-mode derivatives of the FP64 track (one direction per parameter). The window
-// position and the Fresnel branch are held fixed: the almost-everywhere derivative.
+// derivatives with respect to v_1, v_2 and Psi, and turns them into the tranche's
+// sensitivities to (f, fdot, phi, A, T_alpha). A reverse-mode step through the FP64
+// closed-form track adds the tranche's share to the adjoints of the 20 template
+// constants (t_c, F0, C2, P5, P3, phi0, the delay amplitudes, A+ e+, Ax ex); at the end
+// they are contracted with the constants' derivatives with respect to theta (forward
+// mode, one direction per parameter, once per template). The window position and the
+// Fresnel branch are held fixed: the almost-everywhere derivative.
 // ---------------------------------------------------------------------------------
 namespace {
 
@@ -126,33 +129,143 @@ struct GradArgs {
   double* out_grad;     // [8][n]
 };
 
-struct Local {
+// x^(-1/8) to ~2^-21 relative (x > 0), the seed of the FP64 Newton steps below.
+__device__ __forceinline__ float seed_m18(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.125f * l));
+  return r;
+}
+
+// The track at the start of tranche m in FP64 without transcendental calls: the same
+// chirp model as the set-up (f = F0 y^3 (1 + C2 y^2), Phi = phi0 + P5 (1 - u^(5/8)) +
+// P3 (1 - u^(3/8)), y = u^(-1/8), u = 1 - t'/t_c, t' = t + n.r/c) with y from a float
+// seed and two Newton steps, and the intermediates the adjoint needs.
+struct Trk {
   bool ok;
   int kc;
-  double f, fdot, phi, amp, Tr[2], Ti[2];
+  double f, fdot, phi, amp;  // phi absolute [rad]; amp = (f_src/F0)^(2/3)
+  double Tr[2], Ti[2];
+  double u, y, y2, onec, fsrc, fdsrc, d1, d2;
 };
 
-__device__ __forceinline__ Local local_track(const GradArgs& a, const SrcT<double>& s, int m) {
-  Local L;
-  L.ok = false;
-  if (!a.mask[m]) return L;
-  const int ma = (m / a.seg_len) * a.seg_len;
-  const TrkT<double> k = track_of<double>(s, a.tabD[m], a.tabD[ma], (double)(m - ma) * a.g.dT,
-                                          a.response);
-  if (!k.alive || !(k.fdot > 0.0)) return L;
-  const int kc = (int)ceil(k.f * a.g.dT);
-  if (kc - kNFHalf < 1 || kc + kNFHalf > a.g.n_bins - 1) return L;
-  L.ok = true;
-  L.kc = kc;
-  L.f = k.f;
-  L.fdot = k.fdot;
-  L.phi = k.dphi;
-  L.amp = k.amp;
-  for (int c = 0; c < 2; ++c) {
-    L.Tr[c] = k.Tr[c];
-    L.Ti[c] = k.Ti[c];
+struct SrcAux {
+  double tc_inv, inv8tc;
+};
+
+__device__ __forceinline__ Trk track64(const GradArgs& a, const SrcT<double>& s, const SrcAux& x,
+                                       int m) {
+  Trk k;
+  k.ok = false;
+  if (!a.mask[m]) return k;
+  const TrancheD& tr = a.tabD[m];
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+  if (a.response) {
+    d0 = s.dop_c * tr.ca + s.dop_s * tr.sa;
+    d1 = kOmega * (s.dop_s * tr.ca - s.dop_c * tr.sa);
+    d2 = -kOmega * kOmega * d0;
   }
-  return L;
+  const double tp = tr.t + d0;
+  const double u = fma(-tp, x.tc_inv, 1.0);
+  if (!(u > 0.0)) return k;
+  double y = (double)seed_m18((float)u);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // y <- y (1 + (1 - u y^8) / 8)
+    const double y2 = y * y, y4 = y2 * y2;
+    y = fma(y * 0.125, fma(-u, y4 * y4, 1.0), y);
+  }
+  const double y2 = y * y, y3 = y2 * y;
+  const double onec = fma(s.C2, y2, 1.0);
+  const double fsrc = s.F0 * y3 * onec;
+  const double y5 = y3 * y2, y11 = y5 * y5 * y;
+  const double fdsrc = s.F0 * y11 * fma(5.0 * s.C2, y2, 3.0) * x.inv8tc;
+  const double f = fsrc * (1.0 + d1);
+  const double fdot = fdsrc * (1.0 + d1) * (1.0 + d1) + fsrc * d2;
+  if (!(fdot > 0.0)) return k;
+  const int kc = (int)ceil(f * a.g.dT);
+  if (kc - kNFHalf < 1 || kc + kNFHalf > a.g.n_bins - 1) return k;
+  k.ok = true;
+  k.kc = kc;
+  k.f = f;
+  k.fdot = fdot;
+  const double u58 = u * y3;  // u^(5/8)
+  k.phi = s.phi0 + s.P5 * (1.0 - u58) + s.P3 * (1.0 - u58 * y2);
+  const float cb = cbrtf((float)onec);
+  k.amp = y2 * (double)(cb * cb);
+  k.u = u;
+  k.y = y;
+  k.y2 = y2;
+  k.onec = onec;
+  k.fsrc = fsrc;
+  k.fdsrc = fdsrc;
+  k.d1 = d1;
+  k.d2 = d2;
+  if (a.response) {
+    double fpA = 0, fxA = 0, fpE = 0, fxE = 0;
+    for (int q = 0; q < 6; ++q) {
+      fpA = fma(s.pp[q], tr.DA[q], fpA);
+      fxA = fma(s.px[q], tr.DA[q], fxA);
+      fpE = fma(s.pp[q], tr.DE[q], fpE);
+      fxE = fma(s.px[q], tr.DE[q], fxE);
+    }
+    k.Tr[0] = fpA;
+    k.Ti[0] = -fxA;
+    k.Tr[1] = fpE;
+    k.Ti[1] = -fxE;
+  } else {
+    k.Tr[0] = k.Tr[1] = 1.0;
+    k.Ti[0] = k.Ti[1] = 0.0;
+  }
+  return k;
+}
+
+// e^{i phi} with phi in FP64 reduced to cycles first; FP32 sine and cosine.
+__device__ __forceinline__ void phase_factor(double phi, float& s, float& c) {
+  double cyc = phi * (0.5 / kPi);
+  cyc -= rint(cyc);
+  __sincosf(6.283185307f * (float)cyc, &s, &c);
+}
+
+// Reverse-mode step of the track for one tranche: given the tranche's sensitivities
+// of Upsilon to (f, fdot, phi, ln A, T_alpha), add its contribution to the adjoints G
+// of the template constants (tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6]).
+__device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcT<double>& s,
+                                              const SrcAux& x, const Trk& k, int m, double cf,
+                                              double cfd, double cphi, double cP,
+                                              const double cTr[2], const double cTi[2],
+                                              double G[kSrcFields]) {
+  const double op1 = 1.0 + k.d1;
+  const double g_fsrc = cf * op1 + cfd * k.d2;
+  const double g_fdsrc = cfd * op1 * op1;
+  const double g_d1 = cf * k.fsrc + 2.0 * cfd * k.fdsrc * op1;
+  const double g_d2 = cfd * k.fsrc;
+  const double y = k.y, y2 = k.y2, y3 = y2 * y, y5 = y3 * y2;
+  const double y10 = y5 * y5;
+  // f_src = F0 y^3 onec, fdot_src = F0 y^11 (3 + 5 C2 y^2) / (8 t_c), ln A = 2 ln y + (2/3) ln onec
+  const double dfs_dy = s.F0 * y2 * fma(5.0 * s.C2, y2, 3.0);
+  const double dfd_dy = s.F0 * y10 * fma(65.0 * s.C2, y2, 33.0) * x.inv8tc;
+  const double dlnA_dy = 2.0 / y + (4.0 / 3.0) * s.C2 * y / k.onec;
+  const double g_y = g_fsrc * dfs_dy + g_fdsrc * dfd_dy + cP * dlnA_dy;
+  G[2] += g_fsrc * s.F0 * y5 + g_fdsrc * s.F0 * y10 * y3 * 5.0 * x.inv8tc +
+          cP * (2.0 / 3.0) * y2 / k.onec;
+  if (s.F0 != 0.0) G[1] += (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) / s.F0;
+  const double u58 = k.u * y3;
+  G[3] += cphi * (1.0 - u58);
+  G[4] += cphi * (1.0 - u58 * y2);
+  G[5] += cphi;
+  const double g_u = -g_y * y / (8.0 * k.u) - cphi * (0.625 * s.P5 * y3 + 0.375 * s.P3 * y5);
+  G[0] += (g_u * (1.0 - k.u) - g_fdsrc * k.fdsrc) * x.tc_inv;  // du/dtc = (1 - u)/tc
+  if (a.response) {
+    const TrancheD& tr = a.tabD[m];
+    const double g_tp = -g_u * x.tc_inv;
+    const double w2 = kOmega * kOmega;
+    G[6] += g_tp * tr.ca - g_d1 * kOmega * tr.sa - g_d2 * w2 * tr.ca;
+    G[7] += g_tp * tr.sa + g_d1 * kOmega * tr.ca - g_d2 * w2 * tr.sa;
+    for (int q = 0; q < 6; ++q) {
+      G[8 + q] += cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
+      G[14 + q] -= cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q];
+    }
+  }
 }
 
 }  // namespace
@@ -170,6 +283,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   for (int p = 0; p < 8; ++p) th[p] = a.theta[(int64_t)p * a.n_tpl + i];
   const TplConst tc = a.tpl[i];
   const SrcT<double> s = source_of<double>(th, a.pn_order);
+  SrcAux xa;
+  xa.tc_inv = 1.0 / s.tc;
+  xa.inv8tc = 0.125 * xa.tc_inv;
   for (int q = lane; q < a.n_seg; q += 32) seg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   // directional derivatives of the template constants: lane p < 8 takes direction p
   if (lane < 8) {
@@ -191,7 +307,6 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     }
   }
   __syncwarp();
-  const float dTf = (float)g.dT;
 
   // ---- pass A: Z_n, N_n ----
   for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
@@ -199,7 +314,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     const bool inr = m < tc.m_hi;
     float Zr = 0.f, Zi = 0.f, Nn = 0.f;
     if (inr) {
-      const Local L = local_track(a, s, m);
+      const Trk L = track64(a, s, xa, m);
       if (L.ok) {
         const double x = L.f * g.dT;
         const float aa = (float)(x - (double)L.kc);
@@ -222,8 +337,8 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
           }
         }
         const float P = (float)(L.amp / sqrt(2.0 * L.fdot));
-        double sph, cph;
-        sincos(L.phi, &sph, &cph);
+        float sph, cph;
+        phase_factor(L.phi, sph, cph);
         for (int c = 0; c < nch; ++c) {
           const float ar = (float)L.Tr[c] * zr[c] - (float)L.Ti[c] * zi[c];
           const float ai = (float)L.Tr[c] * zi[c] + (float)L.Ti[c] * zr[c];
@@ -273,12 +388,13 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   if (lane == 0) a.out_stat[i] = ups;
   __syncwarp();
 
-  // ---- pass B: gradient ----
-  double grad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // ---- pass B: adjoints of the template constants ----
+  double G[kSrcFields];
+  for (int k = 0; k < kSrcFields; ++k) G[k] = 0.0;
   for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
     const int m = m0 + lane;
     if (m >= tc.m_hi) continue;
-    const Local L = local_track(a, s, m);
+    const Trk L = track64(a, s, xa, m);
     if (!L.ok) continue;
     const float4 lm = seg[m / a.seg_len];
     const double lr = lm.x, li = lm.y, mu = lm.z;
@@ -318,8 +434,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     }
     // sensitivities of this tranche's dUpsilon to (f, fdot, phi, A, T_alpha)
     const double P = L.amp / sqrt(2.0 * L.fdot);
-    double sph, cph;
-    sincos(L.phi, &sph, &cph);
+    float sphf, cphf;
+    phase_factor(L.phi, sphf, cphf);
+    const double sph = sphf, cph = cphf;
     const double Er = P * cph, Ei = P * sph;  // E = P e^{i phi}
     const double rt = sqrt(2.0 / L.fdot), ifd2 = 0.5 / L.fdot;
     const double twopidT = 2.0 * kPi * g.dT, pidT2 = kPi * g.dT * g.dT;
@@ -355,36 +472,21 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     }
     const double cphi = -(lr * Zmi + li * Zmr);       // Re(i lambda z)
     const double cP = (lr * Zmr - li * Zmi) + 2.0 * mu * Nm;  // coefficient of dP/P
-    const double cA = cP / L.amp;
     cfd += -cP * ifd2;
-    // chain to theta: one forward-mode direction per parameter
-    const int ma = (m / a.seg_len) * a.seg_len;
-    const TrancheD tr = a.tabD[m], ta = a.tabD[ma];
-    for (int p = 0; p < 8; ++p) {
-      const double* o = s_dsrc[warp][p];
-      SrcT<D1> sd;
-      sd.tc = mk(s.tc, o[0]);
-      sd.F0 = mk(s.F0, o[1]);
-      sd.C2 = mk(s.C2, o[2]);
-      sd.P5 = mk(s.P5, o[3]);
-      sd.P3 = mk(s.P3, o[4]);
-      sd.phi0 = mk(s.phi0, o[5]);
-      sd.dop_c = mk(s.dop_c, o[6]);
-      sd.dop_s = mk(s.dop_s, o[7]);
-      for (int q = 0; q < 6; ++q) {
-        sd.pp[q] = mk(s.pp[q], o[8 + q]);
-        sd.px[q] = mk(s.px[q], o[14 + q]);
-      }
-      const TrkT<D1> k = track_of<D1>(sd, tr, ta, (double)(m - ma) * g.dT, a.response);
-      double gp = cf * k.f.d + cfd * k.fdot.d + cphi * (k.dphi.d) + cA * k.amp.d;
-      for (int c = 0; c < nch; ++c) gp += cTr[c] * k.Tr[c].d + cTi[c] * k.Ti[c].d;
-      grad[p] += gp;
-    }
+    track_adjoint(a, s, xa, L, m, cf, cfd, cphi, cP, cTr, cTi, G);
   }
-  for (int p = 0; p < 8; ++p) {
-    double v = grad[p];
+  // d Upsilon / d theta_p = sum_k G_k d(constant_k)/d theta_p
+  double grad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < kSrcFields; ++k) {
+    double v = G[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
-    if (lane == 0) a.out_grad[(int64_t)p * a.n_tpl + i] = v;
+    for (int p = 0; p < 8; ++p) grad[p] = fma(v, s_dsrc[warp][p][k], grad[p]);
+  }
+  if (lane < 8) {
+    double v = grad[0];
+    for (int p = 1; p < 8; ++p)
+      if (lane == p) v = grad[p];
+    a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
   }
 }
 

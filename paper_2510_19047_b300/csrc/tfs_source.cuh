@@ -1,6 +1,7 @@
-// Source model of a template and its track at a tranche start, written once over the
+// Source model of a template (its per-template constants), written once over the
 // scalar type R: R = double for values, R = D1 (value and one directional derivative,
-// forward mode) for the gradient kernel.
+// forward mode) for the derivatives of the constants with respect to theta that the
+// gradient kernel contracts its adjoints with.
 //
 // Chirp (Sec. "Time-frequency waveform representation" expands the GW phase about
 // the tranche start; the chirp model itself is the reading stated in the header):
@@ -11,7 +12,8 @@
 //              Phi = phi_c - (2/eta) (Theta^(5/8) + (3715/8064 + 55 eta/96) Theta^(3/8))
 //   Both as f = F0 y^3 (1 + C2 y^2), y = u^(-1/8), Phi = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)).
 // Response (Eq. tdi2 in the long-wavelength limit): T_alpha = D_alpha : (A+ e+) - i D_alpha : (Ax ex),
-// with the barycentre delay t' = t + n.r(t)/c.
+// with the barycentre delay t' = t + n.r(t)/c; the constants here are A+ e+, Ax ex and
+// the delay's amplitudes (R/c) cos(beta) (cos lambda, sin lambda).
 #pragma once
 
 #include <math.h>
@@ -52,15 +54,6 @@ __device__ __forceinline__ D1 r_pow(D1 x, double p) {
   const double y = pow(x.v, p);
   return {y, p * y / x.v * x.d};
 }
-__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ D1 r_sqrt(D1 x) {
-  const double s = sqrt(x.v);
-  return {s, 0.5 * x.d / s};
-}
-__device__ __forceinline__ double r_log1p(double x) { return log1p(x); }
-__device__ __forceinline__ D1 r_log1p(D1 x) { return {log1p(x.v), x.d / (1.0 + x.v)}; }
-__device__ __forceinline__ double r_expm1(double x) { return expm1(x); }
-__device__ __forceinline__ D1 r_expm1(D1 x) { return {expm1(x.v), exp(x.v) * x.d}; }
 __device__ __forceinline__ void r_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ void r_sincos(D1 x, D1* s, D1* c) {
   double sv, cv;
@@ -141,63 +134,6 @@ __device__ SrcT<R> source_of(const R th[8], int pn_order) {
   s.dop_c = kAuS * cb * cl;
   s.dop_s = kAuS * cb * sl;
   return s;
-}
-
-template <class R>
-struct TrkT {
-  R f, fdot, dphi, amp;  // detector-frame f, fdot; phase since the anchor [rad]; (f/F0)^(2/3)
-  R Tr[2], Ti[2];
-  bool alive;
-};
-
-// Track at the start of tranche `tr` with the phase measured from the start of
-// tranche `ta` (the anchor, m_a <= m); dm_dT = (m - m_a) dT exactly.
-template <class R>
-__device__ TrkT<R> track_of(const SrcT<R>& s, const TrancheD& tr, const TrancheD& ta, double dm_dT,
-                            int resp) {
-  TrkT<R> k;
-  const R zero = s.tc * 0.0;
-  R d0 = zero, d1 = zero, d2 = zero, a0 = zero;
-  if (resp) {
-    d0 = s.dop_c * tr.ca + s.dop_s * tr.sa;
-    d1 = kOmega * (s.dop_s * tr.ca - s.dop_c * tr.sa);
-    d2 = (-kOmega * kOmega) * d0;
-    a0 = s.dop_c * ta.ca + s.dop_s * ta.sa;
-  }
-  const R tp = d0 + tr.t;
-  const R tpa = a0 + ta.t;
-  k.alive = val(tp) < val(s.tc) && val(tpa) < val(s.tc);
-  if (!k.alive) return k;
-  const R u = 1.0 - tp / s.tc;
-  const R y = r_pow(u, -0.125), y2 = y * y, y3 = y2 * y;
-  const R onec = 1.0 + s.C2 * y2;
-  const R fsrc = s.F0 * y3 * onec;
-  const R fdsrc = s.F0 * (y3 * y3 * y3 * y2) * (3.0 + 5.0 * s.C2 * y2) / (8.0 * s.tc);
-  k.f = fsrc * (1.0 + d1);
-  k.fdot = fdsrc * (1.0 + d1) * (1.0 + d1) + fsrc * d2;
-  k.amp = r_pow(y3 * onec, 2.0 / 3.0);
-  const R delta = (d0 - a0) + dm_dT;
-  const R ua = 1.0 - tpa / s.tc;
-  const R l = r_log1p((-delta) / (s.tc - tpa));
-  k.dphi = s.P5 * r_pow(ua, 0.625) * (-r_expm1(0.625 * l)) +
-           s.P3 * r_pow(ua, 0.375) * (-r_expm1(0.375 * l));
-  if (resp) {
-    R fpA = zero, fxA = zero, fpE = zero, fxE = zero;
-    for (int q = 0; q < 6; ++q) {
-      fpA = fpA + s.pp[q] * tr.DA[q];
-      fxA = fxA + s.px[q] * tr.DA[q];
-      fpE = fpE + s.pp[q] * tr.DE[q];
-      fxE = fxE + s.px[q] * tr.DE[q];
-    }
-    k.Tr[0] = fpA;
-    k.Ti[0] = -fxA;
-    k.Tr[1] = fpE;
-    k.Ti[1] = -fxE;
-  } else {
-    k.Tr[0] = k.Tr[1] = zero + 1.0;
-    k.Ti[0] = k.Ti[1] = zero;
-  }
-  return k;
 }
 
 }  // namespace tfs
