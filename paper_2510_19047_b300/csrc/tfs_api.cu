@@ -214,7 +214,7 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
   };
   if (c->opt.warps_per_cta) {
     int per_sm = 0;
-    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->opt.warps_per_cta, fine_cap, &per_sm));
+    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.warps_per_cta, fine_cap, &per_sm));
     if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
     *warps_out = c->opt.warps_per_cta;
     shape_for(*warps_out, per_sm, ctas_out);
@@ -229,7 +229,7 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
     cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
     for (int warps : {4, 8}) {
       int occ = 0;
-      CUDA_TRY(c, mixed_occupancy(n_chan, pix, warps, fine_cap, &occ));
+      CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, warps, fine_cap, &occ));
       for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
         int ctas;
         shape_for(warps, per_sm, &ctas);
@@ -253,7 +253,7 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
     it = c->tuned.emplace(key, pick).first;
   }
   int occ = 0;
-  CUDA_TRY(c, mixed_occupancy(n_chan, pix, it->second.first, fine_cap, &occ));
+  CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, it->second.first, fine_cap, &occ));
   *warps_out = it->second.first;
   shape_for(*warps_out, std::min(occ, it->second.second), ctas_out);
   return TFS_OK;
@@ -390,7 +390,8 @@ int tfs_load_tf_data(tfs_ctx* c, int n_chan, int n_tranche, int n_bins, double d
   c->g.df = 1.0 / dT;
   c->g.t0 = t0;
   c->dt = dt;
-  c->pitch = (n_tranche + 31) / 32 * 32;
+  // the mixed plane's m-pitch: the kernel's compile-time pitch when the grid fits it
+  c->pitch = n_tranche <= kMixedPitch ? kMixedPitch : (n_tranche + 31) / 32 * 32;
   const size_t n = (size_t)n_chan * n_tranche * n_bins;
   int r;
   if ((r = buf_ensure(c, c->d_re, n * 8)) || (r = buf_ensure(c, c->d_im, n * 8)) ||

@@ -121,6 +121,19 @@ __device__ __forceinline__ df two_prod(float a, float b) {
   return r;
 }
 
+// The hardware reciprocal and reciprocal square root (one MUFU instruction each, ~1 ulp;
+// subnormal inputs flush to zero, which the callers never pass).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // The paper's auxiliary Fresnel functions f, g in FP32 with approximate division,
 // branch-free: the rational forms for a <= 6 and the printed asymptotic form
 // f = 1/(pi a), g = 0 beyond (Sec. "Fresnel integrals").
@@ -128,9 +141,9 @@ __device__ __forceinline__ void fg_sel(float a, float& f, float& g) {
   const bool big = a > 6.0f;
   const float num = big ? 1.0f : fmaf(0.926f, a, 1.0f);
   const float den = big ? (float)kPi * a : fmaf(a, fmaf(3.104f, a, 1.792f), 2.0f);
-  f = __fdividef(num, den);
+  f = num * rcp_approx(den);
   const float e = fmaf(a, fmaf(a, fmaf(6.670f, a, 3.492f), 4.142f), 2.0f);
-  g = big ? 0.0f : __fdividef(1.0f, e);
+  g = big ? 0.0f : rcp_approx(e);
 }
 
 // General bin: W''_k = sigma pi W_k with W_k = s1 G(|v1|) - s2 G(|v2|) e^{i Psi}
@@ -163,7 +176,7 @@ struct BinAcc {
 
 __device__ __forceinline__ void acc_asym(BinAcc& s, float2 ur, float2 ui, float2 w, float x1,
                                          float x2, float m2c) {
-  const float q1 = __fdividef(1.0f, x1), q2 = __fdividef(1.0f, x2);
+  const float q1 = rcp_approx(x1), q2 = rcp_approx(x2);
   const float2 Q1 = make_float2(q1, q1), Q2 = make_float2(q2, q2);
   s.u1r = __ffma2_rn(ur, Q1, s.u1r);
   s.u1i = __ffma2_rn(ui, Q1, s.u1i);
@@ -193,7 +206,9 @@ __device__ __forceinline__ void acc_general(BinAcc& s, float2 ur, float2 ui, flo
 
 constexpr int kBinUnroll = TFS_MIXED_UNROLL;
 
-template <int NCH, int PIX>
+// PITCH: the m-pitch of the pixel plane as a compile-time constant (kMixedPitch) so that
+// the 21 window rows are immediate offsets from one address, or 0 for a runtime pitch.
+template <int NCH, int PIX, int PITCH>
 __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
@@ -202,7 +217,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   float4* acc = s_acc + (size_t)warp * a.fine_cap;
   const GridDesc g = a.g;
   const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
-  const int pitch = a.pitch;
+  const int pitch = PITCH ? PITCH : a.pitch;
   const df dTd = df_make(g.dT);
   const float dTf = (float)g.dT;
   const float sig_k = (float)(sqrt(2.0) * g.df);       // sigma = df sqrt(2/fdot)
@@ -320,7 +335,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             const float amp_c = amp * cph, amp_s = amp * sph;
             Tr0 = Tr1 = amp_c;
             Ti0 = Ti1 = amp_s;
-            sig = sig_k * rsqrtf(fdot);
+            sig = sig_k * rsqrt_approx(fdot);
             eps = fdot * dTf * dTf;  // fdot dT / df: sweep width in bins
             const float psi = fmaf(2.0f, aa, eps);  // Psi / pi, reduced to [-1, 1]
             __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &spsi, &cpsi);
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
       // warp so that every branch below is warp-uniform.
       // jlo = ceil(aa - r6 - 0.01) and jhi = floor(aa + eps + r6 + 0.01), r6 = 6/sigma;
       // the common case jlo >= -1, jhi <= 0 is tested on the floats
-      const float r6 = act ? __fdividef(6.0f, sig) : 0.0f;
+      const float r6 = act ? 6.0f * rcp_approx(sig) : 0.0f;
       const bool central = !act || (aa - r6 - 0.01f > -2.0f && aa + eps + r6 + 0.01f < 1.0f);
       int JLO = -1, JHI = 0;
       if (!__all_sync(kFull, central)) {
@@ -494,48 +509,57 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   }
 }
 
-template <int NCH, int PIX>
+template <int NCH, int PIX, int PITCH>
 static cudaError_t launch_one(const EvalArgs& a, int warps, int ctas, cudaStream_t s) {
   const size_t smem = (size_t)warps * a.fine_cap * sizeof(float4);
-  k_eval_mixed<NCH, PIX><<<ctas, warps * 32, smem, s>>>(a);
+  k_eval_mixed<NCH, PIX, PITCH><<<ctas, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
+
+// Sets the dynamic shared-memory limit of the instantiation and returns how many CTAs
+// of this shape fit on one SM.
+template <int NCH, int PIX, int PITCH>
+static cudaError_t occ_one(int warps, int fine_cap, int* n) {
+  const size_t smem = (size_t)warps * fine_cap * sizeof(float4);
+  auto kern = k_eval_mixed<NCH, PIX, PITCH>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, warps * 32, smem);
+}
+
+// Instantiation for (channels, pixel type, pitch); CALL(NCH, PIX, PITCH) is an expression.
+#define TFS_MIXED_DISPATCH(CALL, n_chan, pix, pitch)                                        \
+  do {                                                                                      \
+    const bool fixed = (pitch) == kMixedPitch;                                              \
+    if ((n_chan) == 1) {                                                                    \
+      if ((pix) == TFS_PIX_F32)                                                             \
+        return fixed ? CALL(1, TFS_PIX_F32, kMixedPitch) : CALL(1, TFS_PIX_F32, 0);         \
+      if ((pix) == TFS_PIX_F16)                                                             \
+        return fixed ? CALL(1, TFS_PIX_F16, kMixedPitch) : CALL(1, TFS_PIX_F16, 0);         \
+      return fixed ? CALL(1, TFS_PIX_BF16, kMixedPitch) : CALL(1, TFS_PIX_BF16, 0);         \
+    }                                                                                       \
+    if ((pix) == TFS_PIX_F32)                                                               \
+      return fixed ? CALL(2, TFS_PIX_F32, kMixedPitch) : CALL(2, TFS_PIX_F32, 0);           \
+    if ((pix) == TFS_PIX_F16)                                                               \
+      return fixed ? CALL(2, TFS_PIX_F16, kMixedPitch) : CALL(2, TFS_PIX_F16, 0);           \
+    return fixed ? CALL(2, TFS_PIX_BF16, kMixedPitch) : CALL(2, TFS_PIX_BF16, 0);           \
+  } while (0)
 
 // Launch only (no attribute calls, so it can be captured into a CUDA graph);
 // mixed_occupancy() must have been called for the same shape first.
 cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
                               cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
-  if (n_chan == 1) {
-    if (pix == TFS_PIX_F32) return launch_one<1, TFS_PIX_F32>(a, warps, ctas, s);
-    if (pix == TFS_PIX_F16) return launch_one<1, TFS_PIX_F16>(a, warps, ctas, s);
-    return launch_one<1, TFS_PIX_BF16>(a, warps, ctas, s);
-  }
-  if (pix == TFS_PIX_F32) return launch_one<2, TFS_PIX_F32>(a, warps, ctas, s);
-  if (pix == TFS_PIX_F16) return launch_one<2, TFS_PIX_F16>(a, warps, ctas, s);
-  return launch_one<2, TFS_PIX_BF16>(a, warps, ctas, s);
+#define TFS_CALL(N, P, Q) launch_one<N, P, Q>(a, warps, ctas, s)
+  TFS_MIXED_DISPATCH(TFS_CALL, n_chan, pix, a.pitch);
+#undef TFS_CALL
 }
 
-// Sets the dynamic shared-memory limit of the instantiation and returns how many CTAs
-// of this shape fit on one SM.
-template <int NCH, int PIX>
-static cudaError_t occ_one(int warps, int fine_cap, int* n) {
-  const size_t smem = (size_t)warps * fine_cap * sizeof(float4);
-  auto kern = k_eval_mixed<NCH, PIX>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, warps * 32, smem);
-}
-
-cudaError_t mixed_occupancy(int n_chan, int pix, int warps, int fine_cap, int* ctas_per_sm) {
-  if (n_chan == 1) {
-    if (pix == TFS_PIX_F32) return occ_one<1, TFS_PIX_F32>(warps, fine_cap, ctas_per_sm);
-    if (pix == TFS_PIX_F16) return occ_one<1, TFS_PIX_F16>(warps, fine_cap, ctas_per_sm);
-    return occ_one<1, TFS_PIX_BF16>(warps, fine_cap, ctas_per_sm);
-  }
-  if (pix == TFS_PIX_F32) return occ_one<2, TFS_PIX_F32>(warps, fine_cap, ctas_per_sm);
-  if (pix == TFS_PIX_F16) return occ_one<2, TFS_PIX_F16>(warps, fine_cap, ctas_per_sm);
-  return occ_one<2, TFS_PIX_BF16>(warps, fine_cap, ctas_per_sm);
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int warps, int fine_cap,
+                            int* ctas_per_sm) {
+#define TFS_CALL(N, P, Q) occ_one<N, P, Q>(warps, fine_cap, ctas_per_sm)
+  TFS_MIXED_DISPATCH(TFS_CALL, n_chan, pix, pitch);
+#undef TFS_CALL
 }
 
 }  // namespace tfs

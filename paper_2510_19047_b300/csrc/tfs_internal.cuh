@@ -18,6 +18,7 @@ constexpr double kYearS = 31557600.0;       // Julian year [s]
 constexpr double kOmega = 2.0 * kPi / kYearS;
 constexpr int kNF = 21;      // N_F bins per tranche
 constexpr int kNFHalf = 10;  // window k_c - 10 .. k_c + 10
+constexpr int kMixedPitch = 8192;  // m-pitch of the mixed pixel plane for N_t <= 8192
 constexpr int kMaxLevels = 4;
 
 // Grid geometry.

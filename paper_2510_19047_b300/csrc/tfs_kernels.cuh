@@ -56,7 +56,8 @@ cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s);
 // Persistent mixed-precision launch; grid = ctas, block = 32 * warps.
 cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
                               cudaStream_t s);
-cudaError_t mixed_occupancy(int n_chan, int pix, int warps, int fine_cap, int* ctas_per_sm);
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int warps, int fine_cap,
+                            int* ctas_per_sm);
 
 struct AscentParams {
   double step[8], lo[8], hi[8];
