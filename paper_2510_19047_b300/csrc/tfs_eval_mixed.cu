@@ -5,9 +5,9 @@
 // Per tranche (lane):
 //   * the track (Sec. "Time-frequency waveform representation": phi_nm, f_nm,
 //     fdot_nm at the tranche start) in double-float arithmetic: retarded time
-//     t' = t + n.r/c, u = 1 - t'/t_c, y = u^(-1/8) by one Newton step, f, and the phase
-//     in cycles (accurate to ~1e-8 cycles over 1e6 cycles); fdot, amplitude and
-//     response in FP32;
+//     t' = t + n.r/c (the delay itself in FP32), u = 1 - t'/t_c, y = u^(-1/8) by one
+//     Newton step, f, and the phase in cycles (accurate to ~1e-5 cycles over 1e7
+//     cycles); fdot, amplitude and response in FP32;
 //   * the Fresnel-kernel transform (Eq. fresnel-ft) in the phase-cancelled form
 //     h~_k = A/sqrt(2 fdot) e^{i phi} W_k (see tfs_eval_ref.cu), scaled as
 //     W''_k = sigma pi W_k with sigma = df sqrt(2/fdot) so that v = sigma x,
@@ -205,6 +205,10 @@ __device__ __forceinline__ void acc_general(BinAcc& s, float2 ur, float2 ui, flo
 #endif
 
 constexpr int kBinUnroll = TFS_MIXED_UNROLL;
+#ifndef TFS_MIXED_DEPTH
+#define TFS_MIXED_DEPTH 3
+#endif
+constexpr int kDepth = TFS_MIXED_DEPTH;  // pixel-load lead of the unrolled path, in bins
 
 // PITCH: the m-pitch of the pixel plane as a compile-time constant (kMixedPitch) so that
 // the 21 window rows are immediate offsets from one address, or 0 for a runtime pitch.
@@ -276,15 +280,15 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
         const float C2 = c3.z, fd_k = c3.w;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
         const TrancheF tr = a.tabF[m];
         const df tt = {tr.t_hi, tr.t_lo};
-        df d0 = {0.f, 0.f};
-        float d1 = 0.f, d2 = 0.f;
+        // barycentre delay n.r/c (|d0| <= 500 s) in FP32: its rounding, < 1e-4 s, moves
+        // the phase by < 1e-5 cycles
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (a.response) {
-          const df ca = {tr.ca_hi, tr.ca_lo}, sa = {tr.sa_hi, tr.sa_lo};
-          d0 = df_add(df_mul(dopc, ca), df_mul(dops, sa));
-          d1 = (float)kOmega * (dops.hi * ca.hi - dopc.hi * sa.hi);
-          d2 = -(float)(kOmega * kOmega) * d0.hi;
+          d0 = fmaf(dopc.hi, tr.ca_hi, dops.hi * tr.sa_hi);
+          d1 = (float)kOmega * (dops.hi * tr.ca_hi - dopc.hi * tr.sa_hi);
+          d2 = -(float)(kOmega * kOmega) * d0;
         }
-        const df tp = df_add(tt, d0);
+        const df tp = df_add_f(tt, d0);
         const df u = df_sub(one, df_mul(tp, tc_inv));  // 1 - t'/t_c
         if (!(u.hi > 0.f)) {
           act = false;
@@ -393,12 +397,17 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           // Only the two bins next to f_nm (jp = -1, 0) can need the general form:
           // fully unrolled, no per-bin branch. For jp >= 1, x2 < -r6 < 0; for jp <= -2,
           // x1 > 1 > r6; and only jp = 0 can hold the sweep (x1 = aa <= 0 < x2).
+          // pixel loads run kDepth bins ahead (a ring of packed elements in registers)
+          typename Ld::P ring[kDepth];
+          ring[0] = cur;
+#pragma unroll
+          for (int q = 1; q < kDepth; ++q) ring[q] = Ld::raw(Pp + (int64_t)q * pitch);
 #pragma unroll
           for (int j = 0; j < kNF; ++j) {
-            typename Ld::P nxt;
-            if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
+            const typename Ld::P pj = ring[j % kDepth];
+            if (j + kDepth < kNF) ring[j % kDepth] = Ld::raw(Pp + (int64_t)(j + kDepth) * pitch);
             float2 cur_r, cur_i, cur_w;
-            Ld::cvt(cur, cur_r, cur_i, cur_w);
+            Ld::cvt(pj, cur_r, cur_i, cur_w);
             constexpr float kZero = 0.0f;
             const float c = kZero + (float)(j - kNFHalf);
             if (j == kNFHalf - 1 || j == kNFHalf) {
@@ -408,7 +417,6 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             } else {
               acc_asym(s, cur_r, cur_i, cur_w, aa - c, ae - c, m2c);
             }
-            if (j + 1 < kNF) cur = nxt;
           }
         } else {
           float jpf = -(float)kNFHalf;  // jp as an exact float (no int-to-float per bin)

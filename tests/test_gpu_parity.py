@@ -100,6 +100,43 @@ def test_two_channel_response_gaps_levels(ae45, ae45_bank, path, pixel):
     assert np.abs(diag[0] - refs[0][2]).max() <= (0 if path != "mixed" else 1)
 
 
+def fast_chirp_bank(n, seed):
+    """Half the bank sweeps 0.01-0.05 bins per tranche (sigma = df sqrt(2/fdot) > 6: only
+    the two bins next to f_nm can need the general Fresnel form, and some tranches hold
+    a bin inside their sweep), half sweeps ~1-3 bins (sigma < 6: general bins across
+    the window, the mixed kernel's loop path)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    th = synth.two_year_bank(n, seed=seed + 1)
+    h = n // 2
+    th[0, :h] = rng.uniform(20, 30, h)
+    th[2, :h] = rng.uniform(0.022, 0.03, h)
+    th[0, h:] = rng.uniform(50, 60, n - h)
+    th[2, h:] = rng.uniform(0.05, 0.07, n - h)
+    return th
+
+
+@pytest.mark.parametrize("path,pixel", CASES)
+def test_fast_chirps_general_bins(ae45, path, pixel):
+    th = fast_chirp_bank(96, seed=31)
+    lev = [64, 8]
+    refs = [oracle.statistic(ae45.d, ae45.w, ae45.mask, th, L, ae45.dT, pn_order=1, response=1)
+            for L in lev]
+    c = ctx_for(ae45, path, pixel)
+    got, neff, diag = c.eval_statistic(th, lev, diag=True)
+    for i, (ref, rneff, _, _) in enumerate(refs):
+        assert np.count_nonzero(ref) > 0.9 * th.shape[1]
+        mx, p99 = rel_err(got[i], ref)
+        tol = fp64_tol(ae45, lev[i]) if path == "fp64" else TOL[(path, pixel)][0]
+        assert mx < tol and p99 < max(tol, TOL[(path, pixel)][1]), (lev[i], mx, p99)
+        assert np.array_equal(neff[i], rneff)
+    # both halves really exercise their branch: sigma > 6 vs < 6 at the first tranche
+    df = 1.0 / ae45.dT
+    Mc = th[0] * 4.925490947e-6
+    fdot = (96 / 5) * np.pi ** (8 / 3) * Mc ** (5 / 3) * th[2] ** (11 / 3)
+    sig = df * np.sqrt(2 / fdot)
+    assert np.all(sig[:48] > 6) and np.all(sig[48:] < 6)
+
+
 @pytest.mark.parametrize("path", ["fp64", "plain", "mixed"])
 def test_per_template_segment_counts(ae45, ae45_bank, path):
     th = ae45_bank[:, :96]
