@@ -141,18 +141,25 @@ def oracle_sample_rate(D, theta, n_seg, threads=0):
     return theta.shape[1] / dt, dt
 
 
+def kernel_source_sha1():
+    """SHA-1 over the sources the statistic kernel is compiled from."""
+    h = hashlib.sha1()
+    for f in ("tfs_eval_mixed.cu", "tfs_internal.cuh", "tfs_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2510_19047_b300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(units):
     """DRAM bytes (read + write) of one full-size statistic launch, from a committed
     one-pass ncu capture of this bench's workload; valid only while the kernel source is
     unchanged and the launch processes the same number of units. The traffic is not
     proportional to the units (the grid is read about once per launch and then served
     from L2), so a capture of another size is not rescaled."""
-    src = os.path.join(ROOT, "paper_2510_19047_b300", "csrc", "tfs_eval_mixed.cu")
     path = os.path.join(ROOT, "profiles", "k_eval_mixed_dram.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    h = kernel_source_sha1()
     if rec.get("source_sha1") != h or int(rec.get("units_per_launch", -1)) != units:
         return None
     return rec

@@ -45,6 +45,8 @@ struct tfs_ctx {
   DevBuf d_re, d_im, w_in, mask, tabD, tabF;
   // packed pixels
   DevBuf u64, w64, u32, w32, Umix;
+  DevBuf Ugrad;            // FP32 mixed-layout plane for the gradient (when Umix is not FP32)
+  bool ugrad_ok = false;
   int pitch = 0;
   int pix_built = -1;
   double su = 1.0, sw = 1.0;
@@ -138,6 +140,17 @@ double pow2_scale(double maxval) {
   // power of two that brings the largest value to ~2^14 (FP16 keeps 4x headroom)
   if (!(maxval > 0.0) || !std::isfinite(maxval)) return 1.0;
   return std::ldexp(1.0, 14 - (int)std::ceil(std::log2(maxval)));
+}
+
+MixConst mix_const(const GridDesc& g) {
+  MixConst m;
+  m.dT_hi = (float)g.dT;
+  m.dT_lo = (float)(g.dT - (double)m.dT_hi);
+  m.dTf = (float)g.dT;
+  m.sig_k = (float)(std::sqrt(2.0) * g.df);
+  m.ncomp = (float)(10.0 * g.df / g.dT);
+  m.x_hi = (float)(g.n_bins - kNFHalf);
+  return m;
 }
 
 int pack_mixed(tfs_ctx* c, cudaStream_t s) {
@@ -457,6 +470,7 @@ int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tran
                               (double*)c->w64.p, (float2*)c->u32.p, (float*)c->w32.p, c->n_sm, 0));
   r = pack_mixed(c, 0);
   if (r) return r;
+  c->ugrad_ok = false;
   CUDA_TRY(c, cudaDeviceSynchronize());
   c->has_weights = true;
   return TFS_OK;
@@ -559,6 +573,7 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
 
   EvalArgs a{};
   a.g = g;
+  a.mc = mix_const(g);
   a.response = c->opt.response;
   a.pitch = c->pitch;
   a.tabD = (const TrancheD*)c->tabD.p;
@@ -796,6 +811,21 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   const void* th = nullptr;
   if ((r = device_view(c, theta, (size_t)n_tpl * 64, c->theta, s, &th))) return r;
   if ((r = buf_ensure(c, c->tpl, (size_t)n_tpl * sizeof(TplConst)))) return r;
+  if ((r = buf_ensure(c, c->tplm, (size_t)n_tpl * sizeof(TplMix)))) return r;
+  // the FP32 pixel plane: the mixed plane itself when it is FP32, else a copy packed once
+  // per set of noise weights
+  const void* plane = c->Umix.p;
+  if (c->pix_built != TFS_PIX_F32) {
+    if (!c->ugrad_ok) {
+      const size_t npix = (size_t)c->g.n_bins * c->pitch;
+      if ((r = buf_ensure(c, c->Ugrad, npix * 32))) return r;
+      CUDA_TRY(c, launch_pack_mixed(TFS_PIX_F32, c->g, c->pitch, (const double*)c->d_re.p,
+                                    (const double*)c->d_im.p, (const double*)c->w_in.p, c->su,
+                                    c->sw, c->Ugrad.p, c->n_sm, s));
+      c->ugrad_ok = true;
+    }
+    plane = c->Ugrad.p;
+  }
   const bool dev_stat = is_device_ptr(out_stat), dev_grad = is_device_ptr(out_grad);
   double* os = out_stat;
   double* og = out_grad;
@@ -810,14 +840,14 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   c->launches = 0;
   prof_record(c, 0, s);
   CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, c->g, (TplConst*)c->tpl.p,
-                           nullptr, s));
+                           (TplMix*)c->tplm.p, s));
   prof_record(c, 1, s);
   prof_record(c, 2, s);
   const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);
-  CUDA_TRY(c, launch_grad(c->g, c->opt.response, c->opt.pn_order, (const TrancheD*)c->tabD.p,
-                          (const float2*)c->u32.p, (const float*)c->w32.p,
+  CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
+                          (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
-                          n_tpl, n_seg, scale, os, og, s));
+                          (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og, s));
   c->launches = 2;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));

@@ -42,12 +42,15 @@ cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const As
 // template, one lane per tranche. Pass A forms Z_n, N_n in shared memory; pass B
 // recomputes the track (it is never stored), the per-bin sums of the Fresnel-kernel
 // derivatives with respect to v_1, v_2 and Psi, and turns them into the tranche's
-// sensitivities to (f, fdot, phi, A, T_alpha). A reverse-mode step through the FP64
-// closed-form track adds the tranche's share to the adjoints of the 20 template
-// constants (t_c, F0, C2, P5, P3, phi0, the delay amplitudes, A+ e+, Ax ex); at the end
-// they are contracted with the constants' derivatives with respect to theta (forward
-// mode, one direction per parameter, once per template). The window position and the
-// Fresnel branch are held fixed: the almost-everywhere derivative.
+// sensitivities to (f, fdot, phi, A, T_alpha). A reverse-mode step through the track
+// (double-float values as in the mixed kernel, FP32 derivatives) gives the tranche's
+// share of the adjoints of the 20 template constants (t_c, F0, C2, P5, P3, phi0, the
+// delay amplitudes, A+ e+, Ax ex); the warp sums them per 32-tranche block and
+// accumulates in FP64, and at the end contracts them with the constants' derivatives
+// with respect to theta (FP64 forward mode, one direction per parameter, once per
+// template). Pixels come from an FP32 frequency-major plane (coalesced across lanes).
+// The window position and the Fresnel branch are held fixed: the almost-everywhere
+// derivative.
 // ---------------------------------------------------------------------------------
 namespace {
 
@@ -115,13 +118,16 @@ __device__ __forceinline__ BinW bin_w(float v1, float v2, float cps, float sps) 
 
 struct GradArgs {
   GridDesc g;
-  int response, pn_order;
-  const TrancheD* tabD;
-  const float2* u32;
-  const float* w32;
+  MixConst mc;
+  int response;
+  int pitch;            // m-pitch of the pixel plane
+  const TrancheF* tabF;
+  const float4* P;      // FP32 pixel plane [k][pitch] x {u (urA, urE, uiA, uiE), w (wA, wE, 0, 0)}
   const uint8_t* mask;
   const double* theta;  // [8][n]
-  const TplConst* tpl;  // set-up constants (ranges)
+  const TplConst* tpl;  // set-up constants (FP64; ranges)
+  const TplMix* tplm;   // the same split into double-float / FP32
+  int pn_order;
   int64_t n_tpl;
   int seg_len, n_seg;
   double scale;         // Upsilon = scale * sum |Z|^2 / N
@@ -129,141 +135,172 @@ struct GradArgs {
   double* out_grad;     // [8][n]
 };
 
-// x^(-1/8) to ~2^-21 relative (x > 0), the seed of the FP64 Newton steps below.
-__device__ __forceinline__ float seed_m18(float x) {
-  float l, r;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.125f * l));
-  return r;
-}
-
-// The track at the start of tranche m in FP64 without transcendental calls: the same
-// chirp model as the set-up (f = F0 y^3 (1 + C2 y^2), Phi = phi0 + P5 (1 - u^(5/8)) +
-// P3 (1 - u^(3/8)), y = u^(-1/8), u = 1 - t'/t_c, t' = t + n.r/c) with y from a float
-// seed and two Newton steps, and the intermediates the adjoint needs.
+// The track at the start of tranche m: the mixed kernel's double-float evaluation
+// (retarded time, u = 1 - t'/t_c, y = u^(-1/8), f, the phase in cycles), plus the FP32
+// intermediates the reverse-mode step needs.
 struct Trk {
   bool ok;
   int kc;
-  double f, fdot, phi, amp;  // phi absolute [rad]; amp = (f_src/F0)^(2/3)
-  double Tr[2], Ti[2];
-  double u, y, y2, onec, fsrc, fdsrc, d1, d2;
+  float aa, eps, sig, e2;  // f/df - k_c; fdot dT/df; df sqrt(2/fdot); sigma eps
+  float cps, sps;          // e^{i Psi}
+  float cph, sph;          // e^{i phi}
+  float P;                 // A / sqrt(2 fdot)
+  float fdot, amp, u, tpr, y, y2, onec, fsrc, fdsrc, d1, d2, ca, sa;  // tpr = t'/t_c = 1 - u
+  double ud, yd, tprd;  // u, y, t'/t_c from their double-float values (for the phase terms)
+  float Tr[2], Ti[2];      // response (no amplitude)
 };
 
-struct SrcAux {
-  double tc_inv, inv8tc;
-};
-
-__device__ __forceinline__ Trk track64(const GradArgs& a, const SrcT<double>& s, const SrcAux& x,
-                                       int m) {
+__device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int m) {
   Trk k;
   k.ok = false;
   if (!a.mask[m]) return k;
-  const TrancheD& tr = a.tabD[m];
-  double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+  const float4* cq = reinterpret_cast<const float4*>(cp);
+  const float4 c0 = ldg_nc4(cq), c1 = ldg_nc4(cq + 1), c2 = ldg_nc4(cq + 2), c3 = ldg_nc4(cq + 3);
+  const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
+  const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
+  const df Kc = {c2.x, c2.y};
+  const float dopc = c2.z, dops = c3.x;
+  const float C2 = c3.z, fd_k = c3.w;
+  const TrancheF tr = a.tabF[m];
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f;
   if (a.response) {
-    d0 = s.dop_c * tr.ca + s.dop_s * tr.sa;
-    d1 = kOmega * (s.dop_s * tr.ca - s.dop_c * tr.sa);
-    d2 = -kOmega * kOmega * d0;
+    d0 = fmaf(dopc, tr.ca_hi, dops * tr.sa_hi);
+    d1 = (float)kOmega * (dops * tr.ca_hi - dopc * tr.sa_hi);
+    d2 = -(float)(kOmega * kOmega) * d0;
   }
-  const double tp = tr.t + d0;
-  const double u = fma(-tp, x.tc_inv, 1.0);
-  if (!(u > 0.0)) return k;
-  double y = (double)seed_m18((float)u);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {  // y <- y (1 + (1 - u y^8) / 8)
-    const double y2 = y * y, y4 = y2 * y2;
-    y = fma(y * 0.125, fma(-u, y4 * y4, 1.0), y);
-  }
-  const double y2 = y * y, y3 = y2 * y;
-  const double onec = fma(s.C2, y2, 1.0);
-  const double fsrc = s.F0 * y3 * onec;
-  const double y5 = y3 * y2, y11 = y5 * y5 * y;
-  const double fdsrc = s.F0 * y11 * fma(5.0 * s.C2, y2, 3.0) * x.inv8tc;
-  const double f = fsrc * (1.0 + d1);
-  const double fdot = fdsrc * (1.0 + d1) * (1.0 + d1) + fsrc * d2;
-  if (!(fdot > 0.0)) return k;
-  const int kc = (int)ceil(f * a.g.dT);
-  if (kc - kNFHalf < 1 || kc + kNFHalf > a.g.n_bins - 1) return k;
+  const df tp = df_add_f(df{tr.t_hi, tr.t_lo}, d0);
+  const df tpr = df_mul(tp, tc_inv);
+  const df u = df_sub(df{1.0f, 0.0f}, tpr);
+  if (!(u.hi > 0.f)) return k;
+  const float y0 = pow_m18(u.hi);
+  const df y02 = two_prod(y0, y0);
+  const df p = df_mul(u, df_sqr(df_sqr(y02)));
+  const float r = __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo);
+  const df y = quick_two_sum(y0, y0 * r * 0.125f);
+  const df y2 = df_sqr(y);
+  const df y3 = df_mul(y2, y);
+  const float c2y2 = C2 * y2.hi;
+  const df onec = two_sum(1.0f, c2y2);
+  const df fs = df_mul(df_mul(F0, y3), onec);
+  const df f = df_add_f(fs, fs.hi * d1);
+  const float y2f = y2.hi, y3f = y3.hi;
+  const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
+  const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
+  const df x = df_mul(f, df{a.mc.dT_hi, a.mc.dT_lo});
+  const bool inband = x.hi > (float)kNFHalf && x.hi < a.mc.x_hi;
+  float kcf = rint_small(inband ? x.hi : 0.0f);
+  if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
+  const int kc = int_small(kcf);
+  if (!inband || !(fdot > 0.f) || kc - kNFHalf < 1 || kc + kNFHalf > a.g.n_bins - 1) return k;
   k.ok = true;
   k.kc = kc;
-  k.f = f;
+  k.aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
   k.fdot = fdot;
-  const double u58 = u * y3;  // u^(5/8)
-  k.phi = s.phi0 + s.P5 * (1.0 - u58) + s.P3 * (1.0 - u58 * y2);
-  const float cb = cbrtf((float)onec);
-  k.amp = y2 * (double)(cb * cb);
-  k.u = u;
-  k.y = y;
-  k.y2 = y2;
-  k.onec = onec;
-  k.fsrc = fsrc;
-  k.fdsrc = fdsrc;
+  k.sig = a.mc.sig_k * rsqrt_approx(fdot);
+  k.eps = fdot * a.mc.dTf * a.mc.dTf;
+  k.e2 = k.sig * k.eps;
+  const float psi = fmaf(2.0f, k.aa, k.eps);
+  __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &k.sps, &k.cps);
+  const df ph = df_sub(Kc, df_mul(df_mul(u, y3), df_add(P5, df_mul(P3, y2))));
+  float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
+  cyc = __fsub_rn(cyc, rint_small(cyc));
+  __sincosf(6.283185307f * cyc, &k.sph, &k.cph);
+  const float cb = cbrtf(onec.hi);
+  k.amp = y2f * cb * cb;
+  k.P = k.amp * rsqrt_approx(2.0f * fdot);
+  k.u = u.hi;
+  k.tpr = tpr.hi;
+  k.ud = (double)u.hi + (double)u.lo;
+  k.yd = (double)y.hi + (double)y.lo;
+  k.tprd = (double)tpr.hi + (double)tpr.lo;
+  k.y = y.hi;
+  k.y2 = y2f;
+  k.onec = onec.hi;
+  k.fsrc = fs.hi;
+  k.fdsrc = fds;
   k.d1 = d1;
   k.d2 = d2;
+  k.ca = tr.ca_hi;
+  k.sa = tr.sa_hi;
   if (a.response) {
-    double fpA = 0, fxA = 0, fpE = 0, fxE = 0;
+    const float4* pq = reinterpret_cast<const float4*>(cp->pp);
+    const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
+    const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+    const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+    float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
+#pragma unroll
     for (int q = 0; q < 6; ++q) {
-      fpA = fma(s.pp[q], tr.DA[q], fpA);
-      fxA = fma(s.px[q], tr.DA[q], fxA);
-      fpE = fma(s.pp[q], tr.DE[q], fpE);
-      fxE = fma(s.px[q], tr.DE[q], fxE);
+      fpA = fmaf(tr.DA[q], pp[q], fpA);
+      fxA = fmaf(tr.DA[q], px[q], fxA);
+      fpE = fmaf(tr.DE[q], pp[q], fpE);
+      fxE = fmaf(tr.DE[q], px[q], fxE);
     }
     k.Tr[0] = fpA;
     k.Ti[0] = -fxA;
     k.Tr[1] = fpE;
     k.Ti[1] = -fxE;
   } else {
-    k.Tr[0] = k.Tr[1] = 1.0;
-    k.Ti[0] = k.Ti[1] = 0.0;
+    k.Tr[0] = k.Tr[1] = 1.0f;
+    k.Ti[0] = k.Ti[1] = 0.0f;
   }
   return k;
 }
 
-// e^{i phi} with phi in FP64 reduced to cycles first; FP32 sine and cosine.
-__device__ __forceinline__ void phase_factor(double phi, float& s, float& c) {
-  double cyc = phi * (0.5 / kPi);
-  cyc -= rint(cyc);
-  __sincosf(6.283185307f * (float)cyc, &s, &c);
-}
+// FP32 copies of the template constants the reverse-mode step uses (radians for P5, P3),
+// and FP64 ones for its phase terms.
+struct SrcF {
+  float tc, tc_inv, inv8tc, F0, C2, P5, P3;
+  double tc_inv_d, P5d, P3d;
+};
 
 // Reverse-mode step of the track for one tranche: given the tranche's sensitivities
-// of Upsilon to (f, fdot, phi, ln A, T_alpha), add its contribution to the adjoints G
-// of the template constants (tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6]).
-__device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcT<double>& s,
-                                              const SrcAux& x, const Trk& k, int m, double cf,
-                                              double cfd, double cphi, double cP,
-                                              const double cTr[2], const double cTi[2],
-                                              double G[kSrcFields]) {
-  const double op1 = 1.0 + k.d1;
-  const double g_fsrc = cf * op1 + cfd * k.d2;
-  const double g_fdsrc = cfd * op1 * op1;
-  const double g_d1 = cf * k.fsrc + 2.0 * cfd * k.fdsrc * op1;
-  const double g_d2 = cfd * k.fsrc;
-  const double y = k.y, y2 = k.y2, y3 = y2 * y, y5 = y3 * y2;
-  const double y10 = y5 * y5;
-  // f_src = F0 y^3 onec, fdot_src = F0 y^11 (3 + 5 C2 y^2) / (8 t_c), ln A = 2 ln y + (2/3) ln onec
-  const double dfs_dy = s.F0 * y2 * fma(5.0 * s.C2, y2, 3.0);
-  const double dfd_dy = s.F0 * y10 * fma(65.0 * s.C2, y2, 33.0) * x.inv8tc;
-  const double dlnA_dy = 2.0 / y + (4.0 / 3.0) * s.C2 * y / k.onec;
-  const double g_y = g_fsrc * dfs_dy + g_fdsrc * dfd_dy + cP * dlnA_dy;
-  G[2] += g_fsrc * s.F0 * y5 + g_fdsrc * s.F0 * y10 * y3 * 5.0 * x.inv8tc +
-          cP * (2.0 / 3.0) * y2 / k.onec;
-  if (s.F0 != 0.0) G[1] += (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) / s.F0;
-  const double u58 = k.u * y3;
-  G[3] += cphi * (1.0 - u58);
-  G[4] += cphi * (1.0 - u58 * y2);
-  G[5] += cphi;
-  const double g_u = -g_y * y / (8.0 * k.u) - cphi * (0.625 * s.P5 * y3 + 0.375 * s.P3 * y5);
-  G[0] += (g_u * (1.0 - k.u) - g_fdsrc * k.fdsrc) * x.tc_inv;  // du/dtc = (1 - u)/tc
+// of Upsilon to (f, fdot, phi, ln A, T_alpha), its contribution to the adjoints g of
+// the template constants (tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6]). The phase's
+// shares of the t_c, P5 and P3 adjoints, gph = (tc, P5, P3), are formed in FP64: they
+// are large and cancel each other in the final contraction (the phase's leading term
+// 2 pi f0 t does not depend on M_c or eta), so FP32 rounding there would dominate.
+__device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, const Trk& k,
+                                              const TrancheF& tr, float cf, float cfd, float cphi,
+                                              float cP, const float cTr[2], const float cTi[2],
+                                              float g[kSrcFields], double gph[3]) {
+  const float op1 = 1.0f + k.d1;
+  const float g_fsrc = cf * op1 + cfd * k.d2;
+  const float g_fdsrc = cfd * op1 * op1;
+  const float g_d1 = cf * k.fsrc + 2.0f * cfd * k.fdsrc * op1;
+  const float g_d2 = cfd * k.fsrc;
+  const float y = k.y, y2 = k.y2, y3 = y2 * y, y5 = y3 * y2, y10 = y5 * y5;
+  const float dfs_dy = s.F0 * y2 * fmaf(5.0f * s.C2, y2, 3.0f);
+  const float dfd_dy = s.F0 * y10 * fmaf(65.0f * s.C2, y2, 33.0f) * s.inv8tc;
+  const float ionec = 1.0f / k.onec;
+  const float dlnA_dy = 2.0f / y + (4.0f / 3.0f) * s.C2 * y * ionec;
+  const float g_y = g_fsrc * dfs_dy + g_fdsrc * dfd_dy + cP * dlnA_dy;
+  g[2] = g_fsrc * s.F0 * y5 + g_fdsrc * s.F0 * y10 * y3 * 5.0f * s.inv8tc +
+         cP * (2.0f / 3.0f) * y2 * ionec;
+  g[1] = s.F0 != 0.0f ? (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) / s.F0 : 0.0f;
+  // phase: Phi = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u^(5/8) = u y^3
+  const double cphd = cphi;
+  const double y2d = k.yd * k.yd, y3d = y2d * k.yd;
+  const double u58 = k.ud * y3d;
+  gph[1] = cphd * (1.0 - u58);
+  gph[2] = cphd * (1.0 - u58 * y2d);
+  const double gu_ph = -cphd * (0.625 * s.P5d * y3d + 0.375 * s.P3d * y3d * y2d);
+  gph[0] = gu_ph * k.tprd * s.tc_inv_d;  // du/dtc = t'/tc^2
+  g[3] = 0.0f;
+  g[4] = 0.0f;
+  g[5] = cphi;
+  const float g_u = -g_y * y / (8.0f * k.u);
+  g[0] = (g_u * k.tpr - g_fdsrc * k.fdsrc) * s.tc_inv;
+  const float g_u_all = g_u + (float)gu_ph;  // for the delay amplitudes
+  for (int q = 6; q < kSrcFields; ++q) g[q] = 0.0f;
   if (a.response) {
-    const TrancheD& tr = a.tabD[m];
-    const double g_tp = -g_u * x.tc_inv;
-    const double w2 = kOmega * kOmega;
-    G[6] += g_tp * tr.ca - g_d1 * kOmega * tr.sa - g_d2 * w2 * tr.ca;
-    G[7] += g_tp * tr.sa + g_d1 * kOmega * tr.ca - g_d2 * w2 * tr.sa;
+    const float g_tp = -g_u_all * s.tc_inv;
+    const float w1 = (float)kOmega, w2 = (float)(kOmega * kOmega);
+    g[6] = g_tp * k.ca - g_d1 * w1 * k.sa - g_d2 * w2 * k.ca;
+    g[7] = g_tp * k.sa + g_d1 * w1 * k.ca - g_d2 * w2 * k.sa;
+#pragma unroll
     for (int q = 0; q < 6; ++q) {
-      G[8 + q] += cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
-      G[14 + q] -= cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q];
+      g[8 + q] = cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
+      g[14 + q] = -(cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q]);
     }
   }
 }
@@ -277,17 +314,26 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   const int64_t i = (int64_t)blockIdx.x * kGradWarps + warp;
   if (i >= a.n_tpl) return;  // whole warp leaves together
   float4* seg = s_seg + (size_t)warp * a.n_seg;
-  const GridDesc g = a.g;
-  const int nch = g.n_chan;
+  const int nch = a.g.n_chan;
+  const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
   double th[8];
   for (int p = 0; p < 8; ++p) th[p] = a.theta[(int64_t)p * a.n_tpl + i];
   const TplConst tc = a.tpl[i];
-  const SrcT<double> s = source_of<double>(th, a.pn_order);
-  SrcAux xa;
-  xa.tc_inv = 1.0 / s.tc;
-  xa.inv8tc = 0.125 * xa.tc_inv;
+  const TplMix* cp = a.tplm + i;
+  SrcF sf;
+  sf.tc = (float)tc.tc;
+  sf.tc_inv = (float)(1.0 / tc.tc);
+  sf.inv8tc = (float)(0.125 / tc.tc);
+  sf.F0 = (float)tc.F0;
+  sf.C2 = (float)tc.C2;
+  sf.P5 = (float)tc.P5;
+  sf.P3 = (float)tc.P3;
+  sf.tc_inv_d = 1.0 / tc.tc;
+  sf.P5d = tc.P5;
+  sf.P3d = tc.P3;
   for (int q = lane; q < a.n_seg; q += 32) seg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // directional derivatives of the template constants: lane p < 8 takes direction p
+  // derivatives of the template constants with respect to theta: lane p < 8 takes
+  // direction p (FP64 forward mode, once per template)
   if (lane < 8) {
     D1 thd[8];
     for (int p = 0; p < 8; ++p) thd[p] = mk(th[p], p == lane ? 1.0 : 0.0);
@@ -314,37 +360,30 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     const bool inr = m < tc.m_hi;
     float Zr = 0.f, Zi = 0.f, Nn = 0.f;
     if (inr) {
-      const Trk L = track64(a, s, xa, m);
+      const Trk L = track_df(a, cp, m);
       if (L.ok) {
-        const double x = L.f * g.dT;
-        const float aa = (float)(x - (double)L.kc);
-        const float sig = (float)(g.df * sqrt(2.0 / L.fdot));
-        const float e2 = (float)(sqrt(2.0 * L.fdot) * g.dT);
-        float sps, cps;
-        sincospif((float)(2.0 * (x - L.kc) + L.fdot * g.dT * g.dT), &sps, &cps);
         float zr[2] = {0, 0}, zi[2] = {0, 0}, nn[2] = {0, 0};
+        const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
         for (int j = 0; j < kNF; ++j) {
-          const int k = L.kc - kNFHalf + j;
-          const float v1 = (aa - (float)(j - kNFHalf)) * sig;
-          const BinW b = bin_w<false>(v1, v1 + e2, cps, sps);
+          const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
+          const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+          const BinW b = bin_w<false>(v1, v1 + L.e2, L.cps, L.sps);
           const float ww = b.wr * b.wr + b.wi * b.wi;
-          for (int c = 0; c < nch; ++c) {
-            const int64_t px = ((int64_t)c * g.n_tranche + m) * g.n_bins + k;
-            const float2 u = a.u32[px];
-            zr[c] += u.x * b.wr + u.y * b.wi;
-            zi[c] += u.x * b.wi - u.y * b.wr;
-            nn[c] += a.w32[px] * ww;
-          }
+          zr[0] += u.x * b.wr + u.z * b.wi;
+          zi[0] += u.x * b.wi - u.z * b.wr;
+          nn[0] += w.x * ww;
+          zr[1] += u.y * b.wr + u.w * b.wi;
+          zi[1] += u.y * b.wi - u.w * b.wr;
+          nn[1] += w.y * ww;
         }
-        const float P = (float)(L.amp / sqrt(2.0 * L.fdot));
-        float sph, cph;
-        phase_factor(L.phi, sph, cph);
-        for (int c = 0; c < nch; ++c) {
-          const float ar = (float)L.Tr[c] * zr[c] - (float)L.Ti[c] * zi[c];
-          const float ai = (float)L.Tr[c] * zi[c] + (float)L.Ti[c] * zr[c];
-          Zr += P * (ar * (float)cph - ai * (float)sph);
-          Zi += P * (ar * (float)sph + ai * (float)cph);
-          Nn += P * P * (float)(L.Tr[c] * L.Tr[c] + L.Ti[c] * L.Ti[c]) * nn[c];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (c >= nch) break;
+          const float ar = L.Tr[c] * zr[c] - L.Ti[c] * zi[c];
+          const float ai = L.Tr[c] * zi[c] + L.Ti[c] * zr[c];
+          Zr += L.P * (ar * L.cph - ai * L.sph);
+          Zi += L.P * (ar * L.sph + ai * L.cph);
+          Nn += L.P * L.P * (L.Tr[c] * L.Tr[c] + L.Ti[c] * L.Ti[c]) * nn[c];
         }
       }
     }
@@ -378,7 +417,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     if (v.z > 0.f) {
       const double zz = (double)v.x * v.x + (double)v.y * v.y;
       ups += a.scale * zz / v.z;
-      o.x = (float)(2.0 * a.scale * v.x / v.z);   // lambda = 2 s conj(Z)/N
+      o.x = (float)(2.0 * a.scale * v.x / v.z);  // lambda = 2 s conj(Z)/N
       o.y = (float)(-2.0 * a.scale * v.y / v.z);
       o.z = (float)(-a.scale * zz / ((double)v.z * v.z));  // mu
     }
@@ -389,122 +428,130 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   __syncwarp();
 
   // ---- pass B: adjoints of the template constants ----
+  // per 32-tranche block the lanes' FP32 contributions are summed over the warp and
+  // accumulated in FP64 (every lane holds the same totals)
   double G[kSrcFields];
   for (int k = 0; k < kSrcFields; ++k) G[k] = 0.0;
+  const float twopidT = (float)(2.0 * kPi * a.g.dT), pidT2 = (float)(kPi * a.g.dT * a.g.dT);
   for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
     const int m = m0 + lane;
-    if (m >= tc.m_hi) continue;
-    const Trk L = track64(a, s, xa, m);
-    if (!L.ok) continue;
-    const float4 lm = seg[m / a.seg_len];
-    const double lr = lm.x, li = lm.y, mu = lm.z;
-    const double x = L.f * g.dT;
-    const float aa = (float)(x - (double)L.kc);
-    const float sig = (float)(g.df * sqrt(2.0 / L.fdot));
-    const float e2 = (float)(sqrt(2.0 * L.fdot) * g.dT);
-    float sps, cps;
-    sincospif((float)(2.0 * (x - L.kc) + L.fdot * g.dT * g.dT), &sps, &cps);
-    // per channel: complex sums S0..S3, S1v, S2v and real sums R0..R3, R1v, R2v
-    float S[2][6][2], R[2][6];
-    for (int c = 0; c < 2; ++c)
-      for (int q = 0; q < 6; ++q) {
-        S[c][q][0] = S[c][q][1] = 0.f;
-        R[c][q] = 0.f;
-      }
-    for (int j = 0; j < kNF; ++j) {
-      const int k = L.kc - kNFHalf + j;
-      const float v1 = (aa - (float)(j - kNFHalf)) * sig;
-      const BinW b = bin_w<true>(v1, v1 + e2, cps, sps);
-      const float X[6][2] = {{b.wr, b.wi}, {b.a1r, b.a1i}, {b.a2r, b.a2i}, {b.a3r, b.a3i},
-                             {b.a1r * v1, b.a1i * v1}, {b.a2r * v1, b.a2i * v1}};
-      const float r1 = 2.f * (b.wr * b.a1r + b.wi * b.a1i);
-      const float r2 = 2.f * (b.wr * b.a2r + b.wi * b.a2i);
-      const float r3 = 2.f * (b.wr * b.a3r + b.wi * b.a3i);
-      const float Rx[6] = {b.wr * b.wr + b.wi * b.wi, r1, r2, r3, r1 * v1, r2 * v1};
-      for (int c = 0; c < nch; ++c) {
-        const int64_t px = ((int64_t)c * g.n_tranche + m) * g.n_bins + k;
-        const float2 u = a.u32[px];
-        const float w = a.w32[px];
+    float gl[kSrcFields];
+    for (int k = 0; k < kSrcFields; ++k) gl[k] = 0.0f;
+    double gph[3] = {0.0, 0.0, 0.0};
+    Trk L;
+    L.ok = false;
+    if (m < tc.m_hi) L = track_df(a, cp, m);
+    if (L.ok) {
+      const float4 lm = seg[m / a.seg_len];
+      const float lr = lm.x, li = lm.y, mu = lm.z;
+      // per channel: complex sums S0..S3, S1v, S2v and real sums R0..R3, R1v, R2v
+      float S[2][6][2], R[2][6];
+      for (int c = 0; c < 2; ++c)
         for (int q = 0; q < 6; ++q) {
-          S[c][q][0] += u.x * X[q][0] + u.y * X[q][1];
-          S[c][q][1] += u.x * X[q][1] - u.y * X[q][0];
-          R[c][q] += w * Rx[q];
+          S[c][q][0] = S[c][q][1] = 0.f;
+          R[c][q] = 0.f;
+        }
+      const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
+      for (int j = 0; j < kNF; ++j) {
+        const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
+        const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+        const BinW b = bin_w<true>(v1, v1 + L.e2, L.cps, L.sps);
+        const float X[6][2] = {{b.wr, b.wi}, {b.a1r, b.a1i}, {b.a2r, b.a2i}, {b.a3r, b.a3i},
+                               {b.a1r * v1, b.a1i * v1}, {b.a2r * v1, b.a2i * v1}};
+        const float r1 = 2.f * (b.wr * b.a1r + b.wi * b.a1i);
+        const float r2 = 2.f * (b.wr * b.a2r + b.wi * b.a2i);
+        const float r3 = 2.f * (b.wr * b.a3r + b.wi * b.a3i);
+        const float Rx[6] = {b.wr * b.wr + b.wi * b.wi, r1, r2, r3, r1 * v1, r2 * v1};
+        const float ur[2] = {u4.x, u4.y}, ui[2] = {u4.z, u4.w}, wc[2] = {w4.x, w4.y};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            S[c][q][0] += ur[c] * X[q][0] + ui[c] * X[q][1];
+            S[c][q][1] += ur[c] * X[q][1] - ui[c] * X[q][0];
+            R[c][q] += wc[c] * Rx[q];
+          }
         }
       }
+      // sensitivities of this tranche's dUpsilon to (f, fdot, phi, A, T_alpha)
+      const float P = L.P;
+      const float Er = P * L.cph, Ei = P * L.sph;  // E = P e^{i phi}
+      const float rt = L.sig * a.mc.dTf;  // sqrt(2 / fdot) = sigma / df
+      const float ifd2 = 0.5f / L.fdot;
+      const float e2 = L.e2;
+      float Zmr = 0, Zmi = 0, Nm = 0, cf = 0, cfd = 0, cTr[2] = {0, 0}, cTi[2] = {0, 0};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nch) break;
+        const float Qr = Er * S[c][0][0] - Ei * S[c][0][1];
+        const float Qi = Er * S[c][0][1] + Ei * S[c][0][0];
+        const float zr = L.Tr[c] * Qr - L.Ti[c] * Qi, zi = L.Tr[c] * Qi + L.Ti[c] * Qr;
+        Zmr += zr;
+        Zmi += zi;
+        const float T2 = L.Tr[c] * L.Tr[c] + L.Ti[c] * L.Ti[c];
+        Nm += T2 * P * P * R[c][0];
+        // dT terms: Re(lambda dT Q) + mu P^2 R0 d|T|^2
+        cTr[c] = (lr * Qr - li * Qi) + mu * 2.0f * L.Tr[c] * P * P * R[c][0];
+        cTi[c] = -(lr * Qi + li * Qr) + mu * 2.0f * L.Ti[c] * P * P * R[c][0];
+        // dS0 = K1 df + K2 dfdot (complex), dR0 likewise (real)
+        const float K1r = (S[c][1][0] + S[c][2][0]) * rt + S[c][3][0] * twopidT;
+        const float K1i = (S[c][1][1] + S[c][2][1]) * rt + S[c][3][1] * twopidT;
+        const float K2r = (-S[c][4][0] - S[c][5][0] + e2 * S[c][2][0]) * ifd2 + S[c][3][0] * pidT2;
+        const float K2i = (-S[c][4][1] - S[c][5][1] + e2 * S[c][2][1]) * ifd2 + S[c][3][1] * pidT2;
+        const float TEr = L.Tr[c] * Er - L.Ti[c] * Ei, TEi = L.Tr[c] * Ei + L.Ti[c] * Er;
+        const float a1r = TEr * K1r - TEi * K1i, a1i = TEr * K1i + TEi * K1r;
+        const float a2r = TEr * K2r - TEi * K2i, a2i = TEr * K2i + TEi * K2r;
+        cf += lr * a1r - li * a1i;
+        cfd += lr * a2r - li * a2i;
+        const float RK1 = (R[c][1] + R[c][2]) * rt + R[c][3] * twopidT;
+        const float RK2 = (-R[c][4] - R[c][5] + e2 * R[c][2]) * ifd2 + R[c][3] * pidT2;
+        cf += mu * T2 * P * P * RK1;
+        cfd += mu * T2 * P * P * RK2;
+      }
+      const float cphi = -(lr * Zmi + li * Zmr);               // Re(i lambda z)
+      const float cP = (lr * Zmr - li * Zmi) + 2.0f * mu * Nm;  // coefficient of dP/P
+      cfd += -cP * ifd2;
+      track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
     }
-    // sensitivities of this tranche's dUpsilon to (f, fdot, phi, A, T_alpha)
-    const double P = L.amp / sqrt(2.0 * L.fdot);
-    float sphf, cphf;
-    phase_factor(L.phi, sphf, cphf);
-    const double sph = sphf, cph = cphf;
-    const double Er = P * cph, Ei = P * sph;  // E = P e^{i phi}
-    const double rt = sqrt(2.0 / L.fdot), ifd2 = 0.5 / L.fdot;
-    const double twopidT = 2.0 * kPi * g.dT, pidT2 = kPi * g.dT * g.dT;
-    double Zmr = 0, Zmi = 0, Nm = 0, cf = 0, cfd = 0, cTr[2] = {0, 0}, cTi[2] = {0, 0};
-    for (int c = 0; c < nch; ++c) {
-      // Q = E S0; z = T Q
-      const double Qr = Er * S[c][0][0] - Ei * S[c][0][1];
-      const double Qi = Er * S[c][0][1] + Ei * S[c][0][0];
-      const double zr = L.Tr[c] * Qr - L.Ti[c] * Qi, zi = L.Tr[c] * Qi + L.Ti[c] * Qr;
-      Zmr += zr;
-      Zmi += zi;
-      const double T2 = L.Tr[c] * L.Tr[c] + L.Ti[c] * L.Ti[c];
-      const double n = T2 * P * P * R[c][0];
-      Nm += n;
-      // dT terms: Re(lambda dT Q) + mu P^2 R0 d|T|^2
-      cTr[c] = (lr * Qr - li * Qi) + mu * 2.0 * L.Tr[c] * P * P * R[c][0];
-      cTi[c] = -(lr * Qi + li * Qr) + mu * 2.0 * L.Ti[c] * P * P * R[c][0];
-      // dS0 = K1 df + K2 dfdot (complex), dR0 likewise (real)
-      double K1r = (S[c][1][0] + S[c][2][0]) * rt + S[c][3][0] * twopidT;
-      double K1i = (S[c][1][1] + S[c][2][1]) * rt + S[c][3][1] * twopidT;
-      double K2r = (-S[c][4][0] - S[c][5][0] + e2 * S[c][2][0]) * ifd2 + S[c][3][0] * pidT2;
-      double K2i = (-S[c][4][1] - S[c][5][1] + e2 * S[c][2][1]) * ifd2 + S[c][3][1] * pidT2;
-      // T E K
-      const double TEr = L.Tr[c] * Er - L.Ti[c] * Ei, TEi = L.Tr[c] * Ei + L.Ti[c] * Er;
-      const double a1r = TEr * K1r - TEi * K1i, a1i = TEr * K1i + TEi * K1r;
-      const double a2r = TEr * K2r - TEi * K2i, a2i = TEr * K2i + TEi * K2r;
-      cf += lr * a1r - li * a1i;
-      cfd += lr * a2r - li * a2i;
-      const double RK1 = (R[c][1] + R[c][2]) * rt + R[c][3] * twopidT;
-      const double RK2 = (-R[c][4] - R[c][5] + e2 * R[c][2]) * ifd2 + R[c][3] * pidT2;
-      cf += mu * T2 * P * P * RK1;
-      cfd += mu * T2 * P * P * RK2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double v = gph[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
+      G[k == 0 ? 0 : k + 2] += v;  // t_c, P5, P3
     }
-    const double cphi = -(lr * Zmi + li * Zmr);       // Re(i lambda z)
-    const double cP = (lr * Zmr - li * Zmi) + 2.0 * mu * Nm;  // coefficient of dP/P
-    cfd += -cP * ifd2;
-    track_adjoint(a, s, xa, L, m, cf, cfd, cphi, cP, cTr, cTi, G);
+#pragma unroll
+    for (int k = 0; k < kSrcFields; ++k) {
+      float v = gl[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
+      G[k] += (double)v;
+    }
   }
   // d Upsilon / d theta_p = sum_k G_k d(constant_k)/d theta_p
-  double grad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int k = 0; k < kSrcFields; ++k) {
-    double v = G[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
-    for (int p = 0; p < 8; ++p) grad[p] = fma(v, s_dsrc[warp][p][k], grad[p]);
-  }
   if (lane < 8) {
-    double v = grad[0];
-    for (int p = 1; p < 8; ++p)
-      if (lane == p) v = grad[p];
+    double v = 0.0;
+    for (int k = 0; k < kSrcFields; ++k) v = fma(G[k], s_dsrc[warp][lane][k], v);
     a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
   }
 }
 
-cudaError_t launch_grad(const GridDesc& g, int response, int pn_order, const TrancheD* tabD,
-                        const float2* u32, const float* w32, const uint8_t* mask,
-                        const double* theta, const TplConst* tpl, int64_t n, int n_seg,
-                        double scale, double* out_stat, double* out_grad, cudaStream_t s) {
+cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int pn_order,
+                        int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
+                        const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
+                        int n_seg, double scale, double* out_stat, double* out_grad,
+                        cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   GradArgs a;
   a.g = g;
+  a.mc = mc;
   a.response = response;
-  a.pn_order = pn_order;
-  a.tabD = tabD;
-  a.u32 = u32;
-  a.w32 = w32;
+  a.pitch = pitch;
+  a.tabF = tabF;
+  a.P = P;
   a.mask = mask;
   a.theta = theta;
   a.tpl = tpl;
+  a.tplm = tplm;
+  a.pn_order = pn_order;
   a.n_tpl = n;
   a.n_seg = n_seg;
   a.seg_len = g.n_tranche / n_seg;

@@ -155,6 +155,57 @@ __device__ __forceinline__ df df_sqr(df x) {
 }
 __device__ __forceinline__ float df_to_f(df x) { return __fadd_rn(x.hi, x.lo); }
 
+// ---------------------------------------------------------------------------------
+// Single-instruction FP32 helpers shared by the mixed and gradient kernels.
+// ---------------------------------------------------------------------------------
+// Rounding to an integer on the FMA pipe (the conversion units are slow on this part):
+// exact round-half-even for |x| < 2^22, and the integer value of such a float.
+__device__ __forceinline__ float rint_small(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+__device__ __forceinline__ int int_small(float x) {
+  return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
+// Non-coherent 16-byte load kept in place (volatile: not hoisted out of the tranche
+// loop, so its result does not occupy registers across it).
+__device__ __forceinline__ float4 ldg_nc4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// x^(-1/8) to ~2^-21 relative from the hardware base-2 logarithm and exponential
+// (x > 0); the seed of a Newton step.
+__device__ __forceinline__ float pow_m18(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.125f * l));
+  return r;
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  df r;
+  r.hi = __fmul_rn(a, b);
+  r.lo = __fmaf_rn(a, b, -r.hi);
+  return r;
+}
+
+// The hardware reciprocal and reciprocal square root (one MUFU instruction each, ~1 ulp;
+// subnormal inputs flush to zero, which the callers never pass).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Host/device status word written by checked kernels.
 enum DeviceErr : int { kDevOk = 0, kDevBadIndex = 1 };
 

@@ -6,8 +6,19 @@
 namespace tfs {
 
 // Everything an evaluation kernel needs, passed by value.
+// FP32 forms of grid constants for the mixed kernel, rounded once on the host (the
+// kernel then needs no FP64 instruction, even where it re-derives a value per tranche).
+struct MixConst {
+  float dT_hi, dT_lo;  // dT as a double-float
+  float dTf;           // (float) dT
+  float sig_k;         // sqrt(2) df: sigma = sig_k / sqrt(fdot)
+  float ncomp;         // 10 df / dT: fdot above it counts as non-compact
+  float x_hi;          // n_bins - 10: window centres below it are in band
+};
+
 struct EvalArgs {
   GridDesc g;
+  MixConst mc;
   int response;
   int pitch;                    // m-dimension pitch of the mixed planes
   const TrancheD* tabD;         // [N_t]
@@ -65,9 +76,10 @@ struct AscentParams {
 cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const AscentParams& p,
                           cudaStream_t s);
 // Adjoint gradient at one N_seg: out_stat [n], out_grad [8][n] (device pointers).
-cudaError_t launch_grad(const GridDesc& g, int response, int pn_order, const TrancheD* tabD,
-                        const float2* u32, const float* w32, const uint8_t* mask,
-                        const double* theta, const TplConst* tpl, int64_t n, int n_seg,
-                        double scale, double* out_stat, double* out_grad, cudaStream_t s);
+cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int pn_order,
+                        int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
+                        const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
+                        int n_seg, double scale, double* out_stat, double* out_grad,
+                        cudaStream_t s);
 
 }  // namespace tfs
