@@ -178,7 +178,6 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   const float dTf = (float)g.dT;
   const float sig_k = (float)(sqrt(2.0) * g.df);       // sigma = df sqrt(2/fdot)
   const float ncomp = (float)(10.0 * g.df / g.dT);      // fdot > 10 df / dT: non-compact
-  const df one = {1.0f, 0.0f};
 
   for (;;) {
     int t = 0;
@@ -240,8 +239,9 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           d1 = (float)kOmega * (dops.hi * tr.ca_hi - dopc.hi * tr.sa_hi);
           d2 = -(float)(kOmega * kOmega) * d0;
         }
-        const df tp = df_add_f(tt, d0);
-        const df u = df_sub(one, df_mul(tp, tc_inv));  // 1 - t'/t_c
+        // |t| >= |d0| except at t = 0, where the quick sum is exact as well
+        const df tp = quick_add_f(tt, d0);
+        const df u = one_minus(df_mul(tp, tc_inv));  // 1 - t'/t_c
         if (!(u.hi > 0.f)) {
           act = false;
         } else {
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           const float c2y2 = C2 * y2.hi;
           const df onec = two_sum(1.0f, c2y2);
           const df fs = df_mul(df_mul(F0, y3), onec);  // source-frame frequency
-          const df f = df_add_f(fs, fs.hi * d1);        // detector frame: f (1 + dt'/dt - 1)
+          const df f = quick_add_f(fs, fs.hi * d1);     // detector frame: f (1 + dt'/dt - 1)
           const float y2f = y2.hi, y3f = y3.hi;
           const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
           const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;

@@ -154,6 +154,16 @@ __device__ __forceinline__ df df_sqr(df x) {
   return quick_two_sum(p, e);
 }
 __device__ __forceinline__ float df_to_f(df x) { return __fadd_rn(x.hi, x.lo); }
+// x + b for |x.hi| >= |b| (or x.hi = 0): one quick two-sum in place of a two-sum
+__device__ __forceinline__ df quick_add_f(df x, float b) {
+  df s = quick_two_sum(x.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+// 1 - x for 0 <= x.hi <= 1 (for larger x the sign of the result is still right)
+__device__ __forceinline__ df one_minus(df x) {
+  df s = quick_two_sum(1.0f, -x.hi);
+  return quick_two_sum(s.hi, __fsub_rn(s.lo, x.lo));
+}
 
 // ---------------------------------------------------------------------------------
 // Single-instruction FP32 helpers shared by the mixed and gradient kernels.
