@@ -17,5 +17,5 @@ f = (1/2pi) dPhi/dt, the Newtonian limit and the tensor invariants).
 from .build import load_library, build  # noqa: F401
 from .api import (  # noqa: F401
     statistic, gradient, segments, fresnel, tranche_ft, source_constants, track, response,
-    detector_tensors, polarisation, max_threads,
+    detector_tensors, polarisation, max_threads, response_tdi, spacecraft_offsets,
 )

@@ -18,6 +18,7 @@ PN_NEWTONIAN = 0
 PN_1PN = 1
 RESP_NONE = 0
 RESP_LW = 1
+RESP_TDI = 2
 FRESNEL_PAPER = 0
 FRESNEL_EXACT = 1
 
@@ -53,6 +54,10 @@ def _lib():
                                      ctypes.c_double, _D, _D, _D, _D, _D, _U8]
         lib.oracle_response.restype = None
         lib.oracle_response.argtypes = [_D, _D, ctypes.c_int64, ctypes.c_int, _D, _D]
+        lib.oracle_response_tdi.restype = None
+        lib.oracle_response_tdi.argtypes = [_D, _D, _D, ctypes.c_int64, ctypes.c_int, _D, _D]
+        lib.oracle_spacecraft_offsets.restype = None
+        lib.oracle_spacecraft_offsets.argtypes = [ctypes.c_double, _D]
         lib.oracle_detector_tensors.restype = None
         lib.oracle_detector_tensors.argtypes = [ctypes.c_double, _D, _D]
         lib.oracle_polarisation.restype = None
@@ -196,6 +201,24 @@ def response(theta8, t, n_chan=2):
     im = np.empty((n_chan, t.size))
     _lib().oracle_response(_p(th), _p(t), t.size, int(n_chan), _p(re), _p(im))
     return re + 1j * im
+
+
+def response_tdi(theta8, t, f, n_chan=2):
+    """TDI-1.5 transfer T_alpha(t, f) of the A/E channels, complex [n_chan, n]."""
+    th = np.ascontiguousarray(theta8, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64).ravel()
+    f = np.ascontiguousarray(np.broadcast_to(f, t.shape), dtype=np.float64)
+    re = np.empty((n_chan, t.size))
+    im = np.empty((n_chan, t.size))
+    _lib().oracle_response_tdi(_p(th), _p(t), _p(f), t.size, int(n_chan), _p(re), _p(im))
+    return re + 1j * im
+
+
+def spacecraft_offsets(t):
+    """Spacecraft positions relative to the guiding centre [light-s], [3, 3]."""
+    p = np.empty(9)
+    _lib().oracle_spacecraft_offsets(float(t), _p(p))
+    return p.reshape(3, 3)
 
 
 def detector_tensors(t):

@@ -40,6 +40,8 @@
 //   * response (response 1): long-wavelength A/E channels of a rigid LISA
 //     constellation on a circular 1 AU orbit; t' = t + n.r(t)/c; f_nm and fdot_nm
 //     include the Doppler factors dt'/dt and d2t'/dt2. response 0: T = 1, t' = t.
+//     response 2: the TDI-1.5 A/E transfer of the same rigidly rotating constellation
+//     with 2.5e9 m arms, evaluated at (t_nm, f_nm) (tdi_transfer below).
 //   * the window centre printed as ceil(f / f_nm) delta f is read as
 //     k_c = ceil(f_nm / delta f); bins k_c-10 .. k_c+10.
 //   * a tranche is active iff its mask is set, t'_nm < t_c, fdot_nm > 0 and the
@@ -66,6 +68,7 @@ constexpr double GMSUN_S = 4.925490947e-6;  // G M_sun / c^3 [s]
 constexpr double AU_S = 499.004784;         // 1 AU / c [s]
 constexpr double YEAR_S = 31557600.0;       // Julian year [s]
 constexpr double OMEGA_ORB = 2.0 * PI / YEAR_S;
+constexpr double ARM_S = 2.5e9 / 299792458.0;  // constellation arm length L / c [s]
 constexpr int NF = 21;                      // N_F, bins per tranche
 constexpr int NF_HALF = 10;
 constexpr int NPAR = 8;  // (M_c, eta, f_0, phi_0, lambda, beta, psi, iota)
@@ -322,6 +325,7 @@ struct Source {
   R ep[3][3], ex[3][3];  // e+ = p p - q q, ex = p q + q p
   R Ap, Ax;              // (1 + cos^2 iota)/2, cos iota
   R dop_c, dop_s;        // (R/c) cos(beta) cos(lambda), (R/c) cos(beta) sin(lambda)
+  R nhat[3];             // direction to the source (cos b cos l, cos b sin l, sin b)
 };
 
 // 1PN TaylorT3 coefficients (GW phase = 2 x orbital phase; Theta = eta (t_c - t)/(5M)):
@@ -393,6 +397,9 @@ static Source<R> make_source(const R th[NPAR], int pn_order) {
   s.Ax = ci;
   s.dop_c = AU_S * cb * cl;
   s.dop_s = AU_S * cb * sl;
+  s.nhat[0] = cb * cl;
+  s.nhat[1] = cb * sl;
+  s.nhat[2] = sb;
   return s;
 }
 
@@ -454,6 +461,79 @@ static void response(const Source<R>& s, double t, int n_chan, Cx<R> T[2]) {
     T[c].re = Fp * s.Ap;
     T[c].im = -(Fx * s.Ax);
   }
+}
+
+// Spacecraft positions relative to the guiding centre [light-seconds] at detector time
+// t: the vertices of the same rotating triangle as detector_tensors, side ARM_S.
+static void spacecraft_offsets(double t, double p[3][3]) {
+  const double a = 2.0 * PI * t / YEAR_S;
+  const double ca = std::cos(a), sa = std::sin(a);
+  const double e1[3] = {0.5 * std::sqrt(3.0) * ca, 0.5 * std::sqrt(3.0) * sa, 0.5};
+  const double e2[3] = {-sa, ca, 0.0};
+  const double rad = ARM_S / std::sqrt(3.0);
+  for (int i = 0; i < 3; ++i) {
+    const double sg = -a + 2.0 * PI * i / 3.0;
+    for (int k = 0; k < 3; ++k) p[i][k] = rad * (std::cos(sg) * e1[k] + std::sin(sg) * e2[k]);
+  }
+}
+
+// TDI-1.5 transfer factors of the A and E channels at detector time t and GW frequency
+// f (Eq. tdi2 with the full response; the paper builds its TDI variables from
+// single-link observables of a rigidly rotating, constant-arm constellation). For the
+// complex polarisation tensor P = A+ e+ - i Ax ex and propagation direction k = -n:
+//   single link s -> r, unit vector n_sr = (p_r - p_s)/L:
+//     G_sr = i pi f L sinc(pi f L (1 - k.n_sr)) exp(-i pi f (L + k.(p_s + p_r))) n_sr.P.n_sr
+//   (the plane-wave fractional frequency shift [H(t - k.p_r) - H(t - L - k.p_s)] /
+//   (2 (1 - k.n_sr)) of a locally monochromatic wave, with the barycentre delay of the
+//   guiding centre left in the template phase); with z = exp(-2 pi i f L),
+//     X = (1 - z^2) [(G_10 + z G_01) - (G_20 + z G_02)]   (G_sr for link s -> r)
+//   and Y, Z cyclic; A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6. In the long-wavelength
+//   limit X -> -16 pi^2 f^2 L^2 D_X : P.
+template <class R>
+static void tdi_transfer(const Source<R>& s, double t, const R& f, int n_chan, Cx<R> T[2]) {
+  double p[3][3];
+  spacecraft_offsets(t, p);
+  const double L = ARM_S;
+  R kp[3];  // k . p_i
+  for (int i = 0; i < 3; ++i) kp[i] = -(s.nhat[0] * p[i][0] + s.nhat[1] * p[i][1] + s.nhat[2] * p[i][2]);
+  // n.P.n for the arm (i, j) (the same for both directions)
+  auto nPn = [&](int i, int j) {
+    double n[3];
+    for (int k = 0; k < 3; ++k) n[k] = (p[j][k] - p[i][k]) / L;
+    R ep(0.0), ex(0.0);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        ep += n[a] * n[b] * s.ep[a][b];
+        ex += n[a] * n[b] * s.ex[a][b];
+      }
+    return Cx<R>{s.Ap * ep, -(s.Ax * ex)};
+  };
+  const Cx<R> q01 = nPn(0, 1), q02 = nPn(0, 2), q12 = nPn(1, 2);
+  auto link = [&](int sd, int rc, const Cx<R>& q) {
+    const R kn = (kp[rc] - kp[sd]) / L;        // k . n_sr
+    const R x = PI * f * L * (1.0 - kn);
+    const R sinc = std::fabs(lval(x)) < 1e-6 ? R(1.0) - x * x / 6.0 : sin_(x) / x;
+    const R ph = -PI * f * (L + kp[sd] + kp[rc]);
+    const R amp = PI * f * L * sinc;            // times i
+    const Cx<R> e = {cos_(ph), sin_(ph)};
+    const Cx<R> iq = {-amp * q.im, amp * q.re};  // i amp q
+    return cmul(e, iq);
+  };
+  const Cx<R> G01 = link(0, 1, q01), G10 = link(1, 0, q01);
+  const Cx<R> G02 = link(0, 2, q02), G20 = link(2, 0, q02);
+  const Cx<R> G12 = link(1, 2, q12), G21 = link(2, 1, q12);
+  const R w = -2.0 * PI * f * L;
+  const Cx<R> z = {cos_(w), sin_(w)};
+  const Cx<R> z2 = cmul(z, z);
+  const Cx<R> one_mz2 = {1.0 - z2.re, -z2.im};
+  auto rt = [&](const Cx<R>& a, const Cx<R>& b) { return cadd(a, cmul(z, b)); };
+  auto sub = [](const Cx<R>& a, const Cx<R>& b) { return Cx<R>{a.re - b.re, a.im - b.im}; };
+  const Cx<R> X = cmul(one_mz2, sub(rt(G10, G01), rt(G20, G02)));
+  const Cx<R> Y = cmul(one_mz2, sub(rt(G21, G12), rt(G01, G10)));
+  const Cx<R> Z = cmul(one_mz2, sub(rt(G02, G20), rt(G12, G21)));
+  const double r2 = 1.0 / std::sqrt(2.0), r6 = 1.0 / std::sqrt(6.0);
+  T[0] = {(Z.re - X.re) * r2, (Z.im - X.im) * r2};
+  if (n_chan > 1) T[1] = {(X.re - 2.0 * Y.re + Z.re) * r6, (X.im - 2.0 * Y.im + Z.im) * r6};
 }
 
 // Doppler delay n.r(t)/c and its first two time derivatives.
@@ -567,6 +647,8 @@ static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp
       if (resp == 0) {
         T[0] = {R(1.0), R(0.0)};
         T[1] = {R(1.0), R(0.0)};
+      } else if (resp == 2) {
+        tdi_transfer(src, tm, tp.f, g.n_chan, T);
       } else {
         response(src, tm, g.n_chan, T);
       }
@@ -761,6 +843,31 @@ void oracle_response(const double* th8, const double* t, int64_t n, int n_chan, 
       T_im[c * n + i] = T[c].im;
     }
   }
+}
+
+// TDI-1.5 transfer factors at detector times t[n] and GW frequencies f[n]:
+// T_re/T_im [chan][n].
+void oracle_response_tdi(const double* th8, const double* t, const double* f, int64_t n,
+                         int n_chan, double* T_re, double* T_im) {
+  long double th[NPAR];
+  for (int p = 0; p < NPAR; ++p) th[p] = th8[p];
+  const Source<long double> s = make_source<long double>(th, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    Cx<long double> T[2];
+    tdi_transfer(s, t[i], (long double)f[i], n_chan, T);
+    for (int c = 0; c < n_chan; ++c) {
+      T_re[c * n + i] = (double)T[c].re;
+      T_im[c * n + i] = (double)T[c].im;
+    }
+  }
+}
+
+// Spacecraft offsets from the guiding centre [light-seconds], row-major [3][3].
+void oracle_spacecraft_offsets(double t, double* p9) {
+  double p[3][3];
+  spacecraft_offsets(t, p);
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) p9[3 * i + k] = p[i][k];
 }
 
 // Detector tensors D_A, D_E (row-major 3x3 each) at detector time t.

@@ -215,6 +215,79 @@ def _injection_td(theta, dt, n_samples, t0, response, pn_order, chi, ecc, f_cut,
     return out
 
 
+ARM_S = 2.5e9 / 299792458.0  # constellation arm length / c [s]
+
+
+def _spacecraft(t):
+    """Guiding centre r(t) and spacecraft offsets p_i(t) [light-s]: the rotating triangle
+    of _lw_tensors with 2.5e9 m sides. Returns (R [n, 3], P [3, n, 3])."""
+    a = 2 * np.pi * np.asarray(t, dtype=np.float64) / YEAR_S
+    ca, sa = np.cos(a), np.sin(a)
+    n = a.size
+    rhat = np.stack([ca, sa, np.zeros(n)], -1)
+    e1 = (math.sqrt(3) / 2) * rhat + 0.5 * np.array([0.0, 0.0, 1.0])
+    e2 = np.stack([-sa, ca, np.zeros(n)], -1)
+    rad = ARM_S / math.sqrt(3)
+    P = np.stack([rad * (np.cos(-a + 2 * np.pi * i / 3)[:, None] * e1 +
+                         np.sin(-a + 2 * np.pi * i / 3)[:, None] * e2) for i in range(3)])
+    return AU_S * rhat, P
+
+
+def _injection_tdi(theta, dt, n_samples, t0, pn_order, chi, ecc, f_cut, n_chan):
+    """A/E TDI-1.5 time series of the injection, built from delayed single-link
+    observables of the rigidly rotating constellation:
+
+    y_{s->r}(t) = [H(t + n.x_r) - H(t - L + n.x_s)] / (2 (1 + n.n_sr)), H = n_sr.h.n_sr,
+    with h(tau) = A(tau) (A+ e+ cos Phi + Ax ex sin Phi) at barycentre time tau, x the
+    spacecraft positions (guiding centre + offset) and n the direction to the source;
+    X = r2(t) + r3(t - 2L) - r3(t) - r2(t - 2L), r2 = y_{1->0}(t) + y_{0->1}(t - L),
+    r3 = y_{2->0}(t) + y_{0->2}(t - L), Y and Z cyclic, A = (Z - X)/sqrt2,
+    E = (X - 2Y + Z)/sqrt6."""
+    import torch
+    Mc, eta, f0, phi0, lam, beta, psi, iota = [float(x) for x in theta]
+    tc = _chirp_constants(Mc, eta, f0, pn_order)[0]
+    out = np.zeros((n_chan, n_samples))
+    n_live = int(min(n_samples, max(0, math.ceil((tc + AU_S + 40.0 - t0) / dt))))
+    if n_live == 0:
+        return out
+    t = t0 + np.arange(n_live) * dt
+    nhat = np.array([math.cos(beta) * math.cos(lam), math.cos(beta) * math.sin(lam), math.sin(beta)])
+    ep, ex = _polarisation(lam, beta, psi)
+    Ap, Ax = 0.5 * (1 + math.cos(iota) ** 2), math.cos(iota)
+    L = ARM_S
+
+    def y(s_, r_, delay):
+        """y_{s->r}(t - delay) on the sample grid."""
+        td = t - delay
+        Rc, P = _spacecraft(td)
+        xs, xr = Rc + P[s_], Rc + P[r_]
+        nl = (P[r_] - P[s_]) / L
+        hp = np.einsum("ni,ij,nj->n", nl, ep, nl) * Ap
+        hx = np.einsum("ni,ij,nj->n", nl, ex, nl) * Ax
+        vals = []
+        for tau in (td + xr @ nhat, td - L + xs @ nhat):
+            tt = torch.from_numpy(tau)
+            ok = tt < tc
+            ph, fr, _ = _signal_phase_freq(torch.where(ok, tt, torch.zeros_like(tt)), Mc, eta,
+                                           f0, phi0, pn_order, chi, ecc)
+            ok &= fr < f_cut
+            a = torch.where(ok, fr.abs() ** (2.0 / 3.0), torch.zeros_like(fr)).numpy()
+            vals.append(a * (hp * np.cos(ph.numpy()) + hx * np.sin(ph.numpy())))
+        return (vals[0] - vals[1]) / (2.0 * (1.0 + nl @ nhat))
+
+    def michelson(c):
+        a_, b_ = (c + 1) % 3, (c + 2) % 3
+        r2 = lambda d: y(a_, c, d) + y(c, a_, d + L)
+        r3 = lambda d: y(b_, c, d) + y(c, b_, d + L)
+        return r2(0.0) + r3(2 * L) - r3(0.0) - r2(2 * L)
+
+    X, Y, Z = (michelson(c) for c in range(3))
+    out[0, :n_live] = (Z - X) / math.sqrt(2)
+    if n_chan > 1:
+        out[1, :n_live] = (X - 2 * Y + Z) / math.sqrt(6)
+    return out
+
+
 def _tranche_fft(x, L, n_bins, dt, window):
     """Per-tranche FFT d~[m,k] = dt sum_j win_j x(t_m + j dt) e^{-2 pi i jk/L}, k < n_bins."""
     n_chan, N = x.shape
@@ -334,12 +407,13 @@ def cached(fn, **kw):
 
 
 def two_year_two_channel(seed=1002, n_inj=20, inject=True, n_tranche=6144, L=2048,
-                         window="tukey", psd_scale=1.0, gaps=True):
+                         window="tukey", psd_scale=1.0, gaps=True, response="lw"):
     """A and E channels, dt = 5 s, n_tranche x L samples (6144 x 2048 ~ 1.26e7, 728 d),
     L/2 complex bins per tranche; PSD modulated by +-20 % with a 30-day period; 3.5 h
     gaps every 14 days plus 20 Poisson gaps of 1-24 h; n_inj injections (1PN, long-
     wavelength A/E response with annual orbit, M_c in [10, 60], f_0 in [15, 30] mHz,
-    SNR in [11, 20], small spin/eccentricity phase drift)."""
+    SNR in [11, 20], small spin/eccentricity phase drift). response="tdi" builds the
+    injections through the TDI-1.5 single-link response instead (response code 2)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     dt = 5.0
     dT = L * dt
@@ -374,7 +448,10 @@ def two_year_two_channel(seed=1002, n_inj=20, inject=True, n_tranche=6144, L=204
         ecc = irng.uniform(0, 0.01, n_inj)
         N = n_tranche * L
         for i in range(n_inj):
-            s = _injection_td(inj[:, i], dt, N, 0.0, 1, 1, chi[i], ecc[i], 0.095, 2)
+            if response == "tdi":
+                s = _injection_tdi(inj[:, i], dt, N, 0.0, 1, chi[i], ecc[i], 0.095, 2)
+            else:
+                s = _injection_td(inj[:, i], dt, N, 0.0, 1, 1, chi[i], ecc[i], 0.095, 2)
             s_tf = _tranche_fft(s, L, n_bins, dt, window)
             rho2 = _optimal_snr2(s_tf, w, df)
             if rho2 > 0:
@@ -383,9 +460,10 @@ def two_year_two_channel(seed=1002, n_inj=20, inject=True, n_tranche=6144, L=204
     if gaps:
         mask, _ = gap_mask(n_tranche, dT, seed + 5000)
         d[:, mask == 0, :] = 0.0
-    return TFData(d=d, w=w, mask=mask, dt=dt, dT=dT, pn_order=1, response=1,
-                  injections=inj, inj_snr=snr,
-                  meta={"workload": f"AE-2yr-{L}x{n_tranche}", "seed": seed, "window": window})
+    return TFData(d=d, w=w, mask=mask, dt=dt, dT=dT, pn_order=1,
+                  response=2 if response == "tdi" else 1, injections=inj, inj_snr=snr,
+                  meta={"workload": f"AE-2yr-{L}x{n_tranche}", "seed": seed, "window": window,
+                        "response": response})
 
 
 def tf_noise_only(shape, w, df, seed):

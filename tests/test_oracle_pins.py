@@ -475,3 +475,73 @@ def test_gradient_against_central_differences(small_ae):
             assert abs(fd[i] - g[p, i]) < 1e-5 * abs(g[p, i]) + scale, (p, i, fd[i], g[p, i])
             checked += 1
     assert checked >= 30
+
+
+# ---------------------------------------------------------------------------------------
+# TDI-1.5 response (response code 2)
+# ---------------------------------------------------------------------------------------
+
+ARM_S = 2.5e9 / 299792458.0
+
+
+def test_spacecraft_offsets_form_the_lw_triangle():
+    for t in (0.0, 7.3e6, 2.9e7):
+        p = oracle.spacecraft_offsets(t)
+        assert np.allclose(p.sum(0), 0.0, atol=1e-12)
+        for i, j in ((0, 1), (0, 2), (1, 2)):
+            assert np.linalg.norm(p[j] - p[i]) == pytest.approx(ARM_S, rel=1e-13)
+        # the arms point along the long-wavelength tensors' arms: D_X = (l01 l01 - l02 l02)/2
+        l01 = (p[1] - p[0]) / ARM_S
+        l02 = (p[2] - p[0]) / ARM_S
+        DX = 0.5 * (np.outer(l01, l01) - np.outer(l02, l02))
+        l12 = (p[2] - p[1]) / ARM_S
+        DY = 0.5 * (np.outer(l12, l12) - np.outer(l01, l01))
+        DZ = 0.5 * (np.outer(l02, l02) - np.outer(l12, l12))
+        DA, DE = oracle.detector_tensors(t)
+        assert np.allclose(DA, (DZ - DX) / np.sqrt(2), atol=1e-14)
+        assert np.allclose(DE, (DX - 2 * DY + DZ) / np.sqrt(6), atol=1e-14)
+
+
+def test_tdi_transfer_long_wavelength_limit():
+    """f L -> 0: X -> -16 pi^2 f^2 L^2 D_X : P for every channel, with a first-order
+    correction linear in f."""
+    th = np.array([30.0, 0.2, 0.02, 1.0, 0.7, 0.3, 0.4, 0.9])
+    t = np.array([1e6, 1.1e7, 3.0e7])
+    T_lw = oracle.response(th, t)
+    dev = []
+    for f in (1e-7, 1e-6):
+        r = oracle.response_tdi(th, t, f) / (-16 * np.pi ** 2 * f ** 2 * ARM_S ** 2) / T_lw
+        dev.append(np.abs(r - 1).max())
+    assert dev[0] < 2e-5
+    assert 5 < dev[1] / dev[0] < 20  # first order in f
+
+
+def test_tdi_transfer_matches_time_domain_single_links():
+    """A slowly chirping wave run through delayed single-link observables in the time
+    domain (the input generator's own construction) equals Re{T(t, f) A e^{i Phi}} with
+    the oracle's closed-form transfer, to the accuracy of the local-monochromatic
+    reading (the wave's frequency changes by ~1e-9 of itself across the 25 s of TDI
+    delays)."""
+    import math
+    import torch
+    from paper_2510_19047_b300 import synth
+    th = np.array([20.0, 0.2, 0.02, 1.0, 0.7, 0.3, 0.4, 0.9])
+    dt, N, t0 = 5.0, 8000, 1e6
+    s = synth._injection_tdi(th, dt, N, t0, 1, 0.0, 0.0, 0.095, 2)
+    t = t0 + np.arange(N) * dt
+    lam, beta = th[4], th[5]
+    nh = np.array([math.cos(beta) * math.cos(lam), math.cos(beta) * math.sin(lam), math.sin(beta)])
+    Rc, _ = synth._spacecraft(t)
+    ph, fr, _ = synth._signal_phase_freq(torch.from_numpy(t + Rc @ nh), *th[:4], 1)
+    ph, fr = ph.numpy(), fr.numpy()
+    a = 2 * np.pi * t / synth.YEAR_S
+    d1 = (2 * np.pi / synth.YEAR_S) * synth.AU_S * math.cos(beta) * (
+        math.sin(lam) * np.cos(a) - math.cos(lam) * np.sin(a))
+    T = oracle.response_tdi(th, t, fr * (1 + d1))
+    pred = np.real(T * fr ** (2.0 / 3.0) * np.exp(1j * ph))
+    for c in range(2):
+        assert np.abs(s[c] - pred[c]).max() < 2e-4 * np.abs(pred[c]).max()
+    # and the full transfer differs from the long-wavelength one in this band
+    L_lw = np.real(-16 * np.pi ** 2 * (fr * (1 + d1)) ** 2 * ARM_S ** 2 * oracle.response(th, t)
+                   * fr ** (2.0 / 3.0) * np.exp(1j * ph))
+    assert np.abs(s[0] - L_lw[0]).max() > 0.05 * np.abs(pred[0]).max()
