@@ -15,6 +15,7 @@ fap       : background of the coherent (N_seg = 1) tile maximum over 100 noise-o
             of the loudest injection's tile maximum.
 pso       : one particle swarm per injection tile (512 particles, 100 iterations,
             N_seg = 16) against the injection's own statistic.
+tdi       : throughput with the TDI-1.5 response against the long-wavelength one.
 """
 import statistics
 import time
@@ -226,3 +227,35 @@ def pso(args):
             "best_over_snr2": {"min": float((fx.cpu().numpy() / snr2).min()),
                                "median": float(np.median(fx.cpu().numpy() / snr2)),
                                "max": float((fx.cpu().numpy() / snr2).max())}}
+
+
+def tdi(args):
+    """Throughput of the statistic with the TDI-1.5 response (code 2) against the
+    long-wavelength one (code 1) on the bench's two-year workload: 1e6 templates,
+    N_seg 256/64/16 in one pass. The timing does not depend on the data's content;
+    parity of the TDI path is tested on a 45-day grid whose injections went through
+    the time-domain single-link response."""
+    import torch
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.binding import TFS
+    D = synth.cached(synth.two_year_two_channel)
+    th = torch.from_numpy(synth.two_year_bank(1_000_000, seed=2002)).cuda()
+    out = {"study": "tdi", "workload": "AE-2yr-2048x6144, 1e6 templates, N_seg 256/64/16"}
+    for resp in (1, 2):
+        c = TFS(0, pn_order=1, response=resp, profile=1)
+        c.load_tf_data(D.d, D.dt, D.dT)
+        c.set_noise_weights(D.w, D.mask)
+        c.eval_statistic(th, [256, 64, 16])
+        ks, ss = [], []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.eval_statistic(th, [256, 64, 16])
+            e1.record()
+            e1.synchronize()
+            ss.append(e0.elapsed_time(e1))
+            ks.append(c.last_profile()["statistic"])
+        out[f"response{resp}"] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
+                                  "kernel_ms": statistics.median(ks)}
+        c.close()
+    return out

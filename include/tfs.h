@@ -22,8 +22,11 @@
  *   (M_c [M_sun], eta, f_0 [Hz], phi_0 [rad], lambda, beta, psi, iota [rad]);
  *   f_0, phi_0 are the GW frequency and phase at barycentre time t' = 0.
  *   Chirp: Newtonian (pn_order 0) or 1PN TaylorT3 (pn_order 1). Response: none
- *   (T = 1, one or two identical channels) or the long-wavelength A/E response of
- *   a rigid constellation on a 1 AU orbit with Doppler delay t' = t + n.r(t)/c.
+ *   (T = 1, one or two identical channels), the long-wavelength A/E response of a
+ *   rigid constellation on a 1 AU orbit with Doppler delay t' = t + n.r(t)/c
+ *   (response 1), or the TDI-1.5 A/E transfer of the same rigidly rotating,
+ *   constant-arm (2.5e9 m) constellation built from single-link observables and
+ *   evaluated at each tranche's (t_nm, f_nm) (response 2; Eq. tdi2).
  *
  * Pointers: every array argument may be a host pointer or a device pointer of the
  *   context's device (the library asks the CUDA runtime which). Inputs are read
@@ -78,7 +81,8 @@ typedef struct tfs_options {
   int path;          /* tfs_path used by tfs_eval_statistic (default MIXED) */
   int pixel;         /* tfs_pixel: storage of d~/S and 1/S for the mixed path (default F16) */
   int pn_order;      /* 0 Newtonian chirp, 1 1PN TaylorT3 (default 1) */
-  int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1) */
+  int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1),
+                        2 TDI-1.5 A/E (tfs_grad_statistic: TFS_ERR_ARG) */
   int checked;       /* 1: kernels bounds-check every pixel index (slower) */
   int sort;          /* 1: length/frequency-sort templates before the mixed launch (default 1) */
   int warps_per_cta; /* mixed path CTA size in warps; 0 = autotuned on first use */
@@ -138,7 +142,8 @@ int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const i
  * pass recomputes the track and accumulates
  *   dUpsilon = sum_n [8 Re(conj(Z_n) dZ_n) / N_n - 4 |Z_n|^2 dN_n / N_n^2].
  * The window position and the Fresnel branch are held fixed (the almost-everywhere
- * derivative). FP32 arithmetic with a double-float phase track. */
+ * derivative). FP32 arithmetic with a double-float phase track. Responses 0 and 1
+ * only: with response 2 the call returns TFS_ERR_ARG. */
 int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream);
 

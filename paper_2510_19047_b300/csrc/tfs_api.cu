@@ -57,8 +57,9 @@ struct tfs_ctx {
   double prof[4] = {0, 0, 0, 0};
   bool prof_valid = false;
   int mixed_warps = 0;
-  // autotuned mixed launch shapes: (n_chan, pixel, fine_cap, per_template) -> (warps, ctas)
-  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> tuned;
+  // autotuned mixed launch shapes: (n_chan, pixel, fine_cap, per_template, response) ->
+  // (warps, ctas)
+  std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tuned;
   // CUDA graph of the mixed evaluation, replayed while its key is unchanged
   cudaStream_t cstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -227,13 +228,13 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
   };
   if (c->opt.warps_per_cta) {
     int per_sm = 0;
-    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.warps_per_cta, fine_cap, &per_sm));
+    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, c->opt.warps_per_cta, fine_cap, &per_sm));
     if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
     *warps_out = c->opt.warps_per_cta;
     shape_for(*warps_out, per_sm, ctas_out);
     return TFS_OK;
   }
-  const auto key = std::make_tuple(n_chan, pix, fine_cap, per_template);
+  const auto key = std::make_tuple(n_chan, pix, fine_cap, per_template, c->opt.response);
   auto it = c->tuned.find(key);
   if (it == c->tuned.end()) {
     a.n_work = std::min<int64_t>(n_tpl, 24576);
@@ -242,7 +243,7 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
     cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
     for (int warps : {4, 8}) {
       int occ = 0;
-      CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, warps, fine_cap, &occ));
+      CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, warps, fine_cap, &occ));
       for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
         int ctas;
         shape_for(warps, per_sm, &ctas);
@@ -266,7 +267,7 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
     it = c->tuned.emplace(key, pick).first;
   }
   int occ = 0;
-  CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, it->second.first, fine_cap, &occ));
+  CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, it->second.first, fine_cap, &occ));
   *warps_out = it->second.first;
   shape_for(*warps_out, std::min(occ, it->second.second), ctas_out);
   return TFS_OK;
@@ -297,7 +298,8 @@ static int check_options(tfs_ctx* c, const tfs_options* o) {
   if (o->path < 0 || o->path > 2) return fail(c, TFS_ERR_ARG, "options.path must be 0, 1 or 2");
   if (o->pixel < 0 || o->pixel > 2) return fail(c, TFS_ERR_ARG, "options.pixel must be 0, 1 or 2");
   if (o->pn_order < 0 || o->pn_order > 1) return fail(c, TFS_ERR_ARG, "options.pn_order must be 0 or 1");
-  if (o->response < 0 || o->response > 1) return fail(c, TFS_ERR_ARG, "options.response must be 0 or 1");
+  if (o->response < 0 || o->response > 2)
+    return fail(c, TFS_ERR_ARG, "options.response must be 0, 1 or 2");
   if (o->warps_per_cta < 0 || o->warps_per_cta > 8 ||
       (o->warps_per_cta && (o->warps_per_cta & (o->warps_per_cta - 1))))
     return fail(c, TFS_ERR_ARG, "options.warps_per_cta must be 0 or a power of two <= 8");
@@ -623,7 +625,8 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     if (!c->opt.checked && (r = setup(s))) return r;
     int warps = 8, ctas = 1;
     const bool must_time = !c->opt.warps_per_cta &&
-                           !c->tuned.count(std::make_tuple(g.n_chan, c->opt.pixel, fine_cap, per_template));
+                           !c->tuned.count(std::make_tuple(g.n_chan, c->opt.pixel, fine_cap, per_template,
+                                                           c->opt.response));
     if (c->opt.sort && must_time) {
       // the autotuner times the sorted queue, so sort once before choosing
       EvalArgs t = a;
@@ -803,6 +806,8 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
     return fail(c, TFS_ERR_NSEG, "N_t = " + std::to_string(c->g.n_tranche) +
                                      " is not divisible by N_seg = " + std::to_string(n_seg));
   if (n_seg > kMixedMaxFine) return fail(c, TFS_ERR_ARG, "the gradient kernel supports N_seg <= 1024");
+  if (c->opt.response == 2)
+    return fail(c, TFS_ERR_ARG, "the gradient supports response 0 and 1 (long-wavelength)");
   if (n_tpl == 0) return TFS_OK;
   if (!theta || !out_stat || !out_grad) return fail(c, TFS_ERR_ARG, "null argument");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");

@@ -26,6 +26,7 @@
 
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
+#include "tfs_tdi.cuh"
 
 namespace tfs {
 
@@ -83,7 +84,8 @@ struct PixLoad<TFS_PIX_BF16> {
 static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &&
                   offsetof(TplMix, K_hi) == 32 && offsetof(TplMix, dops_hi) == 48 &&
                   offsetof(TplMix, C2) == 56 && offsetof(TplMix, fd_k) == 60 &&
-                  offsetof(TplMix, pp) == 64 && offsetof(TplMix, px) == 88,
+                  offsetof(TplMix, pp) == 64 && offsetof(TplMix, px) == 88 &&
+                  offsetof(TplMix, nx) == 112,
               "TplMix layout assumed by the 16-byte loads of the mixed kernel");
 
 // The paper's auxiliary Fresnel functions f, g in FP32 with approximate division,
@@ -164,7 +166,9 @@ constexpr int kDepth = TFS_MIXED_DEPTH;  // pixel-load lead of the unrolled path
 
 // PITCH: the m-pitch of the pixel plane as a compile-time constant (kMixedPitch) so that
 // the 21 window rows are immediate offsets from one address, or 0 for a runtime pitch.
-template <int NCH, int PIX, int PITCH>
+// TDI: the TDI-1.5 response (response code 2) instead of the long-wavelength one, as
+// its own instantiation so the long-wavelength kernel carries none of its code.
+template <int NCH, int PIX, int PITCH, bool TDI>
 __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
@@ -309,6 +313,15 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
                 fxA = fmaf(tr.DA[q], px[q], fxA);
                 fpE = fmaf(tr.DE[q], pp[q], fpE);
                 fxE = fmaf(tr.DE[q], px[q], fxE);
+              }
+              if (TDI) {  // TDI-1.5 transfer at (t_nm, f_nm)
+                const float4 nq = ldg_nc4(pq + 3);  // (nx, ny, nz, pad)
+                Cplx<float> TA, TE;
+                tdi_transfer<float>(f.hi, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
+                fpA = TA.re;
+                fxA = -TA.im;
+                fpE = TE.re;
+                fxE = -TE.im;
               }
               // (F+ - i Fx)(amp_c + i amp_s)
               Tr0 = fmaf(fpA, amp_c, fxA * amp_s);
@@ -472,16 +485,19 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
 template <int NCH, int PIX, int PITCH>
 static cudaError_t launch_one(const EvalArgs& a, int warps, int ctas, cudaStream_t s) {
   const size_t smem = (size_t)warps * a.fine_cap * sizeof(float4);
-  k_eval_mixed<NCH, PIX, PITCH><<<ctas, warps * 32, smem, s>>>(a);
+  if (a.response == 2)
+    k_eval_mixed<NCH, PIX, PITCH, true><<<ctas, warps * 32, smem, s>>>(a);
+  else
+    k_eval_mixed<NCH, PIX, PITCH, false><<<ctas, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Sets the dynamic shared-memory limit of the instantiation and returns how many CTAs
 // of this shape fit on one SM.
 template <int NCH, int PIX, int PITCH>
-static cudaError_t occ_one(int warps, int fine_cap, int* n) {
+static cudaError_t occ_one(int warps, int fine_cap, int resp, int* n) {
   const size_t smem = (size_t)warps * fine_cap * sizeof(float4);
-  auto kern = k_eval_mixed<NCH, PIX, PITCH>;
+  auto kern = resp == 2 ? k_eval_mixed<NCH, PIX, PITCH, true> : k_eval_mixed<NCH, PIX, PITCH, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, warps * 32, smem);
@@ -515,9 +531,9 @@ cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps,
 #undef TFS_CALL
 }
 
-cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int warps, int fine_cap,
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int warps, int fine_cap,
                             int* ctas_per_sm) {
-#define TFS_CALL(N, P, Q) occ_one<N, P, Q>(warps, fine_cap, ctas_per_sm)
+#define TFS_CALL(N, P, Q) occ_one<N, P, Q>(warps, fine_cap, resp, ctas_per_sm)
   TFS_MIXED_DISPATCH(TFS_CALL, n_chan, pix, pitch);
 #undef TFS_CALL
 }

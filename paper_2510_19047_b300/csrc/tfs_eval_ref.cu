@@ -23,6 +23,7 @@
 
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
+#include "tfs_tdi.cuh"
 
 namespace tfs {
 
@@ -93,15 +94,34 @@ __device__ __forceinline__ LevelState levels_of(const EvalArgs& a, int64_t i) {
   return L;
 }
 
-// Response factors T_alpha = F+ A+ - i Fx Ax (Eq. tdi2, long-wavelength limit).
+// Response factors of Eq. tdi2: T_alpha = F+ A+ - i Fx Ax in the long-wavelength limit
+// (resp 1), or the TDI-1.5 transfer at the tranche's frequency f (resp 2), evaluated
+// in the arithmetic type T.
 template <class T>
-__device__ __forceinline__ void response_factors(const TplConst& c, const double* DA,
-                                                 const double* DE, int resp, T Tr[2], T Ti[2]) {
+__device__ __forceinline__ void response_factors(const TplConst& c, const TrancheD& tr, double f,
+                                                 int resp, T Tr[2], T Ti[2]) {
   if (!resp) {
     Tr[0] = Tr[1] = T(1);
     Ti[0] = Ti[1] = T(0);
     return;
   }
+  if (resp == 2) {
+    T pp[6], px[6];
+    for (int k = 0; k < 6; ++k) {
+      pp[k] = T(c.pp[k]);
+      px[k] = T(c.px[k]);
+    }
+    T o[4];
+    tdi_transfer_call<T>(T(f), T(tr.ca), T(tr.sa), T(c.dop_c / kAuS), T(c.dop_s / kAuS), T(c.nz),
+                         pp, px, o);
+    Tr[0] = o[0];
+    Ti[0] = o[1];
+    Tr[1] = o[2];
+    Ti[1] = o[3];
+    return;
+  }
+  const double* DA = tr.DA;
+  const double* DE = tr.DE;
   double fpA = 0, fxA = 0, fpE = 0, fxE = 0;
   for (int p = 0; p < 6; ++p) {
     fpA += DA[p] * c.pp[p];
@@ -179,7 +199,7 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
     if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
 
     double Tr[2], Ti[2];
-    response_factors<double>(c, tr.DA, tr.DE, a.response, Tr, Ti);
+    response_factors<double>(c, tr, tk.f, a.response, Tr, Ti);
     const double aa = x - kcd;                    // in (-1, 0]
     const double sig = g.df * sqrt(2.0 / tk.fdot);  // v = sig * (f_nm - f_k)/df
     const double e2 = sqrt(2.0 * tk.fdot) * g.dT;   // v_2 - v_1
@@ -323,7 +343,7 @@ __global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
     if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
 
     float Tr[2], Ti[2];
-    response_factors<float>(c, tr.DA, tr.DE, a.response, Tr, Ti);
+    response_factors<float>(c, tr, tk.f, a.response, Tr, Ti);
     const double s2d = sqrt(2.0 * tk.fdot);
     const double inv_fdot = 1.0 / tk.fdot;
     const float P = (float)(pow(tk.fsrc / c.F0, 2.0 / 3.0) / s2d);

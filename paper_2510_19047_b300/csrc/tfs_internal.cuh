@@ -16,6 +16,7 @@ constexpr double kGMsunS = 4.925490947e-6;  // G M_sun / c^3 [s]
 constexpr double kAuS = 499.004784;         // 1 AU / c [s]
 constexpr double kYearS = 31557600.0;       // Julian year [s]
 constexpr double kOmega = 2.0 * kPi / kYearS;
+constexpr double kArmS = 2.5e9 / 299792458.0;  // constellation arm length / c [s]
 constexpr int kNF = 21;      // N_F bins per tranche
 constexpr int kNFHalf = 10;  // window k_c - 10 .. k_c + 10
 constexpr int kMixedPitch = 8192;  // m-pitch of the mixed pixel plane for N_t <= 8192
@@ -63,6 +64,7 @@ struct __align__(16) TplConst {
   int m_lo, m_hi;       // tranche range that can be active: [m_lo, m_hi)
   uint32_t key;         // sort key (longer tracks first, then start frequency)
   int kc_lo;            // window centre bin at m_lo
+  double nz;            // sin(beta): z component of the direction to the source
 };
 
 // The same constants split for the mixed path's double-float / FP32 arithmetic
@@ -76,6 +78,7 @@ struct __align__(16) TplMix {
   float dopc_hi, dopc_lo, dops_hi, dops_lo;
   float C2, fd_k;            // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
   float pp[6], px[6];
+  float nx, ny, nz, pad;     // direction to the source (TDI response)
   int m_lo, m_hi;
 };
 

@@ -67,7 +67,7 @@ cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s);
 // Persistent mixed-precision launch; grid = ctas, block = 32 * warps.
 cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
                               cudaStream_t s);
-cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int warps, int fine_cap,
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int warps, int fine_cap,
                             int* ctas_per_sm);
 
 struct AscentParams {

@@ -230,6 +230,10 @@ __device__ TplMix mix_of(const TplConst& c) {
     t.pp[k] = (float)c.pp[k];
     t.px[k] = (float)c.px[k];
   }
+  t.nx = (float)(c.dop_c / kAuS);
+  t.ny = (float)(c.dop_s / kAuS);
+  t.nz = (float)c.nz;
+  t.pad = 0.0f;
   t.m_lo = c.m_lo;
   t.m_hi = c.m_hi;
   return t;
@@ -268,6 +272,7 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
   }
   c.dop_c = src.dop_c;
   c.dop_s = src.dop_s;
+  c.nz = src.nz;
   // Tranches that can be active: the window k_c +- 10 must lie in [1, N_bins - 1],
   // i.e. 10 df < f_nm <= (N_bins - 11) df, and t' < t_c. The Doppler factor moves
   // f by at most 1.1e-4 relative and t' by at most 1 AU/c; a margin covers both.

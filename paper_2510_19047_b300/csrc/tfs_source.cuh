@@ -68,6 +68,7 @@ template <class R>
 struct SrcT {
   R tc, F0, C2, P5, P3, phi0, dop_c, dop_s;
   R pp[6], px[6];  // A+ e+ and Ax ex packed (xx, yy, zz, 2xy, 2xz, 2yz)
+  R nz;            // sin(beta)
 };
 
 // Template constants from theta = (Mc, eta, f0, phi0, lambda, beta, psi, iota).
@@ -133,6 +134,7 @@ __device__ SrcT<R> source_of(const R th[8], int pn_order) {
   }
   s.dop_c = kAuS * cb * cl;
   s.dop_s = kAuS * cb * sl;
+  s.nz = sb;
   return s;
 }
 

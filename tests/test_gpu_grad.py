@@ -75,3 +75,13 @@ def test_autograd_and_ascent(ae45):
     pred = t * norm ** 2
     ratio = (u1 - u0) / pred
     assert np.mean((ratio > 0.5) & (ratio < 1.5)) > 0.8, ratio
+
+
+def test_gradient_rejects_the_tdi_response(ae45):
+    from paper_2510_19047_b300.binding import TFSError
+    c = ctx_for(ae45)
+    c.set_options(response=2)
+    th = synth.candidates_near(ae45.injections, 4, seed=3)
+    with pytest.raises(TFSError) as e:
+        c.grad_statistic(th, 16)
+    assert e.value.code == -1

@@ -100,6 +100,34 @@ def test_two_channel_response_gaps_levels(ae45, ae45_bank, path, pixel):
     assert np.abs(diag[0] - refs[0][2]).max() <= (0 if path != "mixed" else 1)
 
 
+@pytest.fixture(scope="module")
+def ae45_tdi():
+    # 45 days of A/E data whose injections went through the TDI-1.5 single-link response
+    return synth.cached(synth.two_year_two_channel, seed=78, n_inj=2, n_tranche=384, L=2048,
+                        response="tdi")
+
+
+@pytest.mark.parametrize("path,pixel", CASES)
+def test_tdi_response(ae45_tdi, path, pixel):
+    """Response code 2 (TDI-1.5 transfer per tranche) against the oracle, with the
+    injections themselves in the bank."""
+    D = ae45_tdi
+    assert D.response == 2
+    th = synth.two_year_bank(94, seed=9)
+    th = np.concatenate([D.injections, th], axis=1)
+    lev = [128, 8]
+    refs = [oracle.statistic(D.d, D.w, D.mask, th, L, D.dT, pn_order=1, response=2) for L in lev]
+    c = ctx_for(D, path, pixel)
+    got, neff, diag = c.eval_statistic(th, lev, diag=True)
+    for i, (ref, rneff, rnact, _) in enumerate(refs):
+        mx, p99 = rel_err(got[i], ref)
+        tol = fp64_tol(D, lev[i]) if path == "fp64" else TOL[(path, pixel)][0]
+        assert mx < tol and p99 < max(tol, TOL[(path, pixel)][1]), (lev[i], mx, p99)
+        assert np.array_equal(neff[i], rneff)
+    # the injections stand far above the noise (E[Upsilon] = 2 N_eff in noise)
+    assert np.all(refs[1][0][:2] > 4 * 2 * refs[1][1][:2])
+
+
 def fast_chirp_bank(n, seed):
     """Half the bank sweeps 0.01-0.05 bins per tranche (sigma = df sqrt(2/fdot) > 6: only
     the two bins next to f_nm can need the general Fresnel form, and some tranches hold
