@@ -82,7 +82,7 @@ typedef struct tfs_options {
   int pixel;         /* tfs_pixel: storage of d~/S and 1/S for the mixed path (default F16) */
   int pn_order;      /* 0 Newtonian chirp, 1 1PN TaylorT3 (default 1) */
   int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1),
-                        2 TDI-1.5 A/E (tfs_grad_statistic: TFS_ERR_ARG) */
+                        2 TDI-1.5 A/E */
   int checked;       /* 1: kernels bounds-check every pixel index (slower) */
   int sort;          /* 1: length/frequency-sort templates before the mixed launch (default 1) */
   int warps_per_cta; /* mixed path CTA size in warps; 0 = autotuned on first use */
@@ -142,8 +142,8 @@ int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const i
  * pass recomputes the track and accumulates
  *   dUpsilon = sum_n [8 Re(conj(Z_n) dZ_n) / N_n - 4 |Z_n|^2 dN_n / N_n^2].
  * The window position and the Fresnel branch are held fixed (the almost-everywhere
- * derivative). FP32 arithmetic with a double-float phase track. Responses 0 and 1
- * only: with response 2 the call returns TFS_ERR_ARG. */
+ * derivative). FP32 arithmetic with a double-float phase track; with response 2 the
+ * TDI-1.5 transfer's dependence on f and on the source direction is included. */
 int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream);
 

@@ -806,8 +806,6 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
     return fail(c, TFS_ERR_NSEG, "N_t = " + std::to_string(c->g.n_tranche) +
                                      " is not divisible by N_seg = " + std::to_string(n_seg));
   if (n_seg > kMixedMaxFine) return fail(c, TFS_ERR_ARG, "the gradient kernel supports N_seg <= 1024");
-  if (c->opt.response == 2)
-    return fail(c, TFS_ERR_ARG, "the gradient supports response 0 and 1 (long-wavelength)");
   if (n_tpl == 0) return TFS_OK;
   if (!theta || !out_stat || !out_grad) return fail(c, TFS_ERR_ARG, "null argument");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");

@@ -5,6 +5,7 @@
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
 #include "tfs_source.cuh"
+#include "tfs_tdi.cuh"
 
 namespace tfs {
 
@@ -56,7 +57,7 @@ namespace {
 
 constexpr unsigned kFullG = 0xffffffffu;
 constexpr int kGradWarps = 4;
-constexpr int kSrcFields = 20;  // tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6]
+constexpr int kSrcFields = 21;  // tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6] n_z
 
 // The paper's auxiliary Fresnel functions and their derivatives at a = |v|.
 __device__ __forceinline__ void fg_deriv(float a, float& f, float& g, float& fp, float& gp) {
@@ -116,6 +117,90 @@ __device__ __forceinline__ BinW bin_w(float v1, float v2, float cps, float sps) 
   return b;
 }
 
+// FP32 forward-mode dual in four directions (f, n_x, n_y, n_z): the TDI-1.5 arm
+// coefficients and their derivatives in one evaluation.
+struct DF4 {
+  float v, d[4];
+  __device__ DF4() {}
+  __device__ DF4(double x) : v((float)x) { d[0] = d[1] = d[2] = d[3] = 0.0f; }
+  __device__ DF4(float x, int dir) : v(x) {
+    for (int k = 0; k < 4; ++k) d[k] = k == dir ? 1.0f : 0.0f;
+  }
+};
+__device__ __forceinline__ DF4 operator+(DF4 a, DF4 b) {
+  DF4 r;
+  r.v = a.v + b.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+__device__ __forceinline__ DF4 operator-(DF4 a, DF4 b) {
+  DF4 r;
+  r.v = a.v - b.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+__device__ __forceinline__ DF4 operator-(DF4 a) {
+  DF4 r;
+  r.v = -a.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+__device__ __forceinline__ DF4 operator*(DF4 a, DF4 b) {
+  DF4 r;
+  r.v = a.v * b.v;
+  for (int k = 0; k < 4; ++k) r.d[k] = fmaf(a.d[k], b.v, a.v * b.d[k]);
+  return r;
+}
+__device__ __forceinline__ DF4 operator*(DF4 a, float b) {
+  DF4 r;
+  r.v = a.v * b;
+  for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+__device__ __forceinline__ DF4 operator/(DF4 a, float b) { return a * (1.0f / b); }
+__device__ __forceinline__ DF4 operator+(float b, DF4 a) {
+  a.v += b;
+  return a;
+}
+
+}  // namespace
+
+template <>
+struct TdiMath<DF4> {
+  __device__ static void cis_cycles(DF4 c, DF4& s, DF4& co) {
+    float sv, cv;
+    TdiMath<float>::cis_cycles(c.v, sv, cv);
+    const float w = 6.283185307f;
+    s.v = sv;
+    co.v = cv;
+    for (int k = 0; k < 4; ++k) {
+      s.d[k] = w * cv * c.d[k];
+      co.d[k] = -w * sv * c.d[k];
+    }
+  }
+  // sin(pi x)/(pi x) and its derivative (cos(pi x) - sinc)/x (-> -pi^2 x/3 at x -> 0)
+  __device__ static DF4 sinc_pi(DF4 x) {
+    const float px = 3.141592654f * x.v;
+    float v, dv;
+    if (fabsf(px) < 1e-3f) {
+      v = 1.0f - px * px * (1.0f / 6.0f);
+      dv = -3.141592654f * px * (1.0f / 3.0f);
+    } else {
+      float s, c;
+      const float r = x.v - 2.0f * rint_small(0.5f * x.v);
+      __sincosf(3.141592654f * r, &s, &c);
+      v = s / px;
+      dv = (c - v) / x.v;
+    }
+    DF4 o;
+    o.v = v;
+    for (int k = 0; k < 4; ++k) o.d[k] = dv * x.d[k];
+    return o;
+  }
+};
+
+namespace {
+
 struct GradArgs {
   GridDesc g;
   MixConst mc;
@@ -145,11 +230,12 @@ struct Trk {
   float cps, sps;          // e^{i Psi}
   float cph, sph;          // e^{i phi}
   float P;                 // A / sqrt(2 fdot)
-  float fdot, amp, u, tpr, y, y2, onec, fsrc, fdsrc, d1, d2, ca, sa;  // tpr = t'/t_c = 1 - u
+  float f, fdot, amp, u, tpr, y, y2, onec, fsrc, fdsrc, d1, d2, ca, sa;  // tpr = t'/t_c = 1 - u
   double ud, yd, tprd;  // u, y, t'/t_c from their double-float values (for the phase terms)
   float Tr[2], Ti[2];      // response (no amplitude)
 };
 
+template <bool TDI>
 __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int m) {
   Trk k;
   k.ok = false;
@@ -195,6 +281,7 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   k.ok = true;
   k.kc = kc;
   k.aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
+  k.f = f.hi;
   k.fdot = fdot;
   k.sig = a.mc.sig_k * rsqrt_approx(fdot);
   k.eps = fdot * a.mc.dTf * a.mc.dTf;
@@ -227,18 +314,28 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
     const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
     const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
     const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-    float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
+    if (TDI) {
+      const float4 nq = ldg_nc4(pq + 3);  // direction to the source
+      Cplx<float> TA, TE;
+      tdi_transfer<float>(f.hi, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
+      k.Tr[0] = TA.re;
+      k.Ti[0] = TA.im;
+      k.Tr[1] = TE.re;
+      k.Ti[1] = TE.im;
+    } else {
+      float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      fpA = fmaf(tr.DA[q], pp[q], fpA);
-      fxA = fmaf(tr.DA[q], px[q], fxA);
-      fpE = fmaf(tr.DE[q], pp[q], fpE);
-      fxE = fmaf(tr.DE[q], px[q], fxE);
+      for (int q = 0; q < 6; ++q) {
+        fpA = fmaf(tr.DA[q], pp[q], fpA);
+        fxA = fmaf(tr.DA[q], px[q], fxA);
+        fpE = fmaf(tr.DE[q], pp[q], fpE);
+        fxE = fmaf(tr.DE[q], px[q], fxE);
+      }
+      k.Tr[0] = fpA;
+      k.Ti[0] = -fxA;
+      k.Tr[1] = fpE;
+      k.Ti[1] = -fxE;
     }
-    k.Tr[0] = fpA;
-    k.Ti[0] = -fxA;
-    k.Tr[1] = fpE;
-    k.Ti[1] = -fxE;
   } else {
     k.Tr[0] = k.Tr[1] = 1.0f;
     k.Ti[0] = k.Ti[1] = 0.0f;
@@ -297,16 +394,74 @@ __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, 
     const float w1 = (float)kOmega, w2 = (float)(kOmega * kOmega);
     g[6] = g_tp * k.ca - g_d1 * w1 * k.sa - g_d2 * w2 * k.ca;
     g[7] = g_tp * k.sa + g_d1 * w1 * k.ca - g_d2 * w2 * k.sa;
+    if (a.response != 2) {  // T_alpha = D_alpha : (pp - i px); TDI: tdi_adjoint
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      g[8 + q] = cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
-      g[14 + q] = -(cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q]);
+      for (int q = 0; q < 6; ++q) {
+        g[8 + q] = cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
+        g[14 + q] = -(cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q]);
+      }
     }
   }
 }
 
+// TDI-1.5 response: its share of the adjoints of A+ e+, Ax ex (linear), of the source
+// direction (g[6], g[7] through n_x = dop_c / (R/c), n_y = dop_s / (R/c), and g[20] for
+// n_z), and the response's own dependence on f, returned as an addition to dUpsilon/df.
+// Derivatives of the arm coefficients in (f, n) by the four-direction dual.
+__device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, const float cTr[2],
+                                             const float cTi[2], float g[kSrcFields]) {
+  const float4* pq = reinterpret_cast<const float4*>(cp->pp);
+  const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2), nq = ldg_nc4(pq + 3);
+  const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+  const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+  TdiArms<DF4> arm;
+  float q[3][6];
+  tdi_arms<DF4, float>(DF4(k.f, 0), k.ca, k.sa, DF4(nq.x, 1), DF4(nq.y, 2), DF4(nq.z, 3), arm, q);
+  float dfT = 0.f, dn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    // P_arm = q . (pp - i px)
+    float Pr = 0.f, Pi = 0.f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      Pr = fmaf(q[r][j], pp[j], Pr);
+      Pi = fmaf(-q[r][j], px[j], Pi);
+    }
+    // sum over channels of Re(conj(c) dC) P and of the linear parts
+    float wr = 0.f, wi = 0.f;  // sum_c (cTr C.re + cTi C.im), sum_c (cTr C.im - cTi C.re)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const Cplx<DF4>& C = arm.C[c][r];
+      wr += cTr[c] * C.re.v + cTi[c] * C.im.v;
+      wi += cTr[c] * C.im.v - cTi[c] * C.re.v;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        // d(C P) = dC P; Re and Im against (cTr, cTi)
+        const float tr_ = C.re.d[d] * Pr - C.im.d[d] * Pi;
+        const float ti_ = C.re.d[d] * Pi + C.im.d[d] * Pr;
+        const float v = cTr[c] * tr_ + cTi[c] * ti_;
+        if (d == 0)
+          dfT += v;
+        else
+          dn[d - 1] += v;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      g[8 + j] += q[r][j] * wr;
+      g[14 + j] += q[r][j] * wi;
+    }
+  }
+  g[6] += dn[0] * (float)(1.0 / kAuS);
+  g[7] += dn[1] * (float)(1.0 / kAuS);
+  g[20] += dn[2];
+  return dfT;
+}
+
 }  // namespace
 
+// TDI: the TDI-1.5 response (code 2), as its own instantiation.
+template <bool TDI>
 __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   extern __shared__ float4 s_seg[];
   __shared__ double s_dsrc[kGradWarps][8][kSrcFields];
@@ -351,6 +506,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
       o[8 + q] = sd.pp[q].d;
       o[14 + q] = sd.px[q].d;
     }
+    o[20] = sd.nz.d;
   }
   __syncwarp();
 
@@ -360,7 +516,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     const bool inr = m < tc.m_hi;
     float Zr = 0.f, Zi = 0.f, Nn = 0.f;
     if (inr) {
-      const Trk L = track_df(a, cp, m);
+      const Trk L = track_df<TDI>(a, cp, m);
       if (L.ok) {
         float zr[2] = {0, 0}, zi[2] = {0, 0}, nn[2] = {0, 0};
         const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
@@ -440,7 +596,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     double gph[3] = {0.0, 0.0, 0.0};
     Trk L;
     L.ok = false;
-    if (m < tc.m_hi) L = track_df(a, cp, m);
+    if (m < tc.m_hi) L = track_df<TDI>(a, cp, m);
     if (L.ok) {
       const float4 lm = seg[m / a.seg_len];
       const float lr = lm.x, li = lm.y, mu = lm.z;
@@ -511,7 +667,15 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
       const float cphi = -(lr * Zmi + li * Zmr);               // Re(i lambda z)
       const float cP = (lr * Zmr - li * Zmi) + 2.0f * mu * Nm;  // coefficient of dP/P
       cfd += -cP * ifd2;
-      track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
+      if (TDI) {
+        float tg[kSrcFields];
+        for (int k = 0; k < kSrcFields; ++k) tg[k] = 0.0f;
+        cf += tdi_adjoint(cp, L, cTr, cTi, tg);  // the transfer depends on f too
+        track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
+        for (int k = 0; k < kSrcFields; ++k) gl[k] += tg[k];
+      } else {
+        track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -559,9 +723,10 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.out_stat = out_stat;
   a.out_grad = out_grad;
   const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
-  cudaError_t e = cudaFuncSetAttribute(k_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = response == 2 ? k_grad<true> : k_grad<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_grad<<<(unsigned)((n + kGradWarps - 1) / kGradWarps), kGradWarps * 32, smem, s>>>(a);
+  kern<<<(unsigned)((n + kGradWarps - 1) / kGradWarps), kGradWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -99,18 +99,22 @@ __device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, 
   };
   const Cplx<T> q01 = nPn(0, 1), q02 = nPn(0, 2), q12 = nPn(1, 2);
   const T fL = f * L;
-  auto link = [&](int sd, int rc, Cplx<T> q) {
-    const T kn = (kp[rc] - kp[sd]) / L;
-    const T amp = T(kPi) * fL * M::sinc_pi(fL * (T(1) - kn));
+  // both directions of an arm share the phase factor (k.(p_s + p_r) is symmetric) and
+  // differ in the sinc argument (1 - k.n versus 1 + k.n)
+  auto arm = [&](int i, int j, Cplx<T> q, Cplx<T>& Gij, Cplx<T>& Gji) {
+    const T kn = (kp[j] - kp[i]) / L;  // k . n_ij
     T s, c;
-    M::cis_cycles(T(-0.5) * f * (L + kp[sd] + kp[rc]), s, c);
-    // i amp q e^{i ph}
-    const Cplx<T> iq = {-amp * q.im, amp * q.re};
-    return cmul(Cplx<T>{c, s}, iq);
+    M::cis_cycles(T(-0.5) * f * (L + kp[i] + kp[j]), s, c);
+    const Cplx<T> eq = cmul(Cplx<T>{c, s}, Cplx<T>{-q.im, q.re});  // i q e^{i ph}
+    const T pfl = T(kPi) * fL;
+    const T aij = pfl * M::sinc_pi(fL * (T(1) - kn)), aji = pfl * M::sinc_pi(fL * (T(1) + kn));
+    Gij = {aij * eq.re, aij * eq.im};
+    Gji = {aji * eq.re, aji * eq.im};
   };
-  const Cplx<T> G01 = link(0, 1, q01), G10 = link(1, 0, q01);
-  const Cplx<T> G02 = link(0, 2, q02), G20 = link(2, 0, q02);
-  const Cplx<T> G12 = link(1, 2, q12), G21 = link(2, 1, q12);
+  Cplx<T> G01, G10, G02, G20, G12, G21;
+  arm(0, 1, q01, G01, G10);
+  arm(0, 2, q02, G02, G20);
+  arm(1, 2, q12, G12, G21);
   T zs, zc;
   M::cis_cycles(-fL, zs, zc);
   const Cplx<T> z = {zc, zs};
@@ -122,6 +126,89 @@ __device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, 
   const T r2 = T(0.7071067811865476), r6 = T(0.4082482904638631);
   TA = {(Z.re - X.re) * r2, (Z.im - X.im) * r2};
   TE = {(X.re - T(2) * Y.re + Z.re) * r6, (X.im - T(2) * Y.im + Z.im) * r6};
+}
+
+// ---------------------------------------------------------------------------------
+// Per-arm form for the gradient: T_c = sum_arm C[c][arm] (q_arm . (pp - i px)), with
+// q_arm the products (n0 n0, n1 n1, n2 n2, n0 n1, n0 n2, n1 n2) of the arm's unit vector
+// (geometry only) and C the arm's complex coefficient in channel c (A, E), which
+// carries the dependence on f and on the source direction. Written over T so that a
+// forward-mode dual type gives dC/d(f, n).
+// ---------------------------------------------------------------------------------
+template <class T>
+struct TdiArms {
+  Cplx<T> C[2][3];  // arms (0,1), (0,2), (1,2)
+};
+
+template <class T, class G>
+__device__ __forceinline__ void tdi_arms(T f, G ca, G sa, T nx, T ny, T nz, TdiArms<T>& out,
+                                         G q[3][6]) {
+  using M = TdiMath<T>;
+  const G L = G(kArmS);
+  const G h3 = G(0.8660254037844386);
+  const G rad = G(kArmS / 1.7320508075688772);
+  const G e1[3] = {h3 * ca, h3 * sa, G(0.5)};
+  const G e2[3] = {-sa, ca, G(0)};
+  const G cs[3] = {ca, G(-0.5) * ca + h3 * sa, G(-0.5) * ca - h3 * sa};
+  const G sn[3] = {-sa, G(0.5) * sa + h3 * ca, G(0.5) * sa - h3 * ca};
+  G p[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[i][k] = rad * (cs[i] * e1[k] + sn[i] * e2[k]);
+  T kp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) kp[i] = -(nx * p[i][0] + ny * p[i][1] + nz * p[i][2]);
+  const int ai[3] = {0, 0, 1}, aj[3] = {1, 2, 2};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const G a0 = (p[aj[r]][0] - p[ai[r]][0]) / L, a1 = (p[aj[r]][1] - p[ai[r]][1]) / L,
+            a2 = (p[aj[r]][2] - p[ai[r]][2]) / L;
+    q[r][0] = a0 * a0;
+    q[r][1] = a1 * a1;
+    q[r][2] = a2 * a2;
+    q[r][3] = a0 * a1;
+    q[r][4] = a0 * a2;
+    q[r][5] = a1 * a2;
+  }
+  const T fL = f * L;
+  // link coefficient c_sr = i pi f L sinc(pi f L (1 - k.n_sr)) e^{-i pi f (L + k.(p_s + p_r))};
+  // both directions of an arm share the phase factor
+  auto lc = [&](int i, int j, Cplx<T>& cij, Cplx<T>& cji) {
+    const T kn = (kp[j] - kp[i]) / L;
+    T s, c;
+    M::cis_cycles(T(-0.5) * f * (L + kp[i] + kp[j]), s, c);
+    const T pfl = T(kPi) * fL;
+    const T aij = pfl * M::sinc_pi(fL * (T(1) - kn)), aji = pfl * M::sinc_pi(fL * (T(1) + kn));
+    cij = {T(0) - aij * s, aij * c};
+    cji = {T(0) - aji * s, aji * c};
+  };
+  Cplx<T> c01, c10, c02, c20, c12, c21;
+  lc(0, 1, c01, c10);
+  lc(0, 2, c02, c20);
+  lc(1, 2, c12, c21);
+  T zs, zc;
+  M::cis_cycles(-fL, zs, zc);
+  const Cplx<T> z = {zc, zs};
+  const Cplx<T> z2 = cmul(z, z);
+  const Cplx<T> w = {T(1) - z2.re, T(0) - z2.im};
+  // arm coefficients of X, Y, Z
+  const Cplx<T> x01 = cmul(w, cadd(c10, cmul(z, c01)));
+  const Cplx<T> x02 = cmul(w, cadd(c20, cmul(z, c02)));
+  const Cplx<T> y12 = cmul(w, cadd(c21, cmul(z, c12)));
+  const Cplx<T> y01 = cmul(w, cadd(c01, cmul(z, c10)));
+  const Cplx<T> z02 = cmul(w, cadd(c02, cmul(z, c20)));
+  const Cplx<T> z12 = cmul(w, cadd(c12, cmul(z, c21)));
+  // X = x01 P01 - x02 P02; Y = y12 P12 - y01 P01; Z = z02 P02 - z12 P12
+  const T r2 = T(0.7071067811865476), r6 = T(0.4082482904638631);
+  // A = (Z - X)/sqrt2
+  out.C[0][0] = {T(0) - x01.re * r2, T(0) - x01.im * r2};
+  out.C[0][1] = {(z02.re + x02.re) * r2, (z02.im + x02.im) * r2};
+  out.C[0][2] = {T(0) - z12.re * r2, T(0) - z12.im * r2};
+  // E = (X - 2Y + Z)/sqrt6
+  out.C[1][0] = {(x01.re + T(2) * y01.re) * r6, (x01.im + T(2) * y01.im) * r6};
+  out.C[1][1] = {(z02.re - x02.re) * r6, (z02.im - x02.im) * r6};
+  out.C[1][2] = {(T(0) - T(2) * y12.re - z12.re) * r6, (T(0) - T(2) * y12.im - z12.im) * r6};
 }
 
 // Out-of-line entry: keeps the transfer's registers out of the calling kernel's

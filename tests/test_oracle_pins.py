@@ -441,9 +441,10 @@ def test_sky_and_polarisation_average_of_antenna_power():
 # Gradient
 # ---------------------------------------------------------------------------------------
 
-def test_gradient_against_central_differences(small_ae):
+@pytest.mark.parametrize("resp", [RESP_LW, 2])
+def test_gradient_against_central_differences(small_ae, resp):
     D = small_ae
-    kw = dict(pn_order=PN_1PN, response=RESP_LW)
+    kw = dict(pn_order=PN_1PN, response=resp)
     th = synth.candidates_near(D.injections, 6, seed=3)
     u, g = oracle.gradient(D.d, D.w, D.mask, th, 16, D.dT, **kw)
     # fourth-order (5-point) central differences; steps chosen so that the phase moves
