@@ -97,7 +97,7 @@ __device__ __forceinline__ LevelState levels_of(const EvalArgs& a, int64_t i) {
 // Response factors of Eq. tdi2: T_alpha = F+ A+ - i Fx Ax in the long-wavelength limit
 // (resp 1), or the TDI-1.5 transfer at the tranche's frequency f (resp 2), evaluated
 // in the arithmetic type T.
-template <class T>
+template <class T, bool TDI>
 __device__ __forceinline__ void response_factors(const TplConst& c, const TrancheD& tr, double f,
                                                  int resp, T Tr[2], T Ti[2]) {
   if (!resp) {
@@ -105,19 +105,19 @@ __device__ __forceinline__ void response_factors(const TplConst& c, const Tranch
     Ti[0] = Ti[1] = T(0);
     return;
   }
-  if (resp == 2) {
+  if (TDI) {
     T pp[6], px[6];
     for (int k = 0; k < 6; ++k) {
       pp[k] = T(c.pp[k]);
       px[k] = T(c.px[k]);
     }
-    T o[4];
-    tdi_transfer_call<T>(T(f), T(tr.ca), T(tr.sa), T(c.dop_c / kAuS), T(c.dop_s / kAuS), T(c.nz),
-                         pp, px, o);
-    Tr[0] = o[0];
-    Ti[0] = o[1];
-    Tr[1] = o[2];
-    Ti[1] = o[3];
+    Cplx<T> TA, TE;
+    tdi_transfer<T>(T(f), T(tr.ca), T(tr.sa), T(c.dop_c / kAuS), T(c.dop_s / kAuS), T(c.nz), pp,
+                    px, TA, TE);
+    Tr[0] = TA.re;
+    Ti[0] = TA.im;
+    Tr[1] = TE.re;
+    Ti[1] = TE.im;
     return;
   }
   const double* DA = tr.DA;
@@ -140,6 +140,9 @@ __device__ __forceinline__ void response_factors(const TplConst& c, const Tranch
 // -------------------------------------------------------------------------------------
 // FP64 parity kernel
 // -------------------------------------------------------------------------------------
+// TDI: the TDI-1.5 response (code 2) as its own instantiation (the long-wavelength
+// kernel carries none of its code).
+template <bool TDI>
 __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n_tpl) return;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
     if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
 
     double Tr[2], Ti[2];
-    response_factors<double>(c, tr, tk.f, a.response, Tr, Ti);
+    response_factors<double, TDI>(c, tr, tk.f, a.response, Tr, Ti);
     const double aa = x - kcd;                    // in (-1, 0]
     const double sig = g.df * sqrt(2.0 / tk.fdot);  // v = sig * (f_nm - f_k)/df
     const double e2 = sqrt(2.0 * tk.fdot) * g.dT;   // v_2 - v_1
@@ -286,6 +289,7 @@ __device__ __forceinline__ void fresnel_cs_plain(double v, float& C, float& S) {
   }
 }
 
+template <bool TDI>
 __global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n_tpl) return;
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
     if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
 
     float Tr[2], Ti[2];
-    response_factors<float>(c, tr, tk.f, a.response, Tr, Ti);
+    response_factors<float, TDI>(c, tr, tk.f, a.response, Tr, Ti);
     const double s2d = sqrt(2.0 * tk.fdot);
     const double inv_fdot = 1.0 / tk.fdot;
     const float P = (float)(pow(tk.fsrc / c.F0, 2.0 / 3.0) / s2d);
@@ -397,13 +401,19 @@ __global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
 
 cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
-  k_eval_fp64<<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  if (a.response == 2)
+    k_eval_fp64<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  else
+    k_eval_fp64<false><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
-  k_eval_plain<<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  if (a.response == 2)
+    k_eval_plain<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+  else
+    k_eval_plain<false><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -211,24 +211,4 @@ __device__ __forceinline__ void tdi_arms(T f, G ca, G sa, T nx, T ny, T nz, TdiA
   out.C[1][2] = {(T(0) - T(2) * y12.re - z12.re) * r6, (T(0) - T(2) * y12.im - z12.im) * r6};
 }
 
-// Out-of-line entry: keeps the transfer's registers out of the calling kernel's
-// allocation (its long-wavelength path stays as it is). out = (Re T_A, Im T_A, Re T_E,
-// Im T_E).
-template <class T>
-__device__ __noinline__ void tdi_transfer_call(T f, T ca, T sa, T nx, T ny, T nz, const T* pp,
-                                               const T* px, T* out) {
-  T p6[6], x6[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    p6[k] = pp[k];
-    x6[k] = px[k];
-  }
-  Cplx<T> TA, TE;
-  tdi_transfer<T>(f, ca, sa, nx, ny, nz, p6, x6, TA, TE);
-  out[0] = TA.re;
-  out[1] = TA.im;
-  out[2] = TE.re;
-  out[3] = TE.im;
-}
-
 }  // namespace tfs
