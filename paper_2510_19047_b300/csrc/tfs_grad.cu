@@ -231,7 +231,7 @@ struct Trk {
   float cph, sph;          // e^{i phi}
   float P;                 // A / sqrt(2 fdot)
   float f, fdot, amp, u, tpr, y, y2, onec, fsrc, fdsrc, d1, d2, ca, sa;  // tpr = t'/t_c = 1 - u
-  double ud, yd, tprd;  // u, y, t'/t_c from their double-float values (for the phase terms)
+  df ud, yd, tprd;  // u, y, t'/t_c as double-floats (for the phase terms)
   float Tr[2], Ti[2];      // response (no amplitude)
 };
 
@@ -297,9 +297,9 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   k.P = k.amp * rsqrt_approx(2.0f * fdot);
   k.u = u.hi;
   k.tpr = tpr.hi;
-  k.ud = (double)u.hi + (double)u.lo;
-  k.yd = (double)y.hi + (double)y.lo;
-  k.tprd = (double)tpr.hi + (double)tpr.lo;
+  k.ud = u;
+  k.yd = y;
+  k.tprd = tpr;
   k.y = y.hi;
   k.y2 = y2f;
   k.onec = onec.hi;
@@ -344,22 +344,23 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
 }
 
 // FP32 copies of the template constants the reverse-mode step uses (radians for P5, P3),
-// and FP64 ones for its phase terms.
+// and double-float ones for its phase terms (P5, P3 in cycles).
 struct SrcF {
   float tc, tc_inv, inv8tc, F0, C2, P5, P3;
-  double tc_inv_d, P5d, P3d;
+  df tc_inv_d, P5c, P3c;
 };
 
 // Reverse-mode step of the track for one tranche: given the tranche's sensitivities
 // of Upsilon to (f, fdot, phi, ln A, T_alpha), its contribution to the adjoints g of
 // the template constants (tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6]). The phase's
-// shares of the t_c, P5 and P3 adjoints, gph = (tc, P5, P3), are formed in FP64: they
-// are large and cancel each other in the final contraction (the phase's leading term
-// 2 pi f0 t does not depend on M_c or eta), so FP32 rounding there would dominate.
+// shares of the t_c, P5 and P3 adjoints, gph = (tc, P5, P3), are formed in double-float
+// arithmetic (gph[0] in cycles, the others per radian of phase): they are large and
+// cancel each other in the final contraction (the phase's leading term 2 pi f0 t does
+// not depend on M_c or eta), so FP32 rounding there would dominate.
 __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, const Trk& k,
                                               const TrancheF& tr, float cf, float cfd, float cphi,
                                               float cP, const float cTr[2], const float cTi[2],
-                                              float g[kSrcFields], double gph[3]) {
+                                              float g[kSrcFields], df gph[3]) {
   const float op1 = 1.0f + k.d1;
   const float g_fsrc = cf * op1 + cfd * k.d2;
   const float g_fdsrc = cfd * op1 * op1;
@@ -375,19 +376,21 @@ __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, 
          cP * (2.0f / 3.0f) * y2 * ionec;
   g[1] = s.F0 != 0.0f ? (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) / s.F0 : 0.0f;
   // phase: Phi = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u^(5/8) = u y^3
-  const double cphd = cphi;
-  const double y2d = k.yd * k.yd, y3d = y2d * k.yd;
-  const double u58 = k.ud * y3d;
-  gph[1] = cphd * (1.0 - u58);
-  gph[2] = cphd * (1.0 - u58 * y2d);
-  const double gu_ph = -cphd * (0.625 * s.P5d * y3d + 0.375 * s.P3d * y3d * y2d);
-  gph[0] = gu_ph * k.tprd * s.tc_inv_d;  // du/dtc = t'/tc^2
+  const df y2d = df_sqr(k.yd), y3d = df_mul(y2d, k.yd);
+  const df u58 = df_mul(k.ud, y3d);
+  gph[1] = df_mul_f(one_minus(u58), cphi);
+  gph[2] = df_mul_f(one_minus(df_mul(u58, y2d)), cphi);
+  // dPhi/du [cycles] = -(5/8) P5 y^3 - (3/8) P3 y^5
+  const df dph = df_add(df_mul_f(df_mul(s.P5c, y3d), 0.625f),
+                        df_mul_f(df_mul(df_mul(s.P3c, y3d), y2d), 0.375f));
+  const df gu_ph = df_mul_f(dph, -cphi);                       // cycles
+  gph[0] = df_mul(df_mul(gu_ph, k.tprd), s.tc_inv_d);          // du/dtc = t'/tc^2
   g[3] = 0.0f;
   g[4] = 0.0f;
   g[5] = cphi;
   const float g_u = -g_y * y / (8.0f * k.u);
   g[0] = (g_u * k.tpr - g_fdsrc * k.fdsrc) * s.tc_inv;
-  const float g_u_all = g_u + (float)gu_ph;  // for the delay amplitudes
+  const float g_u_all = g_u + (float)(2.0 * kPi) * gu_ph.hi;  // for the delay amplitudes
   for (int q = 6; q < kSrcFields; ++q) g[q] = 0.0f;
   if (a.response) {
     const float g_tp = -g_u_all * s.tc_inv;
@@ -483,9 +486,9 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   sf.C2 = (float)tc.C2;
   sf.P5 = (float)tc.P5;
   sf.P3 = (float)tc.P3;
-  sf.tc_inv_d = 1.0 / tc.tc;
-  sf.P5d = tc.P5;
-  sf.P3d = tc.P3;
+  sf.tc_inv_d = df_make(1.0 / tc.tc);
+  sf.P5c = df_make(tc.P5 * (0.5 / kPi));
+  sf.P3c = df_make(tc.P3 * (0.5 / kPi));
   for (int q = lane; q < a.n_seg; q += 32) seg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   // derivatives of the template constants with respect to theta: lane p < 8 takes
   // direction p (FP64 forward mode, once per template)
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     const int m = m0 + lane;
     float gl[kSrcFields];
     for (int k = 0; k < kSrcFields; ++k) gl[k] = 0.0f;
-    double gph[3] = {0.0, 0.0, 0.0};
+    df gph[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     Trk L;
     L.ok = false;
     if (m < tc.m_hi) L = track_df<TDI>(a, cp, m);
@@ -677,11 +680,14 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
         track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
       }
     }
+    // warp sums in double-float, then FP64 once per block (gph[0] is in cycles)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double v = gph[k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
-      G[k == 0 ? 0 : k + 2] += v;  // t_c, P5, P3
+      df v = gph[k];
+      for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, df{__shfl_xor_sync(kFullG, v.hi, o), __shfl_xor_sync(kFullG, v.lo, o)});
+      const double vd = (double)v.hi + (double)v.lo;
+      G[k == 0 ? 0 : k + 2] += k == 0 ? 2.0 * kPi * vd : vd;  // t_c, P5, P3
     }
 #pragma unroll
     for (int k = 0; k < kSrcFields; ++k) {
