@@ -815,6 +815,10 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   if ((r = device_view(c, theta, (size_t)n_tpl * 64, c->theta, s, &th))) return r;
   if ((r = buf_ensure(c, c->tpl, (size_t)n_tpl * sizeof(TplConst)))) return r;
   if ((r = buf_ensure(c, c->tplm, (size_t)n_tpl * sizeof(TplMix)))) return r;
+  if ((r = buf_ensure(c, c->counter, 64))) return r;
+  if (c->opt.sort && ((r = buf_ensure(c, c->perm, (size_t)n_tpl * 4)) ||
+                      (r = buf_ensure(c, c->sortbuf, sort_scratch_bytes(n_tpl)))))
+    return r;
   // the FP32 pixel plane: the mixed plane itself when it is FP32, else a copy packed once
   // per set of noise weights
   const void* plane = c->Umix.p;
@@ -845,13 +849,24 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, c->g, (TplConst*)c->tpl.p,
                            (TplMix*)c->tplm.p, s));
   prof_record(c, 1, s);
+  c->launches = 1;
+  // longest templates first, as for the statistic kernel's queue
+  const int32_t* perm = nullptr;
+  if (c->opt.sort) {
+    int nl = 0;
+    CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
+                               c->n_sm, s, &nl));
+    c->launches += nl;
+    perm = (const int32_t*)c->perm.p;
+  }
   prof_record(c, 2, s);
   const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);
   CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
                           (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
-                          (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og, s));
-  c->launches = 2;
+                          (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og,
+                          (unsigned*)c->counter.p, perm, c->n_sm, s));
+  c->launches += 1;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));

@@ -40,7 +40,8 @@ cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const As
 //   dUpsilon = sum_n Re(lambda_n dZ_n) + mu_n dN_n,
 //   lambda_n = 2 s conj(Z_n) / N_n,  mu_n = -s |Z_n|^2 / N_n^2,  Upsilon = s sum |Z_n|^2/N_n
 // (s folds the constant 4 delta f and the storage scales of u and w). One warp per
-// template, one lane per tranche. Pass A forms Z_n, N_n in shared memory; pass B
+// template, one lane per tranche; the warps of a persistent launch take templates from a
+// longest-first queue. Pass A forms Z_n, N_n in shared memory; pass B
 // recomputes the track (it is never stored), the per-bin sums of the Fresnel-kernel
 // derivatives with respect to v_1, v_2 and Psi, and turns them into the tranche's
 // sensitivities to (f, fdot, phi, A, T_alpha). A reverse-mode step through the track
@@ -50,6 +51,10 @@ cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const As
 // accumulates in FP64, and at the end contracts them with the constants' derivatives
 // with respect to theta (FP64 forward mode, one direction per parameter, once per
 // template). Pixels come from an FP32 frequency-major plane (coalesced across lanes).
+// Bins with |v_1|, |v_2| > 6 take the paper's asymptotic Fresnel form in both passes, so
+// their sums reduce to sums of u and w with real weights (powers of 1/v), folded into
+// the complex sums once per tranche; only the warp's union of the other bins takes the
+// full form.
 // The window position and the Fresnel branch are held fixed: the almost-everywhere
 // derivative.
 // ---------------------------------------------------------------------------------
@@ -163,6 +168,24 @@ __device__ __forceinline__ DF4 operator+(float b, DF4 a) {
   return a;
 }
 
+// Window-relative bins jp = j - 10 that need the general Fresnel form (|v| <= 6 for v1
+// or v2, or the sweep [v1, v2] holding 0), joined over the warp: the other bins take
+// the asymptotic form W = (i/pi)(1/v1 - e^{i Psi}/v2), whose sums reduce to sums of
+// u and w with real weights. Every lane of the warp must call this.
+__device__ __forceinline__ void general_range(bool ok, float aa, float eps, float sig, int& JLO,
+                                              int& JHI) {
+  int jlo = 100, jhi = -100;
+  if (ok) {
+    const float r6 = 6.0f / sig;
+    jlo = (int)ceilf(aa - r6 - 0.01f);
+    jhi = (int)floorf(aa + eps + r6 + 0.01f);
+  }
+  JLO = __reduce_min_sync(0xffffffffu, jlo);
+  JHI = __reduce_max_sync(0xffffffffu, jhi);
+}
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
 }  // namespace
 
 template <>
@@ -218,6 +241,8 @@ struct GradArgs {
   double scale;         // Upsilon = scale * sum |Z|^2 / N
   double* out_stat;
   double* out_grad;     // [8][n]
+  unsigned* counter;    // work ticket of the persistent launch (zero at launch)
+  const int32_t* perm;  // queue order (longest templates first), or null for 0..n-1
 };
 
 // The track at the start of tranche m: the mixed kernel's double-float evaluation
@@ -463,15 +488,11 @@ __device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, con
 
 }  // namespace
 
-// TDI: the TDI-1.5 response (code 2), as its own instantiation.
+// Statistic and gradient of template i by one warp. seg: this warp's n_seg float4
+// slots in shared memory; dsrc: its 8 x kSrcFields derivative table.
 template <bool TDI>
-__global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
-  extern __shared__ float4 s_seg[];
-  __shared__ double s_dsrc[kGradWarps][8][kSrcFields];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kGradWarps + warp;
-  if (i >= a.n_tpl) return;  // whole warp leaves together
-  float4* seg = s_seg + (size_t)warp * a.n_seg;
+__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane, float4* seg,
+                                         double (*dsrc)[kSrcFields]) {
   const int nch = a.g.n_chan;
   const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
   double th[8];
@@ -496,7 +517,7 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     D1 thd[8];
     for (int p = 0; p < 8; ++p) thd[p] = mk(th[p], p == lane ? 1.0 : 0.0);
     const SrcT<D1> sd = source_of<D1>(thd, a.pn_order);
-    double* o = s_dsrc[warp][lane];
+    double* o = dsrc[lane];
     o[0] = sd.tc.d;
     o[1] = sd.F0.d;
     o[2] = sd.C2.d;
@@ -518,12 +539,44 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     const int m = m0 + lane;
     const bool inr = m < tc.m_hi;
     float Zr = 0.f, Zi = 0.f, Nn = 0.f;
-    if (inr) {
-      const Trk L = track_df<TDI>(a, cp, m);
+    Trk L;
+    L.ok = false;
+    if (inr) L = track_df<TDI>(a, cp, m);
+    int JLO, JHI;
+    general_range(L.ok, L.aa, L.eps, L.sig, JLO, JHI);
+    {
       if (L.ok) {
-        float zr[2] = {0, 0}, zi[2] = {0, 0}, nn[2] = {0, 0};
+        const int g0 = max(0, min(kNF, JLO + kNFHalf)), g1 = max(g0, min(kNF, JHI + kNFHalf + 1));
         const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
-        for (int j = 0; j < kNF; ++j) {
+        float zr[2], zi[2], nn[2];
+        {
+          // asymptotic bins: A1 = sum u/v1, A2 = sum u/v2, Q = sum w |pi W|^2 (channels
+          // paired); sum conj(u) W over them = (i/pi)(conj(A1) - e^{i Psi} conj(A2))
+          float2 A1r = f2(0.f), A1i = f2(0.f), A2r = f2(0.f), A2i = f2(0.f), Q = f2(0.f);
+          const float m2c = -2.0f * L.cps;
+          for (int j = 0; j < kNF; ++j) {
+            if (j == g0) j = g1;
+            if (j >= kNF) break;
+            const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
+            const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+            const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
+            const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
+            A1r = __ffma2_rn(ur, f2(q1), A1r);
+            A1i = __ffma2_rn(ui, f2(q1), A1i);
+            A2r = __ffma2_rn(ur, f2(q2), A2r);
+            A2i = __ffma2_rn(ui, f2(q2), A2i);
+            Q = __ffma2_rn(make_float2(w.x, w.y), f2(fmaf(q1, fmaf(m2c, q2, q1), q2 * q2)), Q);
+          }
+          const float ip = (float)(1.0 / kPi), ip2 = ip * ip;
+          const float c = L.cps, sn = L.sps;
+          zr[0] = ip * (A1i.x + sn * A2r.x - c * A2i.x);
+          zi[0] = ip * (A1r.x - c * A2r.x - sn * A2i.x);
+          nn[0] = ip2 * Q.x;
+          zr[1] = ip * (A1i.y + sn * A2r.y - c * A2i.y);
+          zi[1] = ip * (A1r.y - c * A2r.y - sn * A2i.y);
+          nn[1] = ip2 * Q.y;
+        }
+        for (int j = g0; j < g1; ++j) {  // general bins
           const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
           const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
           const BinW b = bin_w<false>(v1, v1 + L.e2, L.cps, L.sps);
@@ -600,18 +653,95 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
     Trk L;
     L.ok = false;
     if (m < tc.m_hi) L = track_df<TDI>(a, cp, m);
+    int JLO, JHI;
+    general_range(L.ok, L.aa, L.eps, L.sig, JLO, JHI);
     if (L.ok) {
       const float4 lm = seg[m / a.seg_len];
       const float lr = lm.x, li = lm.y, mu = lm.z;
+      // general bins j in [g0, g1) (warp-uniform); the rest take the asymptotic form
+      const int g0 = max(0, min(kNF, JLO + kNFHalf)), g1 = max(g0, min(kNF, JHI + kNFHalf + 1));
+      const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
       // per channel: complex sums S0..S3, S1v, S2v and real sums R0..R3, R1v, R2v
       float S[2][6][2], R[2][6];
-      for (int c = 0; c < 2; ++c)
-        for (int q = 0; q < 6; ++q) {
-          S[c][q][0] = S[c][q][1] = 0.f;
-          R[c][q] = 0.f;
+      {
+        // asymptotic bins (q = 1/v, channels paired): complex sums of u with weights
+        // q1, q2, q1^2, q2^2, v1 q2^2 and real sums of w with weights q1^2, q2^2, q1 q2,
+        // q1^3, q1^2 q2, q1 q2^2, q2^3, v1 q2^3
+        float2 A1r = f2(0.f), A1i = f2(0.f), A2r = f2(0.f), A2i = f2(0.f), B1r = f2(0.f),
+               B1i = f2(0.f), B2r = f2(0.f), B2i = f2(0.f), C2r = f2(0.f), C2i = f2(0.f);
+        float2 Q11 = f2(0.f), Q22 = f2(0.f), Q12 = f2(0.f), Q111 = f2(0.f), Q112 = f2(0.f),
+               Q122 = f2(0.f), Q222 = f2(0.f), V222 = f2(0.f);
+        for (int j = 0; j < kNF; ++j) {
+          if (j == g0) j = g1;
+          if (j >= kNF) break;
+          const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
+          const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+          const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
+          const float q11 = q1 * q1, q22 = q2 * q2, q12 = q1 * q2;
+          const float vq22 = v1 * q22;
+          const float2 ur = make_float2(u4.x, u4.y), ui = make_float2(u4.z, u4.w);
+          const float2 wv = make_float2(w4.x, w4.y);
+          A1r = __ffma2_rn(ur, f2(q1), A1r);
+          A1i = __ffma2_rn(ui, f2(q1), A1i);
+          A2r = __ffma2_rn(ur, f2(q2), A2r);
+          A2i = __ffma2_rn(ui, f2(q2), A2i);
+          B1r = __ffma2_rn(ur, f2(q11), B1r);
+          B1i = __ffma2_rn(ui, f2(q11), B1i);
+          B2r = __ffma2_rn(ur, f2(q22), B2r);
+          B2i = __ffma2_rn(ui, f2(q22), B2i);
+          C2r = __ffma2_rn(ur, f2(vq22), C2r);
+          C2i = __ffma2_rn(ui, f2(vq22), C2i);
+          Q11 = __ffma2_rn(wv, f2(q11), Q11);
+          Q22 = __ffma2_rn(wv, f2(q22), Q22);
+          Q12 = __ffma2_rn(wv, f2(q12), Q12);
+          Q111 = __ffma2_rn(wv, f2(q11 * q1), Q111);
+          Q112 = __ffma2_rn(wv, f2(q11 * q2), Q112);
+          Q122 = __ffma2_rn(wv, f2(q12 * q2), Q122);
+          Q222 = __ffma2_rn(wv, f2(q22 * q2), Q222);
+          V222 = __ffma2_rn(wv, f2(vq22 * q2), V222);
         }
-      const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
-      for (int j = 0; j < kNF; ++j) {
+        // the asymptotic bins' S and R: with k = 1/pi and e = e^{i Psi} = c + i s,
+        //   W = k i (q1 - e q2), dW/dv1 = -k i q1^2, dW/dv2 = k i e q2^2, dW/dPsi = k e q2,
+        //   v1 dW/dv1 = -k i q1, v1 dW/dv2 = k i e v1 q2^2,
+        // so each sum of conj(u) X is a constant times the conjugate of a sum above; and
+        //   |W|^2 = k^2 (q1^2 + q2^2 - 2 c q1 q2), 2 Re(conj(W) dW/dv1) = -2k^2 (q1^3 - c q1^2 q2),
+        //   2 Re(conj(W) dW/dv2) = 2k^2 (c q1 q2^2 - q2^3), 2 Re(conj(W) dW/dPsi) = 2k^2 s q1 q2,
+        //   and v1 times the v1, v2 ones: -2k^2 (q1^2 - c q1 q2) and 2k^2 (c q2^2 - v1 q2^3)
+        const float k1 = (float)(1.0 / kPi), k2 = k1 * k1;
+        const float c = L.cps, sn = L.sps;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          const float a1r = ch ? A1r.y : A1r.x, a1i = ch ? A1i.y : A1i.x;
+          const float a2r = ch ? A2r.y : A2r.x, a2i = ch ? A2i.y : A2i.x;
+          const float b1r = ch ? B1r.y : B1r.x, b1i = ch ? B1i.y : B1i.x;
+          const float b2r = ch ? B2r.y : B2r.x, b2i = ch ? B2i.y : B2i.x;
+          const float c2r = ch ? C2r.y : C2r.x, c2i = ch ? C2i.y : C2i.x;
+          S[ch][0][0] = k1 * (a1i + sn * a2r - c * a2i);
+          S[ch][0][1] = k1 * (a1r - c * a2r - sn * a2i);
+          S[ch][1][0] = -k1 * b1i;
+          S[ch][1][1] = -k1 * b1r;
+          S[ch][2][0] = -k1 * (sn * b2r - c * b2i);
+          S[ch][2][1] = k1 * (c * b2r + sn * b2i);
+          S[ch][3][0] = k1 * (c * a2r + sn * a2i);
+          S[ch][3][1] = k1 * (sn * a2r - c * a2i);
+          S[ch][4][0] = -k1 * a1i;
+          S[ch][4][1] = -k1 * a1r;
+          S[ch][5][0] = -k1 * (sn * c2r - c * c2i);
+          S[ch][5][1] = k1 * (c * c2r + sn * c2i);
+          const float q11 = ch ? Q11.y : Q11.x, q22 = ch ? Q22.y : Q22.x, q12 = ch ? Q12.y : Q12.x;
+          const float q111 = ch ? Q111.y : Q111.x, q112 = ch ? Q112.y : Q112.x;
+          const float q122 = ch ? Q122.y : Q122.x, q222 = ch ? Q222.y : Q222.x;
+          const float v222 = ch ? V222.y : V222.x;
+          R[ch][0] = k2 * (q11 + q22 - 2.f * c * q12);
+          R[ch][1] = -2.f * k2 * (q111 - c * q112);
+          R[ch][2] = 2.f * k2 * (c * q122 - q222);
+          R[ch][3] = 2.f * k2 * sn * q12;
+          R[ch][4] = -2.f * k2 * (q11 - c * q12);
+          R[ch][5] = 2.f * k2 * (c * q22 - v222);
+        }
+      }
+      // general bins: the paper's Fresnel form and its derivatives per bin
+      for (int j = g0; j < g1; ++j) {
         const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
         const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
         const BinW b = bin_w<true>(v1, v1 + L.e2, L.cps, L.sps);
@@ -699,8 +829,28 @@ __global__ void __launch_bounds__(kGradWarps * 32) k_grad(GradArgs a) {
   // d Upsilon / d theta_p = sum_k G_k d(constant_k)/d theta_p
   if (lane < 8) {
     double v = 0.0;
-    for (int k = 0; k < kSrcFields; ++k) v = fma(G[k], s_dsrc[warp][lane][k], v);
+    for (int k = 0; k < kSrcFields; ++k) v = fma(G[k], dsrc[lane][k], v);
     a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
+  }
+}
+
+// Persistent launch: every warp takes templates from the queue until it is empty, so
+// the long templates (first in the sorted queue) do not leave a tail of idle SMs.
+// TDI: the TDI-1.5 response (code 2), as its own instantiation.
+template <bool TDI>
+__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : 3) k_grad(GradArgs a) {
+  extern __shared__ float4 s_seg[];
+  __shared__ double s_dsrc[kGradWarps][8][kSrcFields];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* seg = s_seg + (size_t)warp * a.n_seg;
+  for (;;) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(kFullG, t, 0);
+    if ((int64_t)t >= a.n_tpl) break;  // whole warp leaves together
+    const int64_t i = a.perm ? (int64_t)a.perm[t] : (int64_t)t;
+    grad_one<TDI>(a, i, lane, seg, s_dsrc[warp]);
+    __syncwarp();  // seg and dsrc are rewritten by the next template
   }
 }
 
@@ -708,7 +858,7 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        cudaStream_t s) {
+                        unsigned* counter, const int32_t* perm, int n_sm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   GradArgs a;
   a.g = g;
@@ -728,11 +878,20 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.scale = scale;
   a.out_stat = out_stat;
   a.out_grad = out_grad;
+  a.counter = counter;
+  a.perm = perm;
   const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
   auto kern = response == 2 ? k_grad<true> : k_grad<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)((n + kGradWarps - 1) / kGradWarps), kGradWarps * 32, smem, s>>>(a);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (n + kGradWarps - 1) / kGradWarps;
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)ctas, kGradWarps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,6 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        cudaStream_t s);
+                        unsigned* counter, const int32_t* perm, int n_sm, cudaStream_t s);
 
 }  // namespace tfs
