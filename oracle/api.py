@@ -41,6 +41,18 @@ def _lib():
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
             _D, _D, _D, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             _D, ctypes.c_int, _D, _D, _D, _D]
+        lib.oracle_statistic_harm.restype = ctypes.c_int
+        lib.oracle_statistic_harm.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+            _D, _D, _D, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, _D, _D, _D,
+            _D, ctypes.c_int64, ctypes.c_int, _D, _I32, _I32, _I32, ctypes.c_int]
+        lib.oracle_segments_harm.restype = ctypes.c_int
+        lib.oracle_segments_harm.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+            _D, _D, _D, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, _D, _D, _D,
+            _D, ctypes.c_int, _D, _D, _D, _D]
         lib.oracle_fresnel.restype = None
         lib.oracle_fresnel.argtypes = [ctypes.c_int, _D, ctypes.c_int64, _D, _D]
         lib.oracle_tranche_ft.restype = None
@@ -151,6 +163,61 @@ def segments(d, w, mask, theta8, n_seg, dT, t0=0.0, pn_order=PN_NEWTONIAN,
         _p(th), int(n_seg), _p(zr), _p(zi), _p(nn), _p(ups))
     if rc != 0:
         raise ValueError(f"oracle_segments failed with code {rc}")
+    return zr + 1j * zi, nn, float(ups[0])
+
+
+def _harmonics(nu, c):
+    nu = np.ascontiguousarray(np.atleast_1d(nu), dtype=np.float64)
+    c = np.atleast_1d(np.asarray(c, dtype=np.complex128))
+    if nu.ndim != 1 or c.shape != nu.shape or nu.size < 1:
+        raise ValueError("nu and c must be 1-D of the same length >= 1")
+    return nu, np.ascontiguousarray(c.real), np.ascontiguousarray(c.imag)
+
+
+def statistic_harm(d, w, mask, theta, n_seg, dT, nu, c, t0=0.0, pn_order=PN_NEWTONIAN,
+                   response=RESP_NONE, fresnel_mode=FRESNEL_PAPER, n_threads=0):
+    """Upsilon_{N_seg} of multi-harmonic templates: harmonic h has phase nu[h] Phi,
+    frequency nu[h] f, derivative nu[h] fdot and amplitude c[h] A.
+
+    Returns (stat[n], n_eff[n], n_active[n], n_noncompact[n]).
+    """
+    d_re, d_im, w, m = _grid(d, w, mask)
+    nu, cr, ci = _harmonics(nu, c)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.ndim != 2 or th.shape[0] != 8:
+        raise ValueError("theta must be SoA [8, n_tpl]")
+    n = th.shape[1]
+    out = np.zeros(n)
+    neff = np.zeros(n, np.int32)
+    nact = np.zeros(n, np.int32)
+    nnc = np.zeros(n, np.int32)
+    rc = _lib().oracle_statistic_harm(
+        d_re.shape[0], d_re.shape[1], d_re.shape[2], float(dT), float(t0),
+        _p(d_re), _p(d_im), _p(w), _p(m, _U8), int(pn_order), int(response), int(fresnel_mode),
+        nu.size, _p(nu), _p(cr), _p(ci),
+        _p(th), n, int(n_seg), _p(out), _p(neff, _I32), _p(nact, _I32), _p(nnc, _I32),
+        int(n_threads))
+    if rc != 0:
+        raise ValueError(f"oracle_statistic_harm failed with code {rc}")
+    return out, neff, nact, nnc
+
+
+def segments_harm(d, w, mask, theta8, n_seg, dT, nu, c, t0=0.0, pn_order=PN_NEWTONIAN,
+                  response=RESP_NONE, fresnel_mode=FRESNEL_PAPER):
+    """Per-segment Z_n (complex) and N_n of one multi-harmonic template, and Upsilon."""
+    d_re, d_im, w, m = _grid(d, w, mask)
+    nu, cr, ci = _harmonics(nu, c)
+    th = np.ascontiguousarray(theta8, dtype=np.float64).ravel()
+    zr = np.zeros(n_seg)
+    zi = np.zeros(n_seg)
+    nn = np.zeros(n_seg)
+    ups = np.zeros(1)
+    rc = _lib().oracle_segments_harm(
+        d_re.shape[0], d_re.shape[1], d_re.shape[2], float(dT), float(t0),
+        _p(d_re), _p(d_im), _p(w), _p(m, _U8), int(pn_order), int(response), int(fresnel_mode),
+        nu.size, _p(nu), _p(cr), _p(ci), _p(th), int(n_seg), _p(zr), _p(zi), _p(nn), _p(ups))
+    if rc != 0:
+        raise ValueError(f"oracle_segments_harm failed with code {rc}")
     return zr + 1j * zi, nn, float(ups[0])
 
 

@@ -52,10 +52,21 @@
 //     phase advanced inside one segment instead of inside the whole track.
 //   * a segment with <y|y>_n = 0 (no active tranche) adds nothing; N_eff counts the
 //     segments that do contribute.
+//   * multi-harmonic templates (Sec. "Outlook": {A, f, fdot, phi} per harmonic, then
+//     the Fresnel expressions per harmonic): harmonic h has phase nu_h Phi(t'),
+//     frequency nu_h f_nm, derivative nu_h fdot_nm and amplitude c_h A (complex c_h),
+//     with the dominant mode's polarisation content (the TDI-1.5 transfer taken at the
+//     harmonic's frequency). The tranche's template is the sum of the harmonics'
+//     21-bin windows, so a bin inside two windows carries both and <y|y> keeps the
+//     cross terms. A harmonic whose window leaves [1, N_bins-1] adds nothing; the
+//     tranche needs t'_nm < t_c and fdot_nm > 0 as before. The phases are absolute
+//     (phi_0 included): the harmonics' relative phases change along the track, so they
+//     do not cancel per segment.
 
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -691,6 +702,108 @@ static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp
   return neff;
 }
 
+// Harmonic set of a multi-harmonic template: n harmonics (nu_h, c_h).
+struct Harmonics {
+  int n;
+  const double *nu, *c_re, *c_im;
+};
+
+// Absolute phase Phi(t') = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u = 1 - t'/t_c,
+// with 1 - u^p = -expm1(p log1p(-t'/t_c)).
+template <class R>
+static R phase_abs(const Source<R>& s, const R& tprime) {
+  const R l = log1p_(-tprime / s.tc);
+  return s.phi0 + s.P5 * (-expm1_(0.625 * l)) + s.P3 * (-expm1_(0.375 * l));
+}
+
+// Upsilon_{N_seg} of a multi-harmonic template, Eq. Upsilon-seg with the template of
+// each tranche written out bin by bin as the sum of its harmonics' Eq. fresnel-ft
+// windows. Returns N_eff.
+template <class R>
+static int statistic_harm_one(const Grid& g, const R th[NPAR], int pn_order, int resp,
+                              int fmode, const Harmonics& H, int n_seg, R& out, Diag* diag,
+                              double* seg_zr = nullptr, double* seg_zi = nullptr,
+                              double* seg_n = nullptr) {
+  const Source<R> src = make_source(th, pn_order);
+  const int seg_len = g.n_tranche / n_seg;
+  R ups(0.0);
+  int neff = 0, nact = 0, nnc = 0;
+  for (int n = 0; n < n_seg; ++n) {
+    const double t_anchor = g.t0 + (double)n * seg_len * g.dT;
+    R a0, a1, a2;
+    doppler(src, t_anchor, resp, a0, a1, a2);
+    const R tp_anchor = t_anchor + a0;
+    // Phi at the anchor; track_point gives the phase advanced from there
+    const R phi_anchor = val(tp_anchor) < val(src.tc) ? phase_abs(src, tp_anchor) : R(0.0);
+    Cx<R> Z = {R(0.0), R(0.0)};
+    R N(0.0);
+    for (int m = n * seg_len; m < (n + 1) * seg_len; ++m) {
+      if (g.mask && !g.mask[m]) continue;
+      const double tm = g.t0 + (double)m * g.dT;
+      const TrackPoint<R> tp = track_point(src, resp, tm, t_anchor);
+      if (!tp.alive) continue;
+      if (!(val(tp.fdot) > 0.0)) continue;
+      const R phi = phi_anchor + tp.dphi;
+      // the tranche's template per channel, bin -> value (T_alpha included)
+      std::map<long, Cx<R>> y[2];
+      bool any = false;
+      for (int h = 0; h < H.n; ++h) {
+        const R fh = H.nu[h] * tp.f, fdh = H.nu[h] * tp.fdot;
+        const long kc = (long)std::ceil(lval(fh) / (long double)g.df);
+        if (kc - NF_HALF < 1 || kc + NF_HALF > g.n_bins - 1) continue;
+        any = true;
+        Cx<R> T[2];
+        if (resp == 0) {
+          T[0] = {R(1.0), R(0.0)};
+          T[1] = {R(1.0), R(0.0)};
+        } else if (resp == 2) {
+          tdi_transfer(src, tm, fh, g.n_chan, T);
+        } else {
+          response(src, tm, g.n_chan, T);
+        }
+        const Cx<R> ch = {R(H.c_re[h]), R(H.c_im[h])};
+        for (int j = 0; j < NF; ++j) {
+          const long k = kc - NF_HALF + j;
+          const Cx<R> hk = tranche_ft_bin(tp.amp, H.nu[h] * phi, fh, fdh, g.dT, k * g.df, fmode);
+          for (int c = 0; c < g.n_chan; ++c) {
+            Cx<R>& v = y[c].emplace(k, Cx<R>{R(0.0), R(0.0)}).first->second;
+            v = cadd(v, cmul(cmul(T[c], ch), hk));
+          }
+        }
+      }
+      if (!any) continue;
+      ++nact;
+      if (val(tp.fdot) * g.dT > 10.0 * g.df) ++nnc;
+      for (int c = 0; c < g.n_chan; ++c) {
+        for (const auto& kv : y[c]) {
+          const size_t idx = ((size_t)c * g.n_tranche + m) * g.n_bins + kv.first;
+          const double wr = g.w[idx] * g.df;
+          const double dr = g.d_re[idx], di = g.d_im[idx];
+          const Cx<R>& v = kv.second;
+          Z.re += (dr * v.re + di * v.im) * wr;  // conj(d) y w delta f
+          Z.im += (dr * v.im - di * v.re) * wr;
+          N += (v.re * v.re + v.im * v.im) * wr;
+        }
+      }
+    }
+    if (seg_zr) {
+      seg_zr[n] = val(Z.re);
+      seg_zi[n] = val(Z.im);
+      seg_n[n] = val(N);
+    }
+    if (val(N) > 0.0) {
+      ups += 4.0 * (Z.re * Z.re + Z.im * Z.im) / N;
+      ++neff;
+    }
+  }
+  out = ups;
+  if (diag) {
+    diag->n_active = nact;
+    diag->n_noncompact = nnc;
+  }
+  return neff;
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -779,6 +892,61 @@ int oracle_segments(int n_chan, int n_tranche, int n_bins, double dT, double t0,
   long double ups;
   statistic_one<long double>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, nullptr, zr, zi,
                              nn);
+  if (out_stat) *out_stat = (double)ups;
+  return ORC_OK;
+}
+
+// Upsilon_{N_seg} of multi-harmonic templates: as oracle_statistic, with n_harm
+// harmonics (nu[h] > 0, complex amplitude c_re[h] + i c_im[h]) shared by all templates.
+int oracle_statistic_harm(int n_chan, int n_tranche, int n_bins, double dT, double t0,
+                          const double* d_re, const double* d_im, const double* w,
+                          const uint8_t* mask, int pn_order, int resp, int fresnel_mode,
+                          int n_harm, const double* nu, const double* c_re, const double* c_im,
+                          const double* theta, int64_t n_tpl, int n_seg, double* out_stat,
+                          int32_t* out_neff, int32_t* out_nact, int32_t* out_nnc, int n_threads) {
+  if (!grid_ok(n_chan, n_tranche, n_bins, dT) || n_tpl < 0 || !theta || !out_stat) return ORC_ERR_ARG;
+  if (n_harm < 1 || !nu || !c_re || !c_im) return ORC_ERR_ARG;
+  for (int h = 0; h < n_harm; ++h)
+    if (!(nu[h] > 0.0)) return ORC_ERR_ARG;
+  if (n_seg < 1 || n_tranche % n_seg != 0) return ORC_ERR_NSEG;
+  Grid g{n_chan, n_tranche, n_bins, dT, t0, 1.0 / dT, d_re, d_im, w, mask};
+  const Harmonics H{n_harm, nu, c_re, c_im};
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t i = 0; i < n_tpl; ++i) {
+    long double th[NPAR];
+    for (int p = 0; p < NPAR; ++p) th[p] = theta[p * n_tpl + i];
+    long double ups;
+    Diag dg;
+    const int neff =
+        statistic_harm_one<long double>(g, th, pn_order, resp, fresnel_mode, H, n_seg, ups, &dg);
+    out_stat[i] = (double)ups;
+    if (out_neff) out_neff[i] = neff;
+    if (out_nact) out_nact[i] = dg.n_active;
+    if (out_nnc) out_nnc[i] = dg.n_noncompact;
+  }
+  return ORC_OK;
+}
+
+// Per-segment Z_n, N_n of one multi-harmonic template (as oracle_segments).
+int oracle_segments_harm(int n_chan, int n_tranche, int n_bins, double dT, double t0,
+                         const double* d_re, const double* d_im, const double* w,
+                         const uint8_t* mask, int pn_order, int resp, int fresnel_mode,
+                         int n_harm, const double* nu, const double* c_re, const double* c_im,
+                         const double* th8, int n_seg, double* zr, double* zi, double* nn,
+                         double* out_stat) {
+  if (!grid_ok(n_chan, n_tranche, n_bins, dT) || !th8 || !zr || !zi || !nn) return ORC_ERR_ARG;
+  if (n_harm < 1 || !nu || !c_re || !c_im) return ORC_ERR_ARG;
+  if (n_seg < 1 || n_tranche % n_seg != 0) return ORC_ERR_NSEG;
+  Grid g{n_chan, n_tranche, n_bins, dT, t0, 1.0 / dT, d_re, d_im, w, mask};
+  const Harmonics H{n_harm, nu, c_re, c_im};
+  long double th[NPAR];
+  for (int p = 0; p < NPAR; ++p) th[p] = th8[p];
+  long double ups;
+  statistic_harm_one<long double>(g, th, pn_order, resp, fresnel_mode, H, n_seg, ups, nullptr,
+                                  zr, zi, nn);
   if (out_stat) *out_stat = (double)ups;
   return ORC_OK;
 }
