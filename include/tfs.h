@@ -147,6 +147,27 @@ int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const i
 int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream);
 
+/* Harmonic content of the templates (Sec. "Outlook": the time-frequency waveform
+ * extends to several harmonics by computing {A, f, fdot, phi} for each harmonic and
+ * applying the Fresnel expressions to each). n_harm = 0, the default, evaluates the
+ * single dominant mode described above. With n_harm in [1, TFS_MAX_HARMONICS],
+ * harmonic h of every template has phase nu[h] Phi(t'), frequency nu[h] f_nm,
+ * derivative nu[h] fdot_nm and amplitude c[h] A with c[h] = c_re[h] + i c_im[h], and
+ * the dominant mode's polarisation content (with response 2 the transfer is taken at
+ * the harmonic's frequency). Each harmonic has its own 21-bin window about
+ * ceil(nu[h] f_nm / delta f), used only where it lies inside [1, N_bins - 1]; the
+ * tranche's template is the sum of the windows, so a bin inside two windows carries
+ * both and N_n keeps the cross terms. Phases are absolute (phi_0 included): the
+ * harmonics' relative phases do not cancel per segment. A tranche is active when it
+ * passes the tests above with at least one window in band.
+ *   nu: double [n_harm], each in (0, 16]; c_re, c_im: double [n_harm], finite; host
+ *   pointers, copied (NULL allowed when n_harm = 0).
+ * Applies to tfs_eval_statistic on the FP64 and mixed paths; the plain path and
+ * tfs_grad_statistic return TFS_ERR_ARG while n_harm > 0. */
+#define TFS_MAX_HARMONICS 8
+int tfs_set_harmonics(tfs_ctx* ctx, int n_harm, const double* nu, const double* c_re,
+                      const double* c_im);
+
 /* Indices of the k largest values of stat[n] (ties broken by the lower index), in
  * decreasing order of stat, into out_index int64 [k]: the survivors of one stage of
  * the adaptive N_seg ladder (Sec. "Time-frequency search statistic": N_seg is reduced

@@ -72,6 +72,7 @@ def load_library(build_if_missing=True):
         "tfs_get_options": (i32, [P, ctypes.POINTER(Options)]),
         "tfs_load_tf_data": (i32, [P, i32, i32, i32, dbl, dbl, dbl, P, P]),
         "tfs_set_noise_weights": (i32, [P, P, P]),
+        "tfs_set_harmonics": (i32, [P, i32, P, P, P]),
         "tfs_eval_statistic": (i32, [P, P, i64, P, i32, i32, P, P, P, P]),
         "tfs_grad_statistic": (i32, [P, P, i64, ctypes.c_int32, P, P, P]),
         "tfs_select_top": (i32, [P, P, i64, i64, P, P]),
@@ -249,6 +250,23 @@ class TFS:
         if scalar or per_template:
             return stat[0], neff[0], dg
         return stat, neff, dg
+
+    def set_harmonics(self, nu=(), c=()):
+        """Harmonic content of the templates: harmonic h has phase nu[h] Phi, frequency
+        nu[h] f, derivative nu[h] fdot and complex amplitude c[h] (relative to the
+        dominant mode's A). Empty (the default) = the dominant mode alone."""
+        nu = np.ascontiguousarray(np.atleast_1d(np.asarray(nu, dtype=np.float64)))
+        c = np.atleast_1d(np.asarray(c, dtype=np.complex128))
+        if nu.shape != c.shape or nu.ndim != 1:
+            raise ValueError("nu and c must be 1-D of the same length")
+        cr = np.ascontiguousarray(c.real)
+        ci = np.ascontiguousarray(c.imag)
+        if nu.size == 0:
+            self._check(self.lib.tfs_set_harmonics(self.h, 0, None, None, None))
+        else:
+            self._check(self.lib.tfs_set_harmonics(
+                self.h, int(nu.size), nu.ctypes.data_as(ctypes.c_void_p),
+                cr.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p)))
 
     def grad_statistic(self, theta, n_seg):
         """(Upsilon [n], d Upsilon / d theta [8, n]) at one N_seg."""

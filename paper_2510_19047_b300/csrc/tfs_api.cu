@@ -52,6 +52,10 @@ struct tfs_ctx {
   double su = 1.0, sw = 1.0;
   // per-call scratch
   DevBuf theta, tpl, tplm, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
+  // harmonic content of the templates (n = 0: the dominant mode) and its per-template
+  // constant phases (mixed path)
+  HarmSet harm{};
+  DevBuf harmK;
   // profiling
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   double prof[4] = {0, 0, 0, 0};
@@ -346,7 +350,8 @@ int tfs_destroy(tfs_ctx* c) {
   DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
-                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ};
+                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad,
+                   &c->harmK};
   for (DevBuf* b : all) buf_free(c, *b);
   for (int i = 0; i < 5; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -368,6 +373,44 @@ int tfs_set_options(tfs_ctx* c, const tfs_options* o) {
 int tfs_get_options(const tfs_ctx* c, tfs_options* o) {
   if (!c || !o) return TFS_ERR_ARG;
   *o = c->opt;
+  return TFS_OK;
+}
+
+int tfs_set_harmonics(tfs_ctx* c, int n_harm, const double* nu, const double* c_re,
+                      const double* c_im) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (n_harm < 0 || n_harm > TFS_MAX_HARMONICS)
+    return fail(c, TFS_ERR_ARG, "n_harm must be in [0, " + std::to_string(TFS_MAX_HARMONICS) + "]");
+  if (n_harm > 0 && (!nu || !c_re || !c_im)) return fail(c, TFS_ERR_ARG, "null argument");
+  if (n_harm > 0 && (is_device_ptr(nu) || is_device_ptr(c_re) || is_device_ptr(c_im)))
+    return fail(c, TFS_ERR_ARG, "harmonics must be given in host memory");
+  HarmSet h{};
+  h.n = n_harm;
+  h.dnu_min = 0.f;
+  for (int i = 0; i < n_harm; ++i) {
+    if (!(nu[i] > 0.0 && nu[i] <= 16.0)) return fail(c, TFS_ERR_ARG, "nu must be in (0, 16]");
+    if (!std::isfinite(c_re[i]) || !std::isfinite(c_im[i]))
+      return fail(c, TFS_ERR_ARG, "harmonic amplitudes must be finite");
+    h.nu[i] = nu[i];
+    h.cr[i] = c_re[i];
+    h.ci[i] = c_im[i];
+    h.nu_hi[i] = (float)nu[i];
+    h.nu_lo[i] = (float)(nu[i] - (double)h.nu_hi[i]);
+    h.crf[i] = (float)c_re[i];
+    h.cif[i] = (float)c_im[i];
+  }
+  double dmin = 0.0;
+  for (int i = 0; i < n_harm; ++i)
+    for (int j = i + 1; j < n_harm; ++j) {
+      const double d = std::fabs(nu[i] - nu[j]);
+      if (dmin == 0.0 || d < dmin) dmin = d;
+      if (d == 0.0) dmin = -1.0;  // equal nu: the windows always coincide
+    }
+  // windows of two harmonics can share bins only below f/df = 21 / dnu_min; equal nu
+  // (always) is a tiny positive value
+  h.dnu_min = dmin < 0.0 ? 1e-30f : (float)dmin;
+  c->harm = h;
   return TFS_OK;
 }
 
@@ -528,7 +571,10 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   c->launches = 0;
   c->prof_valid = false;
   if (n_tpl == 0) return TFS_OK;
-  const bool graph = path == TFS_PATH_MIXED && c->opt.use_graph;
+  const bool harm = c->harm.n > 0;
+  if (harm && path == TFS_PATH_PLAIN)
+    return fail(c, TFS_ERR_ARG, "multi-harmonic templates need the FP64 or mixed path");
+  const bool graph = path == TFS_PATH_MIXED && c->opt.use_graph && !harm;
   // inputs: device theta is read in place, host theta is copied; a graph always reads
   // the context's own copy so that its pointers stay fixed between replays
   const void* th = nullptr;
@@ -601,6 +647,8 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.dev_err = (int*)c->counter.p + 8;
   a.checked = c->opt.checked;
   a.out_scale = path == TFS_PATH_FP64 ? 4.0 * g.df : 4.0 * g.df * c->sw / (c->su * c->su);
+  a.harm = c->harm;
+  a.harm_K = nullptr;
 
   auto setup = [&](cudaStream_t st) -> int {
     prof_record(c, 0, st);
@@ -621,7 +669,25 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     if (herr) return fail(c, TFS_ERR_DEVICE_CHECK, "a template's tranche range lies outside the grid");
   }
 
-  if (path == TFS_PATH_MIXED) {
+  if (path == TFS_PATH_MIXED && harm) {
+    // multi-harmonic mixed launch: set-up, constant phases per harmonic, sort, kernel
+    if ((r = buf_ensure(c, c->harmK, (size_t)n_tpl * c->harm.n * sizeof(float2)))) return r;
+    if (!c->opt.checked && (r = setup(s))) return r;
+    CUDA_TRY(c, launch_harm_phase((const TplConst*)c->tpl.p, n_tpl, c->harm, (float2*)c->harmK.p, s));
+    c->launches += 1;
+    a.harm_K = (const float2*)c->harmK.p;
+    if (c->opt.sort) {
+      int nl = 0;
+      CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
+                                 c->n_sm, s, &nl));
+      c->launches += nl;
+      a.perm = (const int32_t*)c->perm.p;
+    }
+    prof_record(c, 2, s);
+    CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
+    CUDA_TRY(c, launch_eval_harm(a, g.n_chan, c->opt.pixel, c->n_sm, s));
+    c->launches += 1;
+  } else if (path == TFS_PATH_MIXED) {
     if (!c->opt.checked && (r = setup(s))) return r;
     int warps = 8, ctas = 1;
     const bool must_time = !c->opt.warps_per_cta &&
@@ -806,6 +872,8 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
     return fail(c, TFS_ERR_NSEG, "N_t = " + std::to_string(c->g.n_tranche) +
                                      " is not divisible by N_seg = " + std::to_string(n_seg));
   if (n_seg > kMixedMaxFine) return fail(c, TFS_ERR_ARG, "the gradient kernel supports N_seg <= 1024");
+  if (c->harm.n > 0)
+    return fail(c, TFS_ERR_ARG, "the gradient supports the dominant mode only (n_harm = 0)");
   if (n_tpl == 0) return TFS_OK;
   if (!theta || !out_stat || !out_grad) return fail(c, TFS_ERR_ARG, "null argument");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");

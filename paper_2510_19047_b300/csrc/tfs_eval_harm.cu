@@ -1,0 +1,405 @@
+// Mixed-precision evaluation of Upsilon_{N_seg} for multi-harmonic templates (Sec.
+// "Outlook": the quantities {A, f, fdot, phi} of each harmonic, then the Fresnel
+// expressions per harmonic). Same mapping and arithmetic as tfs_eval_mixed.cu: one
+// warp per template, one lane per tranche, persistent CTAs on the sorted queue,
+// FP16/BF16/FP32 pixels with FP32 sums and a double-float phase track.
+//
+// Per tranche (lane) the track is computed once: x = f_nm / df (double-float), fdot,
+// the amplitude, S = (P5 u^(5/8) + P3 u^(3/8)) / 2 pi (double-float cycles) and the
+// long-wavelength response. Harmonic h then has x_h = nu_h x, fdot_h = nu_h fdot,
+// window centre ceil(x_h), sigma_h = df sqrt(2 / fdot_h), Psi_h, and phase
+// frac(nu_h K) - nu_h S cycles (K = (phi0 + P5 + P3) / 2 pi; frac(nu_h K) per template
+// from the FP64 set-up), amplitude c_h A and, for TDI-1.5, the transfer at nu_h f_nm.
+// Its window sums are the mixed kernel's: the general bins of every lane joined over
+// the warp, the rest in the asymptotic form from two reciprocals.
+//
+// N_n holds the cross terms 2 Re(conj(T_a) T_b sum_k w_k conj(W''^a_k) W''^b_k) of the
+// bins two windows share. Windows of nu_a, nu_b can share bins only where
+// |nu_a - nu_b| f_nm / df < 21; lanes that may see such a pair evaluate the shared bins
+// one by one with the general W'' (a rare path at the bank's frequencies for harmonics
+// nu = j / 2).
+#include <math.h>
+#include <stddef.h>
+
+#include <algorithm>
+
+#include "tfs_internal.cuh"
+#include "tfs_kernels.cuh"
+#include "tfs_mixed_bins.cuh"
+#include "tfs_tdi.cuh"
+
+namespace tfs {
+
+namespace {
+
+// The harmonic-independent part of a tranche's track.
+struct TrackH {
+  df x;        // f_nm / df
+  df S;        // (P5 u^(5/8) + P3 u^(3/8)) / 2 pi
+  float fdot;  // fdot_nm
+  float amp;   // (f / F0)^(2/3)
+  float f;     // f_nm (FP32, for the TDI transfer)
+  float fpA, fxA, fpE, fxE;  // long-wavelength F+, Fx of A and E
+};
+
+// One harmonic's window geometry and template factors T_alpha (amplitude, phase, c_h
+// and response included) in one tranche.
+struct HarmM {
+  bool act;
+  int kc;
+  float aa, eps, sig, cpsi, spsi;
+  float Tr0, Ti0, Tr1, Ti1;
+};
+
+template <bool TDI>
+__device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
+                                         const TrancheF& tr, float2 Kh, int h, float sig_k,
+                                         float dTf) {
+  HarmM q;
+  q.act = false;
+  const df nu = {a.harm.nu_hi[h], a.harm.nu_lo[h]};
+  const df x = df_mul(tk.x, nu);
+  const bool inband = x.hi > (float)kNFHalf && x.hi < (float)(a.g.n_bins - kNFHalf);
+  float kcf = rint_small(inband ? x.hi : 0.0f);  // ceil(x) = rint(x) (+1 if below x)
+  if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
+  q.kc = int_small(kcf);
+  q.aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
+  if (!inband || q.kc - kNFHalf < 1 || q.kc + kNFHalf > a.g.n_bins - 1) return q;
+  q.act = true;
+  const float fdh = nu.hi * tk.fdot;
+  q.sig = sig_k * rsqrt_approx(fdh);
+  q.eps = fdh * dTf * dTf;
+  const float psi = fmaf(2.0f, q.aa, q.eps);  // Psi / pi, reduced to [-1, 1]
+  __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &q.spsi, &q.cpsi);
+  // phase frac(nu K) - nu S in cycles, reduced in two steps as in the mixed kernel
+  const df ph = df_sub(df{Kh.x, Kh.y}, df_mul(tk.S, nu));
+  float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
+  cyc = __fsub_rn(cyc, rint_small(cyc));
+  float sph, cph;
+  __sincosf(6.283185307f * cyc, &sph, &cph);
+  // c_h A e^{i phi_h}
+  const float cr = a.harm.crf[h], ci = a.harm.cif[h];
+  const float er = tk.amp * (cph * cr - sph * ci), ei = tk.amp * (cph * ci + sph * cr);
+  q.Tr0 = q.Tr1 = er;
+  q.Ti0 = q.Ti1 = ei;
+  if (a.response) {
+    float fpA = tk.fpA, fxA = tk.fxA, fpE = tk.fpE, fxE = tk.fxE;
+    if (TDI) {  // TDI-1.5 transfer at (t_nm, nu_h f_nm)
+      const float4* pq = reinterpret_cast<const float4*>(cptr->pp);
+      const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
+      const float4 nq = ldg_nc4(pq + 3);  // (nx, ny, nz, pad)
+      const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+      const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+      Cplx<float> TA, TE;
+      tdi_transfer<float>(nu.hi * tk.f, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
+      fpA = TA.re;
+      fxA = -TA.im;
+      fpE = TE.re;
+      fxE = -TE.im;
+    }
+    // (F+ - i Fx)(er + i ei)
+    q.Tr0 = fmaf(fpA, er, fxA * ei);
+    q.Ti0 = fmaf(fpA, ei, -fxA * er);
+    q.Tr1 = fmaf(fpE, er, fxE * ei);
+    q.Ti1 = fmaf(fpE, ei, -fxE * er);
+  }
+  return q;
+}
+
+}  // namespace
+
+template <int NCH, int PIX, bool TDI>
+__global__ void __launch_bounds__(256, 2) k_eval_harm(EvalArgs a) {
+  extern __shared__ float4 s_acc[];
+  using Ld = PixLoad<PIX>;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  float4* acc = s_acc + (size_t)warp * a.fine_cap;
+  const GridDesc g = a.g;
+  const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
+  const int pitch = a.pitch;
+  const int H = a.harm.n;
+  const df dTd = df_make(g.dT);
+  const float dTf = (float)g.dT;
+  const float sig_k = (float)(sqrt(2.0) * g.df);   // sigma = df sqrt(2/fdot)
+  const float ncomp = (float)(10.0 * g.df / g.dT);  // fdot > 10 df / dT: non-compact
+  // windows of two harmonics can share bins only below x = 21 / dnu_min (+ margin);
+  // equal nu (dnu_min tiny) always, a single harmonic never
+  const float x_ov = H > 1 ? 21.5f / a.harm.dnu_min : 0.0f;
+
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= a.n_work) break;
+    const int idx = a.perm ? a.perm[t] : t;
+    const TplMix* __restrict__ cptr = a.tplm + idx;
+    const float2* __restrict__ Kp = a.harm_K + (int64_t)idx * H;
+    const int m_lo = cptr->m_lo, m_hi = cptr->m_hi;
+
+    int nl, fine_len;
+    int seg_len[kMaxLevels];
+    if (a.nseg_pt) {
+      nl = 1;
+      seg_len[0] = g.n_tranche / a.nseg_pt[idx];
+      fine_len = seg_len[0];
+    } else {
+      nl = a.lv.n;
+#pragma unroll
+      for (int l = 0; l < kMaxLevels; ++l) seg_len[l] = a.lv.seg_len[l];
+      fine_len = a.lv.fine_len;
+    }
+    const int n_fine = g.n_tranche / fine_len;
+    for (int q = lane; q < n_fine; q += 32) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int nact = 0, nnc = 0;
+    __syncwarp();
+
+    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
+      const int m = m0 + lane;
+      const bool inr = m < m_hi;
+      bool act = inr && a.mask[m];
+      TrackH tk;
+      tk.x = df{0.f, 0.f};
+      tk.S = df{0.f, 0.f};
+      tk.fdot = 1.f;
+      tk.amp = tk.f = 0.f;
+      tk.fpA = tk.fxA = tk.fpE = tk.fxE = 0.f;
+      TrancheF tr;
+      if (act) {
+        const float4* cq = reinterpret_cast<const float4*>(cptr);
+        const float4 c0 = ldg_nc4(cq), c1 = ldg_nc4(cq + 1), c2 = ldg_nc4(cq + 2),
+                     c3 = ldg_nc4(cq + 3);
+        const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
+        const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
+        const df dopc = {c2.z, c2.w}, dops = {c3.x, c3.y};
+        const float C2 = c3.z, fd_k = c3.w;
+        tr = a.tabF[m];
+        const df tt = {tr.t_hi, tr.t_lo};
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (a.response) {
+          d0 = fmaf(dopc.hi, tr.ca_hi, dops.hi * tr.sa_hi);
+          d1 = (float)kOmega * (dops.hi * tr.ca_hi - dopc.hi * tr.sa_hi);
+          d2 = -(float)(kOmega * kOmega) * d0;
+        }
+        const df tp = quick_add_f(tt, d0);
+        const df u = one_minus(df_mul(tp, tc_inv));  // 1 - t'/t_c
+        if (!(u.hi > 0.f)) {
+          act = false;
+        } else {
+          // y = u^(-1/8): FP32 seed, one Newton step with a double-float residual
+          const float y0 = pow_m18(u.hi);
+          const df y02 = two_prod(y0, y0);
+          const df y08 = df_sqr(df_sqr(y02));
+          const df p = df_mul(u, y08);
+          const float r = __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo);
+          const df y = quick_two_sum(y0, y0 * r * 0.125f);
+          const df y2 = df_sqr(y);
+          const df y3 = df_mul(y2, y);
+          const float c2y2 = C2 * y2.hi;
+          const df fs = df_mul(df_mul(F0, y3), two_sum(1.0f, c2y2));
+          const df f = quick_add_f(fs, fs.hi * d1);
+          const float y2f = y2.hi, y3f = y3.hi;
+          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
+          tk.fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
+          tk.x = df_mul(f, dTd);
+          tk.f = f.hi;
+          if (!(tk.fdot > 0.f)) {
+            act = false;
+          } else {
+            tk.S = df_mul(df_mul(u, y3), df_add(P5, df_mul(P3, y2)));
+            tk.amp = y2f * fmaf(c2y2, fmaf(c2y2, fmaf(c2y2, 4.0f / 81.0f, -1.0f / 9.0f), 2.0f / 3.0f),
+                                1.0f);
+            if (a.response && !TDI) {
+              const float4* pq = reinterpret_cast<const float4*>(cptr->pp);
+              const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
+              const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+              const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                tk.fpA = fmaf(tr.DA[q], pp[q], tk.fpA);
+                tk.fxA = fmaf(tr.DA[q], px[q], tk.fxA);
+                tk.fpE = fmaf(tr.DE[q], pp[q], tk.fpE);
+                tk.fxE = fmaf(tr.DE[q], px[q], tk.fxE);
+              }
+            }
+          }
+        }
+      }
+      float Zr = 0.f, Zi = 0.f, Nn = 0.f;
+      bool any = false;
+      for (int h = 0; h < H; ++h) {
+        HarmM q;
+        q.act = false;
+        if (act) q = harm_of<TDI>(a, tk, cptr, tr, Kp[h], h, sig_k, dTf);
+        // general-bin range of the harmonic, joined over the warp (as in the mixed kernel)
+        int jlo = 100, jhi = -100;
+        if (q.act) {
+          const float r6 = 6.0f * rcp_approx(q.sig);
+          jlo = (int)ceilf(q.aa - r6 - 0.01f);
+          jhi = (int)floorf(q.aa + q.eps + r6 + 0.01f);
+        }
+        const int JLO = __reduce_min_sync(kFull, jlo), JHI = __reduce_max_sync(kFull, jhi);
+        if (!q.act) continue;
+        any = true;
+        const typename Ld::P* Pp = PX + (int64_t)(q.kc - kNFHalf) * pitch + m;
+        const float spi = q.sig * (float)kPi;
+        const float ae = q.aa + q.eps;
+        const float m2c = -2.0f * q.cpsi;
+        BinAcc s;
+        s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
+        typename Ld::P cur = Ld::raw(Pp);
+        float jpf = -(float)kNFHalf;
+        for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
+          typename Ld::P nxt;
+          if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
+          float2 cur_r, cur_i, cur_w;
+          Ld::cvt(cur, cur_r, cur_i, cur_w);
+          const int jp = j - kNFHalf;
+          const float x1 = q.aa - jpf, x2 = ae - jpf;
+          if (jp >= JLO && jp <= JHI) {
+            float wr, wi;
+            w_general(x1, x2, q.sig, spi, q.cpsi, q.spsi, true, wr, wi);
+            acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+          } else {
+            acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
+          }
+          if (j + 1 < kNF) cur = nxt;
+        }
+        // sum conj(u) W'' = i conj(U1) - i e^{i Psi} conj(U2), both channels at once
+        const float2 ncp = make_float2(-q.cpsi, -q.cpsi);
+        const float2 zr = __ffma2_rn(make_float2(q.spsi, q.spsi), s.u2r, __ffma2_rn(ncp, s.u2i, s.u1i));
+        const float2 zi = __ffma2_rn(ncp, s.u2r, __ffma2_rn(make_float2(-q.spsi, -q.spsi), s.u2i, s.u1r));
+        Zr += q.Tr0 * zr.x - q.Ti0 * zi.x;
+        Zi += q.Tr0 * zi.x + q.Ti0 * zr.x;
+        Nn += (q.Tr0 * q.Tr0 + q.Ti0 * q.Ti0) * s.nn.x;
+        if (NCH == 2) {
+          Zr += q.Tr1 * zr.y - q.Ti1 * zi.y;
+          Zi += q.Tr1 * zi.y + q.Ti1 * zr.y;
+          Nn += (q.Tr1 * q.Tr1 + q.Ti1 * q.Ti1) * s.nn.y;
+        }
+      }
+      // cross terms of windows that share bins
+      if (any && tk.x.hi < x_ov) {
+        for (int ha = 0; ha < H; ++ha) {
+          const HarmM A = harm_of<TDI>(a, tk, cptr, tr, Kp[ha], ha, sig_k, dTf);
+          if (!A.act) continue;
+          for (int hb = ha + 1; hb < H; ++hb) {
+            const HarmM B = harm_of<TDI>(a, tk, cptr, tr, Kp[hb], hb, sig_k, dTf);
+            if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
+            // conj(T_a) T_b per channel
+            const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
+            const float y1r = A.Tr1 * B.Tr1 + A.Ti1 * B.Ti1, y1i = A.Tr1 * B.Ti1 - A.Ti1 * B.Tr1;
+            const int k0 = max(A.kc, B.kc) - kNFHalf, k1 = min(A.kc, B.kc) + kNFHalf;
+            for (int k = k0; k <= k1; ++k) {
+              const float ja = (float)(k - A.kc), jb = (float)(k - B.kc);
+              float war, wai, wbr, wbi;
+              w_general(A.aa - ja, A.aa + A.eps - ja, A.sig, A.sig * (float)kPi, A.cpsi, A.spsi,
+                        true, war, wai);
+              w_general(B.aa - jb, B.aa + B.eps - jb, B.sig, B.sig * (float)kPi, B.cpsi, B.spsi,
+                        true, wbr, wbi);
+              const float xr = war * wbr + wai * wbi, xi = war * wbi - wai * wbr;  // conj(Wa) Wb
+              float2 ur, ui, w;
+              Ld::cvt(Ld::raw(PX + (int64_t)k * pitch + m), ur, ui, w);
+              Nn += 2.0f * w.x * (y0r * xr - y0i * xi);
+              if (NCH == 2) Nn += 2.0f * w.y * (y1r * xr - y1i * xi);
+            }
+          }
+        }
+      }
+      if (any) {
+        ++nact;
+        if (tk.fdot > ncomp) ++nnc;
+      }
+      // segmented (by finest segment) suffix sums across the warp; the first lane of
+      // each run adds its segment's sum to shared memory
+      const int key = inr ? m / fine_len : 0x7fffffff;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float zr2 = __shfl_down_sync(kFull, Zr, o);
+        const float zi2 = __shfl_down_sync(kFull, Zi, o);
+        const float n2 = __shfl_down_sync(kFull, Nn, o);
+        const int k2 = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && k2 == key) {
+          Zr += zr2;
+          Zi += zi2;
+          Nn += n2;
+        }
+      }
+      const int kprev = __shfl_up_sync(kFull, key, 1);
+      if (inr && (lane == 0 || kprev != key)) {
+        float4 v = acc[key];
+        v.x += Zr;
+        v.y += Zi;
+        v.z += Nn;
+        acc[key] = v;
+      }
+    }
+    __syncwarp();
+    for (int l = 0; l < nl; ++l) {
+      const int r = seg_len[l] / fine_len;
+      const int ns = g.n_tranche / seg_len[l];
+      float ups = 0.f;
+      int ne = 0;
+      for (int n = lane; n < ns; n += 32) {
+        float zr = 0.f, zi = 0.f, nn = 0.f;
+        for (int q = 0; q < r; ++q) {
+          const float4 v = acc[n * r + q];
+          zr += v.x;
+          zi += v.y;
+          nn += v.z;
+        }
+        if (nn > 0.f) {
+          ups += __fdividef(fmaf(zr, zr, zi * zi), nn);
+          ++ne;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) ups += __shfl_xor_sync(kFull, ups, o);
+      ne = __reduce_add_sync(kFull, ne);
+      if (lane == 0) {
+        a.out_stat[(int64_t)l * a.n_tpl + idx] = (double)ups * a.out_scale;
+        if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + idx] = ne;
+      }
+    }
+    nact = __reduce_add_sync(kFull, nact);
+    nnc = __reduce_add_sync(kFull, nnc);
+    if (lane == 0 && a.out_diag) {
+      a.out_diag[idx] = nact;
+      a.out_diag[a.n_tpl + idx] = nnc;
+    }
+    __syncwarp();
+  }
+}
+
+namespace {
+
+template <int NCH, int PIX>
+cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
+  constexpr int kWarps = 8;
+  const size_t smem = (size_t)kWarps * a.fine_cap * sizeof(float4);
+  auto kern = a.response == 2 ? k_eval_harm<NCH, PIX, true> : k_eval_harm<NCH, PIX, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (a.n_work + kWarps - 1) / kWarps;
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
+  kern<<<(unsigned)ctas, kWarps * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s) {
+  if (a.n_work <= 0) return cudaSuccess;
+  if (n_chan == 1) {
+    if (pix == TFS_PIX_F32) return launch_harm_one<1, TFS_PIX_F32>(a, n_sm, s);
+    if (pix == TFS_PIX_F16) return launch_harm_one<1, TFS_PIX_F16>(a, n_sm, s);
+    return launch_harm_one<1, TFS_PIX_BF16>(a, n_sm, s);
+  }
+  if (pix == TFS_PIX_F32) return launch_harm_one<2, TFS_PIX_F32>(a, n_sm, s);
+  if (pix == TFS_PIX_F16) return launch_harm_one<2, TFS_PIX_F16>(a, n_sm, s);
+  return launch_harm_one<2, TFS_PIX_BF16>(a, n_sm, s);
+}
+
+}  // namespace tfs

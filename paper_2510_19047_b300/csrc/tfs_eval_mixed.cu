@@ -26,60 +26,12 @@
 
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
+#include "tfs_mixed_bins.cuh"
 #include "tfs_tdi.cuh"
 
 namespace tfs {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// Pixel loads: one element per (bin, tranche) holds both channels of u and w,
-// ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E): one 128-bit load for
-// FP16/BF16 pixels, two for FP32. raw() loads, cvt() widens to FP32 at the point of use
-// (the prefetched element stays packed).
-template <int PIX>
-struct PixLoad;
-template <>
-struct PixLoad<TFS_PIX_F32> {
-  struct __align__(16) P {
-    float4 u, w;
-  };
-  __device__ static P raw(const P* p) { return P{__ldg(&p->u), __ldg(&p->w)}; }
-  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
-    ur = make_float2(v.u.x, v.u.y);
-    ui = make_float2(v.u.z, v.u.w);
-    w = make_float2(v.w.x, v.w.y);
-  }
-};
-template <>
-struct PixLoad<TFS_PIX_F16> {
-  using P = uint4;
-  __device__ static float2 cv(unsigned int x) {
-    __half2 h = *reinterpret_cast<__half2*>(&x);
-    return __half22float2(h);
-  }
-  __device__ static P raw(const P* p) { return __ldg(p); }
-  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
-    ur = cv(v.x);
-    ui = cv(v.y);
-    w = cv(v.z);
-  }
-};
-template <>
-struct PixLoad<TFS_PIX_BF16> {
-  using P = uint4;
-  __device__ static float2 cv(unsigned int x) {
-    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&x);
-    return __bfloat1622float2(h);
-  }
-  __device__ static P raw(const P* p) { return __ldg(p); }
-  __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
-    ur = cv(v.x);
-    ui = cv(v.y);
-    w = cv(v.z);
-  }
-};
 
 static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &&
                   offsetof(TplMix, K_hi) == 32 && offsetof(TplMix, dops_hi) == 48 &&
@@ -87,67 +39,6 @@ static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &
                   offsetof(TplMix, pp) == 64 && offsetof(TplMix, px) == 88 &&
                   offsetof(TplMix, nx) == 112,
               "TplMix layout assumed by the 16-byte loads of the mixed kernel");
-
-// The paper's auxiliary Fresnel functions f, g in FP32 with approximate division,
-// branch-free: the rational forms for a <= 6 and the printed asymptotic form
-// f = 1/(pi a), g = 0 beyond (Sec. "Fresnel integrals").
-__device__ __forceinline__ void fg_sel(float a, float& f, float& g) {
-  const bool big = a > 6.0f;
-  const float num = big ? 1.0f : fmaf(0.926f, a, 1.0f);
-  const float den = big ? (float)kPi * a : fmaf(a, fmaf(3.104f, a, 1.792f), 2.0f);
-  f = num * rcp_approx(den);
-  const float e = fmaf(a, fmaf(a, fmaf(6.670f, a, 3.492f), 4.142f), 2.0f);
-  g = big ? 0.0f : rcp_approx(e);
-}
-
-// General bin: W''_k = sigma pi W_k with W_k = s1 G(|v1|) - s2 G(|v2|) e^{i Psi}
-// + [s1 != s2] (1+i) e^{-i pi v1^2 / 2}, G = g + i f, v = sigma x.
-__device__ __forceinline__ void w_general(float x1, float x2, float sig, float spi, float cpsi,
-                                          float spsi, bool sweep, float& wr, float& wi) {
-  const float v1 = sig * x1, v2 = sig * x2;
-  float f1, g1, f2, g2;
-  fg_sel(fabsf(v1), f1, g1);
-  fg_sel(fabsf(v2), f2, g2);
-  const float s1 = v1 < 0.f ? -spi : spi, s2 = v2 < 0.f ? -spi : spi;
-  wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
-  wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
-  if (sweep && v1 < 0.f && v2 >= 0.f) {  // f_k inside this tranche's sweep
-    float sp, cp;
-    sincospif(0.5f * v1 * v1, &sp, &cp);
-    wr = fmaf(spi, cp + sp, wr);
-    wi = fmaf(spi, cp - sp, wi);
-  }
-}
-
-// Per-tranche bin sums, channels A and E paired: with real weights q = 1/x the
-// asymptotic bins need only U1 = sum u q1 and U2 = sum u q2, since
-// sum conj(u) W'' = i conj(U1) - i e^{i Psi} conj(U2) for W'' = i q1 - i e^{i Psi} q2.
-// A general bin with complex W'' adds i u conj(W'') to U1, which the same formula maps
-// back to conj(u) W''. nn = sum w |W''|^2.
-struct BinAcc {
-  float2 u1r, u1i, u2r, u2i, nn;
-};
-
-__device__ __forceinline__ void acc_asym(BinAcc& s, float2 ur, float2 ui, float2 w, float x1,
-                                         float x2, float m2c) {
-  const float q1 = rcp_approx(x1), q2 = rcp_approx(x2);
-  const float2 Q1 = make_float2(q1, q1), Q2 = make_float2(q2, q2);
-  s.u1r = __ffma2_rn(ur, Q1, s.u1r);
-  s.u1i = __ffma2_rn(ui, Q1, s.u1i);
-  s.u2r = __ffma2_rn(ur, Q2, s.u2r);
-  s.u2i = __ffma2_rn(ui, Q2, s.u2i);
-  const float ww = fmaf(q1, fmaf(m2c, q2, q1), q2 * q2);  // |W''|^2 = q1^2 + q2^2 - 2 cos(Psi) q1 q2
-  s.nn = __ffma2_rn(w, make_float2(ww, ww), s.nn);
-}
-
-__device__ __forceinline__ void acc_general(BinAcc& s, float2 ur, float2 ui, float2 w, float wr,
-                                            float wi) {
-  const float2 WR = make_float2(wr, wr), WI = make_float2(wi, wi);
-  s.u1r = __ffma2_rn(ur, WI, __ffma2_rn(ui, make_float2(-wr, -wr), s.u1r));
-  s.u1i = __ffma2_rn(ur, WR, __ffma2_rn(ui, WI, s.u1i));
-  const float ww = fmaf(wr, wr, wi * wi);
-  s.nn = __ffma2_rn(w, make_float2(ww, ww), s.nn);
-}
 
 }  // namespace
 

@@ -135,6 +135,25 @@ __device__ __forceinline__ void response_factors(const TplConst& c, const Tranch
   Ti[1] = T(-fxE);
 }
 
+// W_k of the phase-cancelled form at v_1 = (aa - jp) sig, v_2 = v_1 + e2 (FP64).
+__device__ __forceinline__ void w_fp64(double aa, int jp, double sig, double e2, double cpsi,
+                                       double spsi, double& wr, double& wi) {
+  const double v1 = (aa - (double)jp) * sig;
+  const double v2 = v1 + e2;
+  double f1, g1, f2, g2;
+  fresnel_fg<double>(fabs(v1), f1, g1);
+  fresnel_fg<double>(fabs(v2), f2, g2);
+  const double s1 = v1 < 0.0 ? -1.0 : 1.0, s2 = v2 < 0.0 ? -1.0 : 1.0;
+  wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
+  wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
+  if (s1 != s2) {
+    double sp, cp;
+    sincospi(0.5 * v1 * v1, &sp, &cp);
+    wr += cp + sp;  // (1+i) e^{-i pi v1^2/2}
+    wi += cp - sp;
+  }
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------------------------
@@ -211,20 +230,8 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
     double zcr[2] = {0, 0}, zci[2] = {0, 0}, ncc[2] = {0, 0};
     for (int j = 0; j < kNF; ++j) {
       const int k = kc - kNFHalf + j;
-      const double v1 = (aa - (double)(j - kNFHalf)) * sig;
-      const double v2 = v1 + e2;
-      double f1, g1, f2, g2;
-      fresnel_fg<double>(fabs(v1), f1, g1);
-      fresnel_fg<double>(fabs(v2), f2, g2);
-      const double s1 = v1 < 0.0 ? -1.0 : 1.0, s2 = v2 < 0.0 ? -1.0 : 1.0;
-      double wr = s1 * g1 - s2 * (g2 * cpsi - f2 * spsi);
-      double wi = s1 * f1 - s2 * (g2 * spsi + f2 * cpsi);
-      if (s1 != s2) {
-        double sp, cp;
-        sincospi(0.5 * v1 * v1, &sp, &cp);
-        wr += cp + sp;  // (1+i) e^{-i pi v1^2/2}
-        wi += cp - sp;
-      }
+      double wr, wi;
+      w_fp64(aa, j - kNFHalf, sig, e2, cpsi, spsi, wr, wi);
       const double ww = wr * wr + wi * wi;
       for (int ch = 0; ch < nch; ++ch) {
         const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
@@ -250,6 +257,200 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
       zr[l] += P * Zr;
       zi[l] += P * Zi;
       nn[l] += P * P * N;
+    }
+  }
+  for (int l = 0; l < L.n; ++l) {
+    if (nn[l] > 0.0) {
+      ups[l] += (zr[l] * zr[l] + zi[l] * zi[l]) / nn[l];
+      ++neff[l];
+    }
+    a.out_stat[(int64_t)l * a.n_tpl + i] = ups[l] * a.out_scale;
+    if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + i] = neff[l];
+  }
+  if (a.out_diag) {
+    a.out_diag[i] = nact;
+    a.out_diag[a.n_tpl + i] = nnc;
+  }
+}
+
+// -------------------------------------------------------------------------------------
+// FP64 multi-harmonic kernel (Sec. "Outlook": {A, f, fdot, phi} per harmonic, then the
+// Fresnel expressions per harmonic). Harmonic h of a tranche has frequency nu_h f_nm,
+// derivative nu_h fdot_nm, phase nu_h Phi(t'_nm) and amplitude c_h A; its 21-bin
+// window is the phase-cancelled W_k about ceil(nu_h f_nm / delta f). The tranche's
+// template y_k = sum_h Y_h W^h_k (Y_h = T_alpha c_h A / sqrt(2 nu_h fdot) e^{i phi_h})
+// gives Z = sum_h Y_h sum_k conj(u_k) W^h_k and
+// N = sum_h |Y_h|^2 sum_k w_k |W^h_k|^2 + 2 Re sum_{a<b} conj(Y_a) Y_b sum_k w_k conj(W^a_k) W^b_k,
+// the last sum over the bins two windows share. The phases are absolute: the anchor
+// block's phase since t' = 0 plus the compensated phase advanced inside the block.
+// -------------------------------------------------------------------------------------
+namespace {
+
+// One harmonic's window geometry and template factor Y in one tranche.
+struct HarmD {
+  bool on;
+  int kc;
+  double aa, sig, e2, cpsi, spsi;
+  double Yr[2], Yi[2];
+};
+
+template <bool TDI>
+__device__ __forceinline__ HarmD harm_fp64(const EvalArgs& a, const TplConst& c,
+                                           const TrancheD& tr, const TrackD& tk, double amp,
+                                           double ph_int, double ph_frac, const double Tlr[2],
+                                           const double Tli[2], int h) {
+  HarmD r;
+  r.on = false;
+  const GridDesc& g = a.g;
+  const double nu = a.harm.nu[h];
+  const double fh = nu * tk.f, fdh = nu * tk.fdot;
+  const double x = fh * g.dT;
+  const double kcd = ceil(x);
+  r.kc = (int)kcd;
+  if (r.kc - kNFHalf < 1 || r.kc + kNFHalf > g.n_bins - 1) return r;
+  r.on = true;
+  r.aa = x - kcd;
+  r.sig = g.df * sqrt(2.0 / fdh);
+  r.e2 = sqrt(2.0 * fdh) * g.dT;
+  sincospi(2.0 * r.aa + fdh * g.dT * g.dT, &r.spsi, &r.cpsi);
+  double Tr[2] = {Tlr[0], Tlr[1]}, Ti[2] = {Tli[0], Tli[1]};
+  if (TDI) response_factors<double, true>(c, tr, fh, a.response, Tr, Ti);
+  // nu (I + F) cycles, Phi / 2 pi = I + F: nu I split exactly into product and error
+  const double p = nu * ph_int;
+  const double pe = fma(nu, ph_int, -p);
+  double cyc = (p - floor(p)) + pe + nu * ph_frac;
+  cyc -= floor(cyc);
+  double sph, cph;
+  sincospi(2.0 * cyc, &sph, &cph);
+  const double P = amp / sqrt(2.0 * fdh);
+  const double er = P * (cph * a.harm.cr[h] - sph * a.harm.ci[h]);
+  const double ei = P * (cph * a.harm.ci[h] + sph * a.harm.cr[h]);
+  for (int ch = 0; ch < 2; ++ch) {
+    r.Yr[ch] = Tr[ch] * er - Ti[ch] * ei;
+    r.Yi[ch] = Tr[ch] * ei + Ti[ch] * er;
+  }
+  return r;
+}
+
+}  // namespace
+
+template <bool TDI>
+__global__ void __launch_bounds__(128) k_eval_fp64_harm(EvalArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n_tpl) return;
+  const TplConst c = a.tpl[i];
+  const LevelState L = levels_of(a, i);
+  const GridDesc g = a.g;
+  const int nch = g.n_chan;
+  const int H = a.harm.n;
+  double zr[kMaxLevels], zi[kMaxLevels], nn[kMaxLevels], ups[kMaxLevels];
+  int neff[kMaxLevels], cur[kMaxLevels];
+  for (int l = 0; l < kMaxLevels; ++l) {
+    zr[l] = zi[l] = nn[l] = ups[l] = 0.0;
+    neff[l] = 0;
+    cur[l] = -1;
+  }
+  int nact = 0, nnc = 0;
+  int blk = -1, m_prev = 0;
+  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0;
+  double ph_a = 0.0;  // Phi / 2 pi at the anchor block's first tranche
+  HarmD hd[TFS_MAX_HARMONICS];
+  for (int m = c.m_lo; m < c.m_hi; ++m) {
+    for (int l = 0; l < L.n; ++l) {
+      const int s = m / L.seg_len[l];
+      if (s != cur[l]) {
+        if (nn[l] > 0.0) {
+          ups[l] += (zr[l] * zr[l] + zi[l] * zi[l]) / nn[l];
+          ++neff[l];
+        }
+        zr[l] = zi[l] = nn[l] = 0.0;
+        cur[l] = s;
+      }
+    }
+    if (!a.mask[m]) continue;
+    const TrancheD tr = a.tabD[m];
+    const TrackD tk = track_fp64(c, tr, a.response);
+    if (!(tk.tp < c.tc)) break;
+    if (!(tk.fdot > 0.0)) continue;
+    const int b = m / L.anchor;
+    if (b != blk) {
+      blk = b;
+      m_prev = b * L.anchor;
+      const TrancheD ta = a.tabD[m_prev];
+      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
+      tp_prev = ta.t + d0_prev;
+      acc = comp = 0.0;
+      ph_a = c.phi0 * (0.5 / kPi) + phase_step_cycles(c, 0.0, tp_prev);
+    }
+    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
+    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
+    tp_prev = tk.tp;
+    d0_prev = tk.d0;
+    m_prev = m;
+    // Phi / 2 pi = ph_int + ph_frac with ph_int an integer
+    const double ph_int = floor(ph_a) + floor(acc);
+    const double ph_frac = (ph_a - floor(ph_a)) + ((acc - floor(acc)) - comp);
+
+    double Tlr[2] = {1.0, 1.0}, Tli[2] = {0.0, 0.0};
+    if (!TDI) response_factors<double, false>(c, tr, tk.f, a.response, Tlr, Tli);
+    const double amp = pow(tk.fsrc / c.F0, 2.0 / 3.0);
+    double Zr = 0.0, Zi = 0.0, N = 0.0;
+    bool any = false;
+    for (int h = 0; h < H; ++h) {
+      hd[h] = harm_fp64<TDI>(a, c, tr, tk, amp, ph_int, ph_frac, Tlr, Tli, h);
+      const HarmD& q = hd[h];
+      if (!q.on) continue;
+      any = true;
+      double zcr[2] = {0, 0}, zci[2] = {0, 0}, ncc[2] = {0, 0};
+      for (int j = 0; j < kNF; ++j) {
+        const int k = q.kc - kNFHalf + j;
+        double wr, wi;
+        w_fp64(q.aa, j - kNFHalf, q.sig, q.e2, q.cpsi, q.spsi, wr, wi);
+        const double ww = wr * wr + wi * wi;
+        for (int ch = 0; ch < nch; ++ch) {
+          const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
+          const double2 u = a.u64[px];
+          zcr[ch] += u.x * wr + u.y * wi;  // conj(u) W
+          zci[ch] += u.x * wi - u.y * wr;
+          ncc[ch] += a.w64[px] * ww;
+        }
+      }
+      for (int ch = 0; ch < nch; ++ch) {
+        Zr += q.Yr[ch] * zcr[ch] - q.Yi[ch] * zci[ch];
+        Zi += q.Yr[ch] * zci[ch] + q.Yi[ch] * zcr[ch];
+        N += (q.Yr[ch] * q.Yr[ch] + q.Yi[ch] * q.Yi[ch]) * ncc[ch];
+      }
+    }
+    if (!any) continue;
+    // cross terms of windows that share bins
+    for (int ha = 0; ha < H; ++ha) {
+      if (!hd[ha].on) continue;
+      for (int hb = ha + 1; hb < H; ++hb) {
+        if (!hd[hb].on) continue;
+        const HarmD &A = hd[ha], &B = hd[hb];
+        const int k0 = max(A.kc, B.kc) - kNFHalf, k1 = min(A.kc, B.kc) + kNFHalf;
+        for (int k = k0; k <= k1; ++k) {
+          double war, wai, wbr, wbi;
+          w_fp64(A.aa, k - A.kc, A.sig, A.e2, A.cpsi, A.spsi, war, wai);
+          w_fp64(B.aa, k - B.kc, B.sig, B.e2, B.cpsi, B.spsi, wbr, wbi);
+          // conj(W^a) W^b
+          const double xr = war * wbr + wai * wbi, xi = war * wbi - wai * wbr;
+          for (int ch = 0; ch < nch; ++ch) {
+            const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
+            // Re(conj(Y_a) Y_b (xr + i xi))
+            const double yr = A.Yr[ch] * B.Yr[ch] + A.Yi[ch] * B.Yi[ch];
+            const double yi = A.Yr[ch] * B.Yi[ch] - A.Yi[ch] * B.Yr[ch];
+            N += 2.0 * a.w64[px] * (yr * xr - yi * xi);
+          }
+        }
+      }
+    }
+    ++nact;
+    if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
+    for (int l = 0; l < L.n; ++l) {
+      zr[l] += Zr;
+      zi[l] += Zi;
+      nn[l] += N;
     }
   }
   for (int l = 0; l < L.n; ++l) {
@@ -401,6 +602,13 @@ __global__ void __launch_bounds__(128) k_eval_plain(EvalArgs a) {
 
 cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
+  if (a.harm.n > 0) {
+    if (a.response == 2)
+      k_eval_fp64_harm<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+    else
+      k_eval_fp64_harm<false><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (a.response == 2)
     k_eval_fp64<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
   else

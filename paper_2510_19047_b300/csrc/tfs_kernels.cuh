@@ -16,6 +16,18 @@ struct MixConst {
   float x_hi;          // n_bins - 10: window centres below it are in band
 };
 
+// Harmonic set of the templates (n = 0: the dominant mode alone).
+struct HarmSet {
+  int n;
+  double nu[TFS_MAX_HARMONICS];
+  double cr[TFS_MAX_HARMONICS], ci[TFS_MAX_HARMONICS];
+  // the same for the mixed path: nu as double-float, c in FP32, and the smallest
+  // |nu_a - nu_b| over pairs (windows can share bins only where dnu_min f/df < 21)
+  float nu_hi[TFS_MAX_HARMONICS], nu_lo[TFS_MAX_HARMONICS];
+  float crf[TFS_MAX_HARMONICS], cif[TFS_MAX_HARMONICS];
+  float dnu_min;
+};
+
 struct EvalArgs {
   GridDesc g;
   MixConst mc;
@@ -44,6 +56,8 @@ struct EvalArgs {
   int* counter;                 // work ticket of the persistent launch
   int* dev_err;                 // checked-mode status word
   int checked;
+  HarmSet harm;                 // harmonics (FP64 and mixed paths)
+  const float2* harm_K;         // [n_tpl][harm.n] frac(nu_h Phi_const) as double-float (mixed path)
 };
 
 cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, cudaStream_t s);
@@ -69,6 +83,12 @@ cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps,
                               cudaStream_t s);
 cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int warps, int fine_cap,
                             int* ctas_per_sm);
+// Multi-harmonic mixed launch (persistent, a.counter zeroed by the caller); a.harm_K
+// from launch_harm_phase. Chooses its own grid (n_sm x resident CTAs of 8 warps).
+cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s);
+// K[i][h] = frac(nu_h (phi0 + P5 + P3) / 2 pi) of template i as double-float.
+cudaError_t launch_harm_phase(const TplConst* tpl, int64_t n, const HarmSet& h, float2* K,
+                              cudaStream_t s);
 
 struct AscentParams {
   double step[8], lo[8], hi[8];

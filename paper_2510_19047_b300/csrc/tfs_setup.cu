@@ -363,6 +363,34 @@ cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int*
   return cudaGetLastError();
 }
 
+// Constant phase of each harmonic of each template: with Phi / 2 pi = K - S,
+// K = (phi0 + P5 + P3) / 2 pi and S = (P5 u^(5/8) + P3 u^(3/8)) / 2 pi, harmonic h has
+// phase nu_h K - nu_h S cycles; K[i][h] = frac(nu_h K) (the product split into its
+// rounded value and exact error before the fraction is taken).
+__global__ void k_harm_phase(const TplConst* __restrict__ tpl, int64_t n, HarmSet h,
+                             float2* __restrict__ K) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * h.n) return;
+  const int64_t i = t / h.n;
+  const int q = (int)(t - i * h.n);
+  const TplConst c = tpl[i];
+  const double B = (c.phi0 + c.P5 + c.P3) * (0.5 / kPi);
+  const double nu = h.nu[q];
+  const double p = nu * B;
+  double r = (p - floor(p)) + fma(nu, B, -p);
+  r -= floor(r);
+  const df v = df_make(r);
+  K[t] = make_float2(v.hi, v.lo);
+}
+
+cudaError_t launch_harm_phase(const TplConst* tpl, int64_t n, const HarmSet& h, float2* K,
+                              cudaStream_t s) {
+  if (n <= 0 || h.n <= 0) return cudaSuccess;
+  const int64_t work = n * h.n;
+  k_harm_phase<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(tpl, n, h, K);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
                          TplConst* out, TplMix* mix, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -1,0 +1,136 @@
+"""Multi-harmonic templates on the CUDA paths against the FP64 oracle (same seeded
+inputs, element by element).
+
+Tolerances: the mixed path keeps the single-mode bounds of its pixel type. The FP64
+path adds one floor to the single-mode one: the harmonics' relative phases depend on
+the absolute phase nu_h Phi(t'), which the FP64 kernel forms from FP64 constants
+(~eps64 relative each), so it carries ~4 eps64 nu_max Phi_tot rad with
+Phi_tot = 2 pi f_max N_t dT the largest phase on the grid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_19047_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {("fp64", "f16"): (1e-10, 1e-10), ("mixed", "f32"): (1e-4, 1e-4),
+       ("mixed", "f16"): (1.5e-3, 1e-3), ("mixed", "bf16"): (1.2e-2, 8e-3)}
+CASES = list(TOL)
+EPS64 = 2.0 ** -53
+NU = [0.5, 1.0, 1.5]
+C = [0.3 + 0.1j, 1.0, 0.4 - 0.2j]
+
+
+def fp64_tol(D, n_seg, nu_max):
+    f_max = D.n_bins / D.dT
+    phi_seg = 2 * np.pi * f_max * (D.n_tranche // int(n_seg)) * D.dT
+    phi_tot = 2 * np.pi * f_max * D.n_tranche * D.dT
+    return max(1e-10, 4 * EPS64 * phi_seg, 4 * EPS64 * nu_max * phi_tot)
+
+
+def rel_err(got, ref):
+    got, ref = np.asarray(got, float), np.asarray(ref, float)
+    assert np.all(np.isfinite(got))
+    zero = ref == 0
+    assert np.all(got[zero] == 0)
+    r = np.abs(got[~zero] - ref[~zero]) / ref[~zero]
+    return (r.max(), np.percentile(r, 99)) if r.size else (0.0, 0.0)
+
+
+def ctx_for(D, path, pixel, nu, c):
+    from paper_2510_19047_b300.binding import TFS
+    t = TFS(0, path=path, pixel=pixel, pn_order=D.pn_order, response=D.response)
+    t.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    t.set_noise_weights(D.w, D.mask)
+    t.set_harmonics(nu, c)
+    return t
+
+
+def check(D, th, lev, path, pixel, nu, c, diag_slack=None):
+    refs = [oracle.statistic_harm(D.d, D.w, D.mask, th, L, D.dT, nu, c, pn_order=D.pn_order,
+                                  response=D.response) for L in lev]
+    t = ctx_for(D, path, pixel, nu, c)
+    got, neff, diag = t.eval_statistic(th, lev, diag=True)
+    for i, (ref, rneff, rnact, _) in enumerate(refs):
+        assert np.count_nonzero(ref) > 0.8 * th.shape[1]
+        mx, p99 = rel_err(got[i], ref)
+        tol = fp64_tol(D, lev[i], max(nu)) if path == "fp64" else TOL[(path, pixel)][0]
+        assert mx < tol and p99 < max(tol, TOL[(path, pixel)][1]), (lev[i], mx, p99)
+        assert np.array_equal(neff[i], rneff)
+    slack = (0 if path == "fp64" else 1) if diag_slack is None else diag_slack
+    assert np.abs(diag[0] - refs[0][2]).max() <= slack
+    return got
+
+
+@pytest.fixture(scope="module")
+def ae45():
+    return synth.two_year_two_channel(seed=77, n_inj=3, n_tranche=384, L=2048)
+
+
+@pytest.fixture(scope="module")
+def bank(ae45):
+    th = synth.two_year_bank(77, seed=13)  # ragged: not a multiple of 32
+    th[:, :3] = ae45.injections
+    return th
+
+
+@pytest.mark.parametrize("path,pixel", CASES)
+def test_three_harmonics_long_wavelength(ae45, bank, path, pixel):
+    check(ae45, bank, [64, 8], path, pixel, NU, C)
+
+
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f16")])
+def test_three_harmonics_tdi(path, pixel):
+    D = synth.cached(synth.two_year_two_channel, seed=78, n_inj=2, n_tranche=384, L=2048,
+                     response="tdi")
+    th = np.concatenate([D.injections, synth.two_year_bank(46, seed=17)], axis=1)
+    check(D, th, [32, 8], path, pixel, NU, C)
+
+
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f32"), ("mixed", "f16")])
+def test_one_channel_and_band_edges(path, pixel):
+    # one channel, no response; nu = 0.5 puts part of the bank below the band's lower edge
+    D = synth.week_one_channel(seed=0)
+    th = synth.week_bank(200, 0)
+    check(D, th, [8, 2], path, pixel, [0.5, 1.0, 2.0], [0.5, 1.0, 0.25j])
+
+
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f32"), ("mixed", "f16")])
+def test_overlapping_windows_keep_cross_terms(ae45, bank, path, pixel):
+    # nu = 1 and 1.05 share ~10 bins at 20 mHz: the cross terms of N_n are evaluated
+    # bin by bin
+    check(ae45, bank[:, :40], [16], path, pixel, [1.0, 1.05], [1.0, 0.6 + 0.3j])
+    # two copies of the dominant mode whose amplitudes sum to 1 are the single-mode
+    # template (the oracle's single-mode statistic is the reference)
+    t = ctx_for(ae45, path, pixel, [1.0, 1.0], [0.3 + 0.2j, 0.7 - 0.2j])
+    got, _, _ = t.eval_statistic(bank[:, :40], 16)
+    ref = oracle.statistic(ae45.d, ae45.w, ae45.mask, bank[:, :40], 16, ae45.dT, pn_order=1,
+                           response=1)[0]
+    mx, _ = rel_err(got, ref)
+    assert mx < (fp64_tol(ae45, 16, 1.0) if path == "fp64" else TOL[(path, pixel)][0])
+
+
+def test_harmonic_settings_and_errors(ae45, bank):
+    from paper_2510_19047_b300.binding import TFSError
+    t = ctx_for(ae45, "mixed", "f16", [], [])
+    base, _, _ = t.eval_statistic(bank, [64, 8])
+    t.set_harmonics([1.0], [1.0])
+    one, _, _ = t.eval_statistic(bank, [64, 8])
+    assert rel_err(one, base)[0] < 1e-3  # the single-mode template through the harmonic kernel
+    t.set_harmonics()
+    again, _, _ = t.eval_statistic(bank, [64, 8])
+    assert np.array_equal(again, base)  # back to the dominant-mode kernel, bit for bit
+    for nu, c in (([0.0], [1.0]), ([17.0], [1.0]), ([1.0], [np.nan]), ([1.0] * 9, [1.0] * 9)):
+        with pytest.raises(TFSError, match="ARG"):
+            t.set_harmonics(nu, c)
+    t.set_harmonics(NU, C)
+    with pytest.raises(TFSError, match="ARG"):
+        t.grad_statistic(bank[:, :4], 8)
+    t.set_options(path="plain")
+    with pytest.raises(TFSError, match="ARG"):
+        t.eval_statistic(bank[:, :4], 8)
+    t.set_options(path="mixed")
+    s, n, _ = t.eval_statistic(np.zeros((8, 0)), 8)
+    assert s.shape == (0,)
