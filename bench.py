@@ -68,7 +68,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
-    p.add_argument("--study", default=None, choices=["precision", "ladder", "refine", "fap", "pso", "tdi"],
+    p.add_argument("--study", default=None, choices=["precision", "ladder", "refine", "fap", "pso", "tdi", "harmonics"],
                    help="run one of the workload studies instead of the headline step")
     return p.parse_args()
 

@@ -16,6 +16,9 @@ fap       : background of the coherent (N_seg = 1) tile maximum over 100 noise-o
 pso       : one particle swarm per injection tile (512 particles, 100 iterations,
             N_seg = 16) against the injection's own statistic.
 tdi       : throughput with the TDI-1.5 response against the long-wavelength one.
+harmonics : throughput of three-harmonic templates (nu = 1/2, 1, 3/2, synthetic complex
+            amplitudes) on the bench's two-year workload against the single-mode kernel,
+            and their error against the oracle on a sample of the bank.
 """
 import statistics
 import time
@@ -258,4 +261,54 @@ def tdi(args):
         out[f"response{resp}"] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
                                   "kernel_ms": statistics.median(ks)}
         c.close()
+    return out
+
+
+def harmonics(args):
+    """Multi-harmonic templates (Sec. "Outlook") on the bench's two-year workload:
+    1e6 templates, N_seg 256/64/16 in one pass, LW response, FP16 pixels. Harmonic sets:
+    the dominant mode through the single-mode kernel, nu = {1} through the harmonic
+    kernel, and nu = {1/2, 1, 3/2} with amplitudes (0.3 + 0.1i, 1, 0.4 - 0.2i) (synthetic:
+    the paper gives no harmonic model). Error against the oracle on 192 templates."""
+    import torch
+    import oracle
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.binding import TFS
+    D = synth.cached(synth.two_year_two_channel)
+    bank = synth.two_year_bank(1_000_000, seed=2002)
+    th = torch.from_numpy(bank).cuda()
+    lev = [256, 64, 16]
+    sets = {"single_mode_kernel": ([], []), "nu1": ([1.0], [1.0]),
+            "nu_half_1_3half": ([0.5, 1.0, 1.5], [0.3 + 0.1j, 1.0, 0.4 - 0.2j])}
+    out = {"study": "harmonics", "workload": "AE-2yr-2048x6144, 1e6 templates, N_seg 256/64/16"}
+    c = TFS(0, pn_order=1, response=1, profile=1)
+    c.load_tf_data(D.d, D.dt, D.dT)
+    c.set_noise_weights(D.w, D.mask)
+    for name, (nu, cc) in sets.items():
+        c.set_harmonics(nu, cc)
+        c.eval_statistic(th, lev)
+        ks, ss = [], []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.eval_statistic(th, lev)
+            e1.record()
+            e1.synchronize()
+            ss.append(e0.elapsed_time(e1))
+            ks.append(c.last_profile()["statistic"])
+        out[name] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
+                     "kernel_ms": statistics.median(ks)}
+    nu, cc = sets["nu_half_1_3half"]
+    c.set_harmonics(nu, cc)
+    sample = bank[:, :192]
+    got = c.eval_statistic(sample, [16])[0][0]
+    t0 = time.perf_counter()
+    ref = oracle.statistic_harm(D.d, D.w, D.mask, sample, 16, D.dT, nu, cc, pn_order=1,
+                                response=1)[0]
+    mx, p99 = _rel(got, ref)
+    out["nu_half_1_3half"]["rel_err_vs_oracle_nseg16"] = {"max": mx, "p99": p99, "n": 192,
+                                                          "oracle_s": time.perf_counter() - t0}
+    out["cost_ratio_3h_vs_single_mode"] = (out["nu_half_1_3half"]["kernel_ms"]
+                                           / out["single_mode_kernel"]["kernel_ms"])
+    c.close()
     return out

@@ -650,9 +650,18 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.harm = c->harm;
   a.harm_K = nullptr;
 
+  double nu_min = 1.0, nu_max = 1.0;
+  if (harm) {
+    nu_min = nu_max = c->harm.nu[0];
+    for (int h = 1; h < c->harm.n; ++h) {
+      nu_min = std::min(nu_min, c->harm.nu[h]);
+      nu_max = std::max(nu_max, c->harm.nu[h]);
+    }
+  }
   auto setup = [&](cudaStream_t st) -> int {
     prof_record(c, 0, st);
-    CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, g, (TplConst*)c->tpl.p, mix, st));
+    CUDA_TRY(c, launch_setup((const double*)th, n_tpl, c->opt.pn_order, g, (TplConst*)c->tpl.p, mix, st,
+                             nu_min, nu_max));
     c->launches++;
     prof_record(c, 1, st);
     return TFS_OK;

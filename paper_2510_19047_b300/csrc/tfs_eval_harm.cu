@@ -106,10 +106,52 @@ __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, co
   return q;
 }
 
+// The cross terms 2 Re sum_alpha conj(T_a) T_b sum_k w_k conj(W''^a_k) W''^b_k of every
+// pair of harmonics whose windows share bins, in one tranche (bin by bin, general W'').
+template <int NCH, int PIX, bool TDI>
+__device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
+                                          const TrancheF& tr, const float2* Kp, int m,
+                                          float sig_k, float dTf) {
+  using Ld = PixLoad<PIX>;
+  const typename Ld::P* PX = (const typename Ld::P*)a.Umix;
+  float N = 0.0f;
+  for (int ha = 0; ha < a.harm.n; ++ha) {
+    const HarmM A = harm_of<TDI>(a, tk, cptr, tr, Kp[ha], ha, sig_k, dTf);
+    if (!A.act) continue;
+    for (int hb = ha + 1; hb < a.harm.n; ++hb) {
+      const HarmM B = harm_of<TDI>(a, tk, cptr, tr, Kp[hb], hb, sig_k, dTf);
+      if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
+      // conj(T_a) T_b per channel
+      const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
+      const float y1r = A.Tr1 * B.Tr1 + A.Ti1 * B.Ti1, y1i = A.Tr1 * B.Ti1 - A.Ti1 * B.Tr1;
+      const int k0 = max(A.kc, B.kc) - kNFHalf, k1 = min(A.kc, B.kc) + kNFHalf;
+      for (int k = k0; k <= k1; ++k) {
+        const float ja = (float)(k - A.kc), jb = (float)(k - B.kc);
+        float war, wai, wbr, wbi;
+        w_general(A.aa - ja, A.aa + A.eps - ja, A.sig, A.sig * (float)kPi, A.cpsi, A.spsi, true,
+                  war, wai);
+        w_general(B.aa - jb, B.aa + B.eps - jb, B.sig, B.sig * (float)kPi, B.cpsi, B.spsi, true,
+                  wbr, wbi);
+        const float xr = war * wbr + wai * wbi, xi = war * wbi - wai * wbr;  // conj(Wa) Wb
+        float2 ur, ui, w;
+        Ld::cvt(Ld::raw(PX + (int64_t)k * a.pitch + m), ur, ui, w);
+        N += 2.0f * w.x * (y0r * xr - y0i * xi);
+        if (NCH == 2) N += 2.0f * w.y * (y1r * xr - y1i * xi);
+      }
+    }
+  }
+  return N;
+}
+
 }  // namespace
 
+#ifndef TFS_HARM_MINB
+#define TFS_HARM_MINB 3
+#endif
+constexpr int kHarmDepth = 3;  // pixel-load lead of the unrolled window path, in bins
+
 template <int NCH, int PIX, bool TDI>
-__global__ void __launch_bounds__(256, 2) k_eval_harm(EvalArgs a) {
+__global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
   const int lane = threadIdx.x & 31;
@@ -247,23 +289,47 @@ __global__ void __launch_bounds__(256, 2) k_eval_harm(EvalArgs a) {
         const float m2c = -2.0f * q.cpsi;
         BinAcc s;
         s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
-        typename Ld::P cur = Ld::raw(Pp);
-        float jpf = -(float)kNFHalf;
-        for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
-          typename Ld::P nxt;
-          if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
-          float2 cur_r, cur_i, cur_w;
-          Ld::cvt(cur, cur_r, cur_i, cur_w);
-          const int jp = j - kNFHalf;
-          const float x1 = q.aa - jpf, x2 = ae - jpf;
-          if (jp >= JLO && jp <= JHI) {
-            float wr, wi;
-            w_general(x1, x2, q.sig, spi, q.cpsi, q.spsi, true, wr, wi);
-            acc_general(s, cur_r, cur_i, cur_w, wr, wi);
-          } else {
-            acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
+        if (JLO >= -1 && JHI <= 0) {
+          // only the two bins next to f_nm (jp = -1, 0) can need the general form, and
+          // only jp = 0 can hold the sweep: fully unrolled, loads kHarmDepth bins ahead
+          typename Ld::P ring[kHarmDepth];
+#pragma unroll
+          for (int r = 0; r < kHarmDepth; ++r) ring[r] = Ld::raw(Pp + (int64_t)r * pitch);
+#pragma unroll
+          for (int j = 0; j < kNF; ++j) {
+            const typename Ld::P pj = ring[j % kHarmDepth];
+            if (j + kHarmDepth < kNF) ring[j % kHarmDepth] = Ld::raw(Pp + (int64_t)(j + kHarmDepth) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(pj, cur_r, cur_i, cur_w);
+            constexpr float kZero = 0.0f;
+            const float c = kZero + (float)(j - kNFHalf);
+            if (j == kNFHalf - 1 || j == kNFHalf) {
+              float wr, wi;
+              w_general(q.aa - c, ae - c, q.sig, spi, q.cpsi, q.spsi, j == kNFHalf, wr, wi);
+              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+            } else {
+              acc_asym(s, cur_r, cur_i, cur_w, q.aa - c, ae - c, m2c);
+            }
           }
-          if (j + 1 < kNF) cur = nxt;
+        } else {
+          typename Ld::P cur = Ld::raw(Pp);
+          float jpf = -(float)kNFHalf;
+          for (int j = 0; j < kNF; ++j, jpf += 1.0f) {
+            typename Ld::P nxt;
+            if (j + 1 < kNF) nxt = Ld::raw(Pp + (int64_t)(j + 1) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(cur, cur_r, cur_i, cur_w);
+            const int jp = j - kNFHalf;
+            const float x1 = q.aa - jpf, x2 = ae - jpf;
+            if (jp >= JLO && jp <= JHI) {
+              float wr, wi;
+              w_general(x1, x2, q.sig, spi, q.cpsi, q.spsi, true, wr, wi);
+              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+            } else {
+              acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
+            }
+            if (j + 1 < kNF) cur = nxt;
+          }
         }
         // sum conj(u) W'' = i conj(U1) - i e^{i Psi} conj(U2), both channels at once
         const float2 ncp = make_float2(-q.cpsi, -q.cpsi);
@@ -278,34 +344,8 @@ __global__ void __launch_bounds__(256, 2) k_eval_harm(EvalArgs a) {
           Nn += (q.Tr1 * q.Tr1 + q.Ti1 * q.Ti1) * s.nn.y;
         }
       }
-      // cross terms of windows that share bins
-      if (any && tk.x.hi < x_ov) {
-        for (int ha = 0; ha < H; ++ha) {
-          const HarmM A = harm_of<TDI>(a, tk, cptr, tr, Kp[ha], ha, sig_k, dTf);
-          if (!A.act) continue;
-          for (int hb = ha + 1; hb < H; ++hb) {
-            const HarmM B = harm_of<TDI>(a, tk, cptr, tr, Kp[hb], hb, sig_k, dTf);
-            if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
-            // conj(T_a) T_b per channel
-            const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
-            const float y1r = A.Tr1 * B.Tr1 + A.Ti1 * B.Ti1, y1i = A.Tr1 * B.Ti1 - A.Ti1 * B.Tr1;
-            const int k0 = max(A.kc, B.kc) - kNFHalf, k1 = min(A.kc, B.kc) + kNFHalf;
-            for (int k = k0; k <= k1; ++k) {
-              const float ja = (float)(k - A.kc), jb = (float)(k - B.kc);
-              float war, wai, wbr, wbi;
-              w_general(A.aa - ja, A.aa + A.eps - ja, A.sig, A.sig * (float)kPi, A.cpsi, A.spsi,
-                        true, war, wai);
-              w_general(B.aa - jb, B.aa + B.eps - jb, B.sig, B.sig * (float)kPi, B.cpsi, B.spsi,
-                        true, wbr, wbi);
-              const float xr = war * wbr + wai * wbi, xi = war * wbi - wai * wbr;  // conj(Wa) Wb
-              float2 ur, ui, w;
-              Ld::cvt(Ld::raw(PX + (int64_t)k * pitch + m), ur, ui, w);
-              Nn += 2.0f * w.x * (y0r * xr - y0i * xi);
-              if (NCH == 2) Nn += 2.0f * w.y * (y1r * xr - y1i * xi);
-            }
-          }
-        }
-      }
+      // cross terms of windows that share bins (a rare path, out of line)
+      if (any && tk.x.hi < x_ov) Nn += cross_terms<NCH, PIX, TDI>(a, tk, cptr, tr, Kp, m, sig_k, dTf);
       if (any) {
         ++nact;
         if (tk.fdot > ncomp) ++nnc;

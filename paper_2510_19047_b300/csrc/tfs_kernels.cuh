@@ -71,9 +71,11 @@ cudaError_t launch_pack_ref(int64_t n, const double* d_re, const double* d_im, c
 cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const double* d_re,
                               const double* d_im, const double* w, double su, double sw, void* P,
                               int n_sm, cudaStream_t s);
-// mix may be null (only the mixed path reads it).
+// mix may be null (only the mixed path reads it). [nu_min, nu_max]: the harmonics'
+// frequency factors, which widen the tranche range that can be active.
 cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
-                         TplConst* out, TplMix* mix, cudaStream_t s);
+                         TplConst* out, TplMix* mix, cudaStream_t s, double nu_min = 1.0,
+                         double nu_max = 1.0);
 
 cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int* err, cudaStream_t s);
 cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s);

@@ -240,7 +240,8 @@ __device__ TplMix mix_of(const TplConst& c) {
 }
 
 __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_order,
-                        GridDesc g, TplConst* __restrict__ out, TplMix* __restrict__ mix) {
+                        GridDesc g, double nu_min, double nu_max, TplConst* __restrict__ out,
+                        TplMix* __restrict__ mix) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double th[8];
@@ -274,11 +275,12 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
   c.dop_s = src.dop_s;
   c.nz = src.nz;
   // Tranches that can be active: the window k_c +- 10 must lie in [1, N_bins - 1],
-  // i.e. 10 df < f_nm <= (N_bins - 11) df, and t' < t_c. The Doppler factor moves
-  // f by at most 1.1e-4 relative and t' by at most 1 AU/c; a margin covers both.
+  // i.e. 10 df < nu f_nm <= (N_bins - 11) df for some harmonic nu in [nu_min, nu_max]
+  // (nu = 1 for the dominant mode alone), and t' < t_c. The Doppler factor moves f by
+  // at most 1.1e-4 relative and t' by at most 1 AU/c; a margin covers both.
   const double dop_f = 1.5e-4, dop_t = kAuS + 1.0;
-  const double f_lo = 10.0 * g.df / (1.0 + dop_f);
-  const double f_hi = (g.n_bins - 11) * g.df / (1.0 - dop_f);
+  const double f_lo = 10.0 * g.df / (1.0 + dop_f) / nu_max;
+  const double f_hi = (g.n_bins - 11) * g.df / (1.0 - dop_f) / nu_min;
   const double tp_lo = time_at_frequency(c.tc, c.F0, c.C2, f_lo);
   const double tp_hi = fmin(time_at_frequency(c.tc, c.F0, c.C2, f_hi), c.tc);
   const double T_end = g.t0 + g.n_tranche * g.dT;
@@ -392,9 +394,11 @@ cudaError_t launch_harm_phase(const TplConst* tpl, int64_t n, const HarmSet& h, 
 }
 
 cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const GridDesc& g,
-                         TplConst* out, TplMix* mix, cudaStream_t s) {
+                         TplConst* out, TplMix* mix, cudaStream_t s, double nu_min,
+                         double nu_max) {
   if (n <= 0) return cudaSuccess;
-  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, n, pn_order, g, out, mix);
+  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(theta, n, pn_order, g, nu_min, nu_max, out,
+                                                        mix);
   return cudaGetLastError();
 }
 

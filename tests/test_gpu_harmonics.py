@@ -112,6 +112,22 @@ def test_overlapping_windows_keep_cross_terms(ae45, bank, path, pixel):
     assert mx < (fp64_tol(ae45, 16, 1.0) if path == "fp64" else TOL[(path, pixel)][0])
 
 
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f16")])
+def test_low_harmonic_outlives_the_dominant_window(ae45, path, pixel):
+    # chirps that leave the band (f > (N_bins - 11) df) inside the grid: the nu = 1/2
+    # harmonic stays in band until coalescence, so the tranche range that can be active
+    # reaches past the dominant mode's
+    rng = np.random.Generator(np.random.PCG64(41))
+    th = synth.two_year_bank(48, seed=42)
+    th[0] = rng.uniform(45, 60, 48)
+    th[2] = rng.uniform(0.05, 0.08, 48)
+    ref1 = oracle.statistic(ae45.d, ae45.w, ae45.mask, th, 8, ae45.dT, pn_order=1, response=1)
+    ref = oracle.statistic_harm(ae45.d, ae45.w, ae45.mask, th, 8, ae45.dT, [0.5, 1.0],
+                                [0.5, 1.0], pn_order=1, response=1)
+    assert np.sum(ref[2] > ref1[2] + 10) > 10  # the low harmonic adds active tranches
+    check(ae45, th, [8], path, pixel, [0.5, 1.0], [0.5, 1.0])
+
+
 def test_harmonic_settings_and_errors(ae45, bank):
     from paper_2510_19047_b300.binding import TFSError
     t = ctx_for(ae45, "mixed", "f16", [], [])
