@@ -266,7 +266,7 @@ def tdi(args):
 
 def harmonics(args):
     """Multi-harmonic templates (Sec. "Outlook") on the bench's two-year workload:
-    1e6 templates, N_seg 256/64/16 in one pass, LW response, FP16 pixels. Harmonic sets:
+    1e6 templates (--n-templates), N_seg 256/64/16 in one pass, LW response, FP16 pixels. Harmonic sets:
     the dominant mode through the single-mode kernel, nu = {1} through the harmonic
     kernel, and nu = {1/2, 1, 3/2} with amplitudes (0.3 + 0.1i, 1, 0.4 - 0.2i) (synthetic:
     the paper gives no harmonic model). Error against the oracle on 192 templates."""
@@ -275,12 +275,13 @@ def harmonics(args):
     from paper_2510_19047_b300 import synth
     from paper_2510_19047_b300.binding import TFS
     D = synth.cached(synth.two_year_two_channel)
-    bank = synth.two_year_bank(1_000_000, seed=2002)
+    n = int(getattr(args, "n_templates", 1_000_000))
+    bank = synth.two_year_bank(n, seed=2002)
     th = torch.from_numpy(bank).cuda()
     lev = [256, 64, 16]
     sets = {"single_mode_kernel": ([], []), "nu1": ([1.0], [1.0]),
             "nu_half_1_3half": ([0.5, 1.0, 1.5], [0.3 + 0.1j, 1.0, 0.4 - 0.2j])}
-    out = {"study": "harmonics", "workload": "AE-2yr-2048x6144, 1e6 templates, N_seg 256/64/16"}
+    out = {"study": "harmonics", "workload": f"AE-2yr-2048x6144, {n} templates, N_seg 256/64/16"}
     c = TFS(0, pn_order=1, response=1, profile=1)
     c.load_tf_data(D.d, D.dt, D.dT)
     c.set_noise_weights(D.w, D.mask)
@@ -296,7 +297,7 @@ def harmonics(args):
             e1.synchronize()
             ss.append(e0.elapsed_time(e1))
             ks.append(c.last_profile()["statistic"])
-        out[name] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
+        out[name] = {"templates_per_s": n / (statistics.median(ss) / 1000.0),
                      "kernel_ms": statistics.median(ks)}
     nu, cc = sets["nu_half_1_3half"]
     c.set_harmonics(nu, cc)

@@ -63,6 +63,7 @@ namespace {
 constexpr unsigned kFullG = 0xffffffffu;
 constexpr int kGradWarps = 4;
 constexpr int kSrcFields = 21;  // tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6] n_z
+static_assert(kSrcFields + 3 <= 32, "one lane per field and per phase share");
 
 // The paper's auxiliary Fresnel functions and their derivatives at a = |v|.
 __device__ __forceinline__ void fg_deriv(float a, float& f, float& g, float& fp, float& gp) {
@@ -640,10 +641,10 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
   __syncwarp();
 
   // ---- pass B: adjoints of the template constants ----
-  // per 32-tranche block the lanes' FP32 contributions are summed over the warp and
-  // accumulated in FP64 (every lane holds the same totals)
-  double G[kSrcFields];
-  for (int k = 0; k < kSrcFields; ++k) G[k] = 0.0;
+  // per 32-tranche block the lanes' FP32 contributions are summed over the warp; lane
+  // k < 21 accumulates field k across blocks in FP64, lanes 21-23 the phase shares of
+  // t_c, P5, P3 (one FP64 add per lane and block: the FP64 pipe is slow)
+  double Gown = 0.0;
   const float twopidT = (float)(2.0 * kPi * a.g.dT), pidT2 = (float)(kPi * a.g.dT * a.g.dT);
   for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
     const int m = m0 + lane;
@@ -810,35 +811,48 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
         track_adjoint(a, sf, L, a.tabF[m], cf, cfd, cphi, cP, cTr, cTi, gl, gph);
       }
     }
-    // warp sums in double-float, then FP64 once per block (gph[0] is in cycles)
+    // warp sums (the phase shares in double-float; gph[0] is in cycles), each kept by
+    // the lane that owns it
+    float own_f = 0.0f;
+    df own_d = {0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       df v = gph[k];
       for (int o = 16; o > 0; o >>= 1)
         v = df_add(v, df{__shfl_xor_sync(kFullG, v.hi, o), __shfl_xor_sync(kFullG, v.lo, o)});
-      const double vd = (double)v.hi + (double)v.lo;
-      G[k == 0 ? 0 : k + 2] += k == 0 ? 2.0 * kPi * vd : vd;  // t_c, P5, P3
+      if (lane == kSrcFields + k) own_d = v;
     }
 #pragma unroll
     for (int k = 0; k < kSrcFields; ++k) {
       float v = gl[k];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
-      G[k] += (double)v;
+      if (lane == k) own_f = v;
     }
+    const double sc = lane == kSrcFields ? 2.0 * kPi : 1.0;
+    Gown += (double)own_f + sc * ((double)own_d.hi + (double)own_d.lo);
   }
-  // d Upsilon / d theta_p = sum_k G_k d(constant_k)/d theta_p
-  if (lane < 8) {
-    double v = 0.0;
-    for (int k = 0; k < kSrcFields; ++k) v = fma(G[k], dsrc[lane][k], v);
-    a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
+  // d Upsilon / d theta_p = sum_k G_k d(constant_k)/d theta_p, with the phase shares
+  // added to t_c, P5, P3
+  double v = 0.0;
+  for (int k = 0; k < kSrcFields; ++k) {
+    double Gk = __shfl_sync(kFullG, Gown, k);
+    if (k == 0) Gk += __shfl_sync(kFullG, Gown, kSrcFields);
+    if (k == 3) Gk += __shfl_sync(kFullG, Gown, kSrcFields + 1);
+    if (k == 4) Gk += __shfl_sync(kFullG, Gown, kSrcFields + 2);
+    if (lane < 8) v = fma(Gk, dsrc[lane][k], v);
   }
+  if (lane < 8) a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
 }
+
+#ifndef TFS_GRAD_MINB
+#define TFS_GRAD_MINB 4
+#endif
 
 // Persistent launch: every warp takes templates from the queue until it is empty, so
 // the long templates (first in the sorted queue) do not leave a tail of idle SMs.
 // TDI: the TDI-1.5 response (code 2), as its own instantiation.
 template <bool TDI>
-__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : 3) k_grad(GradArgs a) {
+__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_grad(GradArgs a) {
   extern __shared__ float4 s_seg[];
   __shared__ double s_dsrc[kGradWarps][8][kSrcFields];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
