@@ -64,6 +64,10 @@ constexpr unsigned kFullG = 0xffffffffu;
 constexpr int kGradWarps = 4;
 constexpr int kSrcFields = 21;  // tc F0 C2 P5 P3 phi0 dop_c dop_s pp[6] px[6] n_z
 static_assert(kSrcFields + 3 <= 32, "one lane per field and per phase share");
+#ifndef TFS_GRAD_UNROLL
+#define TFS_GRAD_UNROLL 3
+#endif
+constexpr int kGradUnroll = TFS_GRAD_UNROLL;  // asymptotic-bin loop unroll (load batching)
 
 // The paper's auxiliary Fresnel functions and their derivatives at a = |v|.
 __device__ __forceinline__ void fg_deriv(float a, float& f, float& g, float& fp, float& gp) {
@@ -555,9 +559,11 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
           // paired); sum conj(u) W over them = (i/pi)(conj(A1) - e^{i Psi} conj(A2))
           float2 A1r = f2(0.f), A1i = f2(0.f), A2r = f2(0.f), A2i = f2(0.f), Q = f2(0.f);
           const float m2c = -2.0f * L.cps;
-          for (int j = 0; j < kNF; ++j) {
-            if (j == g0) j = g1;
-            if (j >= kNF) break;
+          // the asymptotic bins j in [0, g0) and [g1, kNF) as one counted loop
+          const int n_as = kNF - (g1 - g0);
+#pragma unroll kGradUnroll
+          for (int i = 0; i < n_as; ++i) {
+            const int j = i < g0 ? i : i + (g1 - g0);
             const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
             const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
             const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
@@ -672,9 +678,10 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
                B1i = f2(0.f), B2r = f2(0.f), B2i = f2(0.f), C2r = f2(0.f), C2i = f2(0.f);
         float2 Q11 = f2(0.f), Q22 = f2(0.f), Q12 = f2(0.f), Q111 = f2(0.f), Q112 = f2(0.f),
                Q122 = f2(0.f), Q222 = f2(0.f), V222 = f2(0.f);
-        for (int j = 0; j < kNF; ++j) {
-          if (j == g0) j = g1;
-          if (j >= kNF) break;
+        const int n_as = kNF - (g1 - g0);
+#pragma unroll kGradUnroll
+        for (int i = 0; i < n_as; ++i) {
+          const int j = i < g0 ? i : i + (g1 - g0);
           const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
           const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
           const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
