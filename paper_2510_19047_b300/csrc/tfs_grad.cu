@@ -69,22 +69,30 @@ static_assert(kSrcFields + 3 <= 32, "one lane per field and per phase share");
 #endif
 constexpr int kGradUnroll = TFS_GRAD_UNROLL;  // asymptotic-bin loop unroll (load batching)
 
-// The paper's auxiliary Fresnel functions and their derivatives at a = |v|.
+// The paper's auxiliary Fresnel functions and their derivatives at a = |v| (the
+// hardware reciprocal in place of IEEE division: ~1 ulp).
 __device__ __forceinline__ void fg_deriv(float a, float& f, float& g, float& fp, float& gp) {
   if (a > 6.0f) {
-    f = 1.0f / ((float)kPi * a);
+    const float ra = rcp_approx(a);
+    f = (float)(1.0 / kPi) * ra;
     g = 0.0f;
-    fp = -f / a;
+    fp = -f * ra;
     gp = 0.0f;
   } else {
     const float N = fmaf(0.926f, a, 1.0f);
     const float D = fmaf(a, fmaf(3.104f, a, 1.792f), 2.0f);
-    f = N / D;
-    fp = (0.926f * D - N * fmaf(6.208f, a, 1.792f)) / (D * D);
+    const float rD = rcp_approx(D);
+    f = N * rD;
+    fp = (0.926f * D - N * fmaf(6.208f, a, 1.792f)) * rD * rD;
     const float E = fmaf(a, fmaf(a, fmaf(6.670f, a, 3.492f), 4.142f), 2.0f);
-    g = 1.0f / E;
+    g = rcp_approx(E);
     gp = -fmaf(a, fmaf(20.01f, a, 6.984f), 4.142f) * g * g;
   }
+}
+
+// (float)j for 0 <= j < 2^22 on the FMA pipe (2^23 + j is exact in FP32)
+__device__ __forceinline__ float small_int_f(int j) {
+  return __fsub_rn(__int_as_float(0x4B000000 + j), 8388608.0f);
 }
 
 struct BinW {
@@ -181,7 +189,7 @@ __device__ __forceinline__ void general_range(bool ok, float aa, float eps, floa
                                               int& JHI) {
   int jlo = 100, jhi = -100;
   if (ok) {
-    const float r6 = 6.0f / sig;
+    const float r6 = 6.0f * rcp_approx(sig);
     jlo = (int)ceilf(aa - r6 - 0.01f);
     jhi = (int)floorf(aa + eps + r6 + 0.01f);
   }
@@ -399,12 +407,12 @@ __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, 
   const float y = k.y, y2 = k.y2, y3 = y2 * y, y5 = y3 * y2, y10 = y5 * y5;
   const float dfs_dy = s.F0 * y2 * fmaf(5.0f * s.C2, y2, 3.0f);
   const float dfd_dy = s.F0 * y10 * fmaf(65.0f * s.C2, y2, 33.0f) * s.inv8tc;
-  const float ionec = 1.0f / k.onec;
-  const float dlnA_dy = 2.0f / y + (4.0f / 3.0f) * s.C2 * y * ionec;
+  const float ionec = rcp_approx(k.onec);
+  const float dlnA_dy = 2.0f * rcp_approx(y) + (4.0f / 3.0f) * s.C2 * y * ionec;
   const float g_y = g_fsrc * dfs_dy + g_fdsrc * dfd_dy + cP * dlnA_dy;
   g[2] = g_fsrc * s.F0 * y5 + g_fdsrc * s.F0 * y10 * y3 * 5.0f * s.inv8tc +
          cP * (2.0f / 3.0f) * y2 * ionec;
-  g[1] = s.F0 != 0.0f ? (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) / s.F0 : 0.0f;
+  g[1] = s.F0 != 0.0f ? (g_fsrc * k.fsrc + g_fdsrc * k.fdsrc) * rcp_approx(s.F0) : 0.0f;
   // phase: Phi = phi0 + P5 (1 - u^(5/8)) + P3 (1 - u^(3/8)), u^(5/8) = u y^3
   const df y2d = df_sqr(k.yd), y3d = df_mul(y2d, k.yd);
   const df u58 = df_mul(k.ud, y3d);
@@ -418,7 +426,7 @@ __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, 
   g[3] = 0.0f;
   g[4] = 0.0f;
   g[5] = cphi;
-  const float g_u = -g_y * y / (8.0f * k.u);
+  const float g_u = -g_y * y * rcp_approx(8.0f * k.u);
   g[0] = (g_u * k.tpr - g_fdsrc * k.fdsrc) * s.tc_inv;
   const float g_u_all = g_u + (float)(2.0 * kPi) * gu_ph.hi;  // for the delay amplitudes
   for (int q = 6; q < kSrcFields; ++q) g[q] = 0.0f;
@@ -565,7 +573,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
           for (int i = 0; i < n_as; ++i) {
             const int j = i < g0 ? i : i + (g1 - g0);
             const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
-            const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+            const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
             const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
             const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
             A1r = __ffma2_rn(ur, f2(q1), A1r);
@@ -585,7 +593,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
         }
         for (int j = g0; j < g1; ++j) {  // general bins
           const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
-          const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+          const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
           const BinW b = bin_w<false>(v1, v1 + L.e2, L.cps, L.sps);
           const float ww = b.wr * b.wr + b.wi * b.wi;
           zr[0] += u.x * b.wr + u.z * b.wi;
@@ -683,7 +691,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
         for (int i = 0; i < n_as; ++i) {
           const int j = i < g0 ? i : i + (g1 - g0);
           const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
-          const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+          const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
           const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
           const float q11 = q1 * q1, q22 = q2 * q2, q12 = q1 * q2;
           const float vq22 = v1 * q22;
@@ -751,7 +759,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
       // general bins: the paper's Fresnel form and its derivatives per bin
       for (int j = g0; j < g1; ++j) {
         const float4 u4 = __ldg(Pp + j * pitch2), w4 = __ldg(Pp + j * pitch2 + 1);
-        const float v1 = (L.aa - (float)(j - kNFHalf)) * L.sig;
+        const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
         const BinW b = bin_w<true>(v1, v1 + L.e2, L.cps, L.sps);
         const float X[6][2] = {{b.wr, b.wi}, {b.a1r, b.a1i}, {b.a2r, b.a2i}, {b.a3r, b.a3i},
                                {b.a1r * v1, b.a1i * v1}, {b.a2r * v1, b.a2i * v1}};
@@ -774,7 +782,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
       const float P = L.P;
       const float Er = P * L.cph, Ei = P * L.sph;  // E = P e^{i phi}
       const float rt = L.sig * a.mc.dTf;  // sqrt(2 / fdot) = sigma / df
-      const float ifd2 = 0.5f / L.fdot;
+      const float ifd2 = 0.5f * rcp_approx(L.fdot);
       const float e2 = L.e2;
       float Zmr = 0, Zmi = 0, Nm = 0, cf = 0, cfd = 0, cTr[2] = {0, 0}, cTi[2] = {0, 0};
 #pragma unroll

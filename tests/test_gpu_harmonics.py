@@ -177,3 +177,30 @@ def test_two_year_full_bank_three_harmonics_sampled():
         assert rel_err(st[i, idx], ref)[0] < TOL[("mixed", "f16")][0], L
         assert np.array_equal(ne[i, idx], rneff)
         assert rel_err(g64[i], ref)[0] < fp64_tol(D, L, max(NU)), L
+
+
+def test_harmonics_per_template_segments_checked_and_graph_options(ae45, bank):
+    # per-template N_seg, checked mode and the graph option (the harmonic launch is not
+    # captured: the option is ignored) against the plain call
+    from paper_2510_19047_b300.binding import TFS
+    th = bank[:, :64]
+    ns = np.array([64, 16, 8, 1], np.int32)[np.arange(64) % 4]
+    for path, tol in (("fp64", fp64_tol(ae45, 1, max(NU))), ("mixed", TOL[("mixed", "f16")][0])):
+        t = ctx_for(ae45, path, "f16", NU, C)
+        got, neff, _ = t.eval_statistic(th, ns, per_template=True)
+        for L in (64, 16, 8, 1):
+            sel = ns == L
+            ref, rneff, _, _ = oracle.statistic_harm(ae45.d, ae45.w, ae45.mask, th[:, sel], int(L),
+                                                     ae45.dT, NU, C, pn_order=1, response=1)
+            assert rel_err(got[sel], ref)[0] < tol, (path, L)
+            assert np.array_equal(neff[sel], rneff)
+    base = ctx_for(ae45, "mixed", "f16", NU, C)
+    ref, _, _ = base.eval_statistic(th, [64, 8])
+    for kw in ({"checked": 1}, {"use_graph": 1}, {"sort": 0}):
+        t = TFS(0, path="mixed", pixel="f16", pn_order=1, response=1, **kw)
+        t.load_tf_data(ae45.d, ae45.dt, ae45.dT, ae45.t0)
+        t.set_noise_weights(ae45.w, ae45.mask)
+        t.set_harmonics(NU, C)
+        for _ in range(2):
+            got, _, _ = t.eval_statistic(th, [64, 8])
+            assert np.array_equal(got, ref), kw
