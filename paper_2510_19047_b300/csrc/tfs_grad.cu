@@ -90,6 +90,28 @@ __device__ __forceinline__ void fg_deriv(float a, float& f, float& g, float& fp,
   }
 }
 
+// Warp sums of K <= 32 per-lane values, lane k receiving the sum of v[k] (0 for
+// k >= K): at each of the five steps a lane keeps half of its partial sums, sends the
+// other half to its partner and adds what it receives (31 shuffles instead of 5 K).
+template <int K>
+__device__ __forceinline__ float transpose_sum(const float (&v)[K], int lane) {
+  float w[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float a = i < K ? v[i] : 0.0f, b = i + 16 < K ? v[i + 16] : 0.0f;
+    const bool up = lane & 16;
+    w[i] = (up ? b : a) + __shfl_xor_sync(0xffffffffu, up ? a : b, 16);
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < o; ++i)
+      w[i] = (up ? w[i + o] : w[i]) + __shfl_xor_sync(0xffffffffu, up ? w[i] : w[i + o], o);
+  }
+  return w[0];
+}
+
 // (float)j for 0 <= j < 2^22 on the FMA pipe (2^23 + j is exact in FP32)
 __device__ __forceinline__ float small_int_f(int j) {
   return __fsub_rn(__int_as_float(0x4B000000 + j), 8388608.0f);
@@ -837,12 +859,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
         v = df_add(v, df{__shfl_xor_sync(kFullG, v.hi, o), __shfl_xor_sync(kFullG, v.lo, o)});
       if (lane == kSrcFields + k) own_d = v;
     }
-#pragma unroll
-    for (int k = 0; k < kSrcFields; ++k) {
-      float v = gl[k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullG, v, o);
-      if (lane == k) own_f = v;
-    }
+    own_f = transpose_sum<kSrcFields>(gl, lane);
     const double sc = lane == kSrcFields ? 2.0 * kPi : 1.0;
     Gown += (double)own_f + sc * ((double)own_d.hi + (double)own_d.lo);
   }
