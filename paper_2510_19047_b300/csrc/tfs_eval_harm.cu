@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         const float spi = q.sig * (float)kPi;
         const float ae = q.aa + q.eps;
         const float m2c = -2.0f * q.cpsi;
+        const float2 xae = make_float2(q.aa, ae);
         BinAcc s;
         s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
         if (JLO >= -1 && JHI <= 0) {
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
               w_general(q.aa - c, ae - c, q.sig, spi, q.cpsi, q.spsi, j == kNFHalf, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, q.aa - c, ae - c, m2c);
+              acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
             }
           }
         } else {
@@ -320,13 +321,14 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
             float2 cur_r, cur_i, cur_w;
             Ld::cvt(cur, cur_r, cur_i, cur_w);
             const int jp = j - kNFHalf;
-            const float x1 = q.aa - jpf, x2 = ae - jpf;
+            const float2 xx = __fadd2_rn(xae, make_float2(-jpf, -jpf));
+            const float x1 = xx.x, x2 = xx.y;
             if (jp >= JLO && jp <= JHI) {
               float wr, wi;
               w_general(x1, x2, q.sig, spi, q.cpsi, q.spsi, true, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
+              acc_asym(s, cur_r, cur_i, cur_w, xx, m2c);
             }
             if (j + 1 < kNF) cur = nxt;
           }

@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
         const float spi = sig * (float)kPi;
         const float ae = aa + eps;
         const float m2c = -2.0f * cpsi;
+        const float2 xae = make_float2(aa, ae);
         BinAcc s;
         s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
         // pixel loads run one bin ahead of the arithmetic
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
               w_general(aa - c, ae - c, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, aa - c, ae - c, m2c);
+              acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
             }
           }
         } else {
@@ -285,14 +286,14 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             const int jp = j - kNFHalf;
             // x1 = (f_nm - f_k)/df formed directly from aa: aa + 10 - j would round aa
             // to ulp(10) and ruin 1/x1 for the bins next to f_nm
-            const float x1 = aa - jpf;
-            const float x2 = ae - jpf;
+            const float2 xx = __fadd2_rn(xae, make_float2(-jpf, -jpf));
+            const float x1 = xx.x, x2 = xx.y;
             if (jp >= JLO && jp <= JHI) {
               float wr, wi;
               w_general(x1, x2, sig, spi, cpsi, spsi, true, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, x1, x2, m2c);
+              acc_asym(s, cur_r, cur_i, cur_w, xx, m2c);
             }
             if (j + 1 < kNF) cur = nxt;
           }

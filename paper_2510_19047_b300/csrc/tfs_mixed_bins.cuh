@@ -98,9 +98,10 @@ struct BinAcc {
   float2 u1r, u1i, u2r, u2i, nn;
 };
 
-__device__ __forceinline__ void acc_asym(BinAcc& s, float2 ur, float2 ui, float2 w, float x1,
-                                         float x2, float m2c) {
-  const float q1 = rcp_approx(x1), q2 = rcp_approx(x2);
+__device__ __forceinline__ void acc_asym(BinAcc& s, float2 ur, float2 ui, float2 w, float2 x,
+                                         float m2c) {
+  // x = (x1, x2); m2c = -2 cos(Psi)
+  const float q1 = rcp_approx(x.x), q2 = rcp_approx(x.y);
   const float2 Q1 = make_float2(q1, q1), Q2 = make_float2(q2, q2);
   s.u1r = __ffma2_rn(ur, Q1, s.u1r);
   s.u1i = __ffma2_rn(ui, Q1, s.u1i);
