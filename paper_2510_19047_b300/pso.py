@@ -7,10 +7,11 @@ inertia weight. For each particle:
     v <- w v + c1 r1 (p - x) + c2 r2 (g - x),    x <- x + v,
 
 where p is the particle's best position, g is its swarm's best, and r1, r2 ~ U(0, 1)
-are drawn per coordinate (for wrapped angles p - x and g - x take the shorter way round). Positions are wrapped for the angles (phi_0 and lambda mod
-2 pi, psi mod pi) where the tile spans the whole period, and clipped to the tile
-otherwise and for the other parameters; clipping a
-coordinate stops its velocity. A parameter with lo == hi stays fixed.
+are drawn per coordinate (for wrapped angles p - x and g - x take the shorter way
+round). Positions are wrapped for the angles (phi_0 and lambda mod 2 pi, psi mod pi)
+where the tile spans the whole period, and clipped to the tile otherwise and for the
+other parameters; clipping a coordinate stops its velocity. A parameter with lo == hi
+stays fixed.
 
 Many swarms, one per tile, run together. Every iteration evaluates all particles of all
 swarms with one call of the objective on the device; the bookkeeping is elementwise
