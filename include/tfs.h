@@ -162,8 +162,8 @@ int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t
  * passes the tests above with at least one window in band.
  *   nu: double [n_harm], each in (0, 16]; c_re, c_im: double [n_harm], finite; host
  *   pointers, copied (NULL allowed when n_harm = 0).
- * Applies to tfs_eval_statistic on the FP64 and mixed paths; the plain path and
- * tfs_grad_statistic return TFS_ERR_ARG while n_harm > 0. */
+ * Applies to tfs_eval_statistic on every path; tfs_grad_statistic returns TFS_ERR_ARG
+ * while n_harm > 0. */
 #define TFS_MAX_HARMONICS 8
 int tfs_set_harmonics(tfs_ctx* ctx, int n_harm, const double* nu, const double* c_re,
                       const double* c_im);

@@ -572,8 +572,6 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   c->prof_valid = false;
   if (n_tpl == 0) return TFS_OK;
   const bool harm = c->harm.n > 0;
-  if (harm && path == TFS_PATH_PLAIN)
-    return fail(c, TFS_ERR_ARG, "multi-harmonic templates need the FP64 or mixed path");
   const bool graph = path == TFS_PATH_MIXED && c->opt.use_graph && !harm;
   // inputs: device theta is read in place, host theta is copied; a graph always reads
   // the context's own copy so that its pointers stay fixed between replays

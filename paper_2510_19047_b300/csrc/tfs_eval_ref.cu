@@ -616,8 +616,195 @@ cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// -------------------------------------------------------------------------------------
+// Plain multi-harmonic kernel: the paper's mapping and printed Eq. fresnel-ft, with
+// harmonic h of the tranche at frequency nu_h f_nm, derivative nu_h fdot_nm, phase
+// nu_h Phi(t'_nm) (absolute, as in k_eval_fp64_harm) and amplitude c_h A. Every bin of
+// the union of the harmonics' windows is visited once: its template value is the sum
+// of the harmonics whose window holds it, so the norm keeps the cross terms.
+// -------------------------------------------------------------------------------------
+namespace {
+
+// One harmonic's Eq. fresnel-ft geometry in one tranche (FP64 frequency, FP32 factors).
+struct HarmP {
+  bool on;
+  int kc;
+  double f, fdot, s2d, inv_fdot;
+  double cyc;        // phase / 2 pi, reduced to [0, 1)
+  float Yr[2], Yi[2];  // T_alpha c_h A / sqrt(2 fdot) per channel
+};
+
+template <bool TDI>
+__device__ __forceinline__ HarmP harm_plain(const EvalArgs& a, const TplConst& c,
+                                            const TrancheD& tr, const TrackD& tk, double amp,
+                                            double ph_int, double ph_frac, const float Tlr[2],
+                                            const float Tli[2], int h) {
+  HarmP r;
+  r.on = false;
+  const GridDesc& g = a.g;
+  const double nu = a.harm.nu[h];
+  r.f = nu * tk.f;
+  r.fdot = nu * tk.fdot;
+  r.kc = (int)ceil(r.f * g.dT);
+  if (r.kc - kNFHalf < 1 || r.kc + kNFHalf > g.n_bins - 1) return r;
+  r.on = true;
+  r.s2d = sqrt(2.0 * r.fdot);
+  r.inv_fdot = 1.0 / r.fdot;
+  const double p = nu * ph_int;
+  r.cyc = (p - floor(p)) + fma(nu, ph_int, -p) + nu * ph_frac;
+  r.cyc -= floor(r.cyc);
+  float Tr[2] = {Tlr[0], Tlr[1]}, Ti[2] = {Tli[0], Tli[1]};
+  if (TDI) response_factors<float, true>(c, tr, r.f, a.response, Tr, Ti);
+  const float P = (float)(amp / r.s2d);
+  const float cr = (float)a.harm.cr[h] * P, ci = (float)a.harm.ci[h] * P;
+  for (int ch = 0; ch < 2; ++ch) {
+    r.Yr[ch] = Tr[ch] * cr - Ti[ch] * ci;
+    r.Yi[ch] = Tr[ch] * ci + Ti[ch] * cr;
+  }
+  return r;
+}
+
+// The printed transform of one harmonic at bin k: (C2 - C1 + i (S2 - S1)) times
+// exp(i (phi - pi fdot zeta^2)), without the amplitude.
+__device__ __forceinline__ void plain_bin(const HarmP& q, double df, double dT, int k, float& hr,
+                                          float& hi) {
+  const double zeta = (q.f - (double)k * df) * q.inv_fdot;
+  const double v1 = q.s2d * zeta, v2 = q.s2d * (dT + zeta);
+  float C1, S1, C2, S2;
+  fresnel_cs_plain(v1, C1, S1);
+  fresnel_cs_plain(v2, C2, S2);
+  float sn, cs;
+  sincospif(reduce_mod2(2.0 * q.cyc - q.fdot * zeta * zeta), &sn, &cs);
+  const float Fr = C2 - C1, Fi = S2 - S1;
+  hr = cs * Fr - sn * Fi;
+  hi = cs * Fi + sn * Fr;
+}
+
+}  // namespace
+
+template <bool TDI>
+__global__ void __launch_bounds__(128) k_eval_plain_harm(EvalArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n_tpl) return;
+  const TplConst c = a.tpl[i];
+  const LevelState L = levels_of(a, i);
+  const GridDesc g = a.g;
+  const int nch = g.n_chan;
+  const int H = a.harm.n;
+  float zr[kMaxLevels], zi[kMaxLevels], nn[kMaxLevels];
+  double ups[kMaxLevels];
+  int neff[kMaxLevels], cur[kMaxLevels];
+  for (int l = 0; l < kMaxLevels; ++l) {
+    zr[l] = zi[l] = nn[l] = 0.0f;
+    ups[l] = 0.0;
+    neff[l] = 0;
+    cur[l] = -1;
+  }
+  int nact = 0, nnc = 0;
+  int blk = -1, m_prev = 0;
+  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0, ph_a = 0.0;
+  HarmP hp[TFS_MAX_HARMONICS];
+  for (int m = c.m_lo; m < c.m_hi; ++m) {
+    for (int l = 0; l < L.n; ++l) {
+      const int s = m / L.seg_len[l];
+      if (s != cur[l]) {
+        if (nn[l] > 0.0f) {
+          ups[l] += ((double)zr[l] * zr[l] + (double)zi[l] * zi[l]) / (double)nn[l];
+          ++neff[l];
+        }
+        zr[l] = zi[l] = nn[l] = 0.0f;
+        cur[l] = s;
+      }
+    }
+    if (!a.mask[m]) continue;
+    const TrancheD tr = a.tabD[m];
+    const TrackD tk = track_fp64(c, tr, a.response);
+    if (!(tk.tp < c.tc)) break;
+    if (!(tk.fdot > 0.0)) continue;
+    const int b = m / L.anchor;
+    if (b != blk) {
+      blk = b;
+      m_prev = b * L.anchor;
+      const TrancheD ta = a.tabD[m_prev];
+      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
+      tp_prev = ta.t + d0_prev;
+      acc = comp = 0.0;
+      ph_a = c.phi0 * (0.5 / kPi) + phase_step_cycles(c, 0.0, tp_prev);
+    }
+    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
+    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
+    tp_prev = tk.tp;
+    d0_prev = tk.d0;
+    m_prev = m;
+    const double ph_int = floor(ph_a) + floor(acc);
+    const double ph_frac = (ph_a - floor(ph_a)) + ((acc - floor(acc)) - comp);
+    float Tlr[2] = {1.0f, 1.0f}, Tli[2] = {0.0f, 0.0f};
+    if (!TDI) response_factors<float, false>(c, tr, tk.f, a.response, Tlr, Tli);
+    const double amp = pow(tk.fsrc / c.F0, 2.0 / 3.0);
+    bool any = false;
+    for (int h = 0; h < H; ++h) {
+      hp[h] = harm_plain<TDI>(a, c, tr, tk, amp, ph_int, ph_frac, Tlr, Tli, h);
+      any = any || hp[h].on;
+    }
+    if (!any) continue;
+    ++nact;
+    if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
+    float Zr = 0.f, Zi = 0.f, N = 0.f;
+    for (int h = 0; h < H; ++h) {
+      if (!hp[h].on) continue;
+      for (int j = 0; j < kNF; ++j) {
+        const int k = hp[h].kc - kNFHalf + j;
+        bool seen = false;  // bin k already visited through an earlier harmonic's window
+        for (int e = 0; e < h; ++e) seen = seen || (hp[e].on && abs(k - hp[e].kc) <= kNFHalf);
+        if (seen) continue;
+        float yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
+        for (int e = h; e < H; ++e) {
+          if (!hp[e].on || abs(k - hp[e].kc) > kNFHalf) continue;
+          float hr, hi;
+          plain_bin(hp[e], g.df, g.dT, k, hr, hi);
+          for (int ch = 0; ch < nch; ++ch) {
+            yr[ch] += hp[e].Yr[ch] * hr - hp[e].Yi[ch] * hi;
+            yi[ch] += hp[e].Yr[ch] * hi + hp[e].Yi[ch] * hr;
+          }
+        }
+        for (int ch = 0; ch < nch; ++ch) {
+          const int64_t px = ((int64_t)ch * g.n_tranche + m) * g.n_bins + k;
+          const float2 u = a.u32[px];
+          Zr += u.x * yr[ch] + u.y * yi[ch];  // conj(u) y
+          Zi += u.x * yi[ch] - u.y * yr[ch];
+          N += a.w32[px] * (yr[ch] * yr[ch] + yi[ch] * yi[ch]);
+        }
+      }
+    }
+    for (int l = 0; l < L.n; ++l) {
+      zr[l] += Zr;
+      zi[l] += Zi;
+      nn[l] += N;
+    }
+  }
+  for (int l = 0; l < L.n; ++l) {
+    if (nn[l] > 0.0f) {
+      ups[l] += ((double)zr[l] * zr[l] + (double)zi[l] * zi[l]) / (double)nn[l];
+      ++neff[l];
+    }
+    a.out_stat[(int64_t)l * a.n_tpl + i] = ups[l] * a.out_scale;
+    if (a.out_neff) a.out_neff[(int64_t)l * a.n_tpl + i] = neff[l];
+  }
+  if (a.out_diag) {
+    a.out_diag[i] = nact;
+    a.out_diag[a.n_tpl + i] = nnc;
+  }
+}
+
 cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
+  if (a.harm.n > 0) {
+    if (a.response == 2)
+      k_eval_plain_harm<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+    else
+      k_eval_plain_harm<false><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (a.response == 2)
     k_eval_plain<true><<<(unsigned)((a.n_tpl + 127) / 128), 128, 0, s>>>(a);
   else

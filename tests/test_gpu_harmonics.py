@@ -15,8 +15,9 @@ from paper_2510_19047_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {("fp64", "f16"): (1e-10, 1e-10), ("mixed", "f32"): (1e-4, 1e-4),
-       ("mixed", "f16"): (1.5e-3, 1e-3), ("mixed", "bf16"): (1.2e-2, 8e-3)}
+TOL = {("fp64", "f16"): (1e-10, 1e-10), ("plain", "f16"): (1e-4, 1e-4),
+       ("mixed", "f32"): (1e-4, 1e-4), ("mixed", "f16"): (1.5e-3, 1e-3),
+       ("mixed", "bf16"): (1.2e-2, 8e-3)}
 CASES = list(TOL)
 EPS64 = 2.0 ** -53
 NU = [0.5, 1.0, 1.5]
@@ -81,7 +82,7 @@ def test_three_harmonics_long_wavelength(ae45, bank, path, pixel):
     check(ae45, bank, [64, 8], path, pixel, NU, C)
 
 
-@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f16")])
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("plain", "f16"), ("mixed", "f16")])
 def test_three_harmonics_tdi(path, pixel):
     D = synth.cached(synth.two_year_two_channel, seed=78, n_inj=2, n_tranche=384, L=2048,
                      response="tdi")
@@ -89,7 +90,8 @@ def test_three_harmonics_tdi(path, pixel):
     check(D, th, [32, 8], path, pixel, NU, C)
 
 
-@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f32"), ("mixed", "f16")])
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("plain", "f16"), ("mixed", "f32"),
+                                        ("mixed", "f16")])
 def test_one_channel_and_band_edges(path, pixel):
     # one channel, no response; nu = 0.5 puts part of the bank below the band's lower edge
     D = synth.week_one_channel(seed=0)
@@ -97,7 +99,8 @@ def test_one_channel_and_band_edges(path, pixel):
     check(D, th, [8, 2], path, pixel, [0.5, 1.0, 2.0], [0.5, 1.0, 0.25j])
 
 
-@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f32"), ("mixed", "f16")])
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("plain", "f16"), ("mixed", "f32"),
+                                        ("mixed", "f16")])
 def test_overlapping_windows_keep_cross_terms(ae45, bank, path, pixel):
     # nu = 1 and 1.05 share ~10 bins at 20 mHz: the cross terms of N_n are evaluated
     # bin by bin
@@ -112,7 +115,7 @@ def test_overlapping_windows_keep_cross_terms(ae45, bank, path, pixel):
     assert mx < (fp64_tol(ae45, 16, 1.0) if path == "fp64" else TOL[(path, pixel)][0])
 
 
-@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("mixed", "f16")])
+@pytest.mark.parametrize("path,pixel", [("fp64", "f16"), ("plain", "f16"), ("mixed", "f16")])
 def test_low_harmonic_outlives_the_dominant_window(ae45, path, pixel):
     # chirps that leave the band (f > (N_bins - 11) df) inside the grid: the nu = 1/2
     # harmonic stays in band until coalescence, so the tranche range that can be active
@@ -144,9 +147,6 @@ def test_harmonic_settings_and_errors(ae45, bank):
     t.set_harmonics(NU, C)
     with pytest.raises(TFSError, match="ARG"):
         t.grad_statistic(bank[:, :4], 8)
-    t.set_options(path="plain")
-    with pytest.raises(TFSError, match="ARG"):
-        t.eval_statistic(bank[:, :4], 8)
     t.set_options(path="mixed")
     s, n, _ = t.eval_statistic(np.zeros((8, 0)), 8)
     assert s.shape == (0,)
