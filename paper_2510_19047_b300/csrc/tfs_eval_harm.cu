@@ -150,7 +150,9 @@ __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, c
 #endif
 constexpr int kHarmDepth = 3;  // pixel-load lead of the unrolled window path, in bins
 
-template <int NCH, int PIX, bool TDI>
+// PITCH: the pixel plane's m-pitch as a compile-time constant (immediate row offsets),
+// or 0 for a runtime pitch.
+template <int NCH, int PIX, int PITCH, bool TDI>
 __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   float4* acc = s_acc + (size_t)warp * a.fine_cap;
   const GridDesc g = a.g;
   const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
-  const int pitch = a.pitch;
+  const int pitch = PITCH ? PITCH : a.pitch;
   const int H = a.harm.n;
   const df dTd = df_make(g.dT);
   const float dTf = (float)g.dT;
@@ -414,11 +416,11 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
 
 namespace {
 
-template <int NCH, int PIX>
+template <int NCH, int PIX, int PITCH>
 cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
   constexpr int kWarps = 8;
   const size_t smem = (size_t)kWarps * a.fine_cap * sizeof(float4);
-  auto kern = a.response == 2 ? k_eval_harm<NCH, PIX, true> : k_eval_harm<NCH, PIX, false>;
+  auto kern = a.response == 2 ? k_eval_harm<NCH, PIX, PITCH, true> : k_eval_harm<NCH, PIX, PITCH, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -434,14 +436,25 @@ cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
 
 cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s) {
   if (a.n_work <= 0) return cudaSuccess;
+  const bool fixed = a.pitch == kMixedPitch;
   if (n_chan == 1) {
-    if (pix == TFS_PIX_F32) return launch_harm_one<1, TFS_PIX_F32>(a, n_sm, s);
-    if (pix == TFS_PIX_F16) return launch_harm_one<1, TFS_PIX_F16>(a, n_sm, s);
-    return launch_harm_one<1, TFS_PIX_BF16>(a, n_sm, s);
+    if (pix == TFS_PIX_F32)
+      return fixed ? launch_harm_one<1, TFS_PIX_F32, kMixedPitch>(a, n_sm, s)
+                   : launch_harm_one<1, TFS_PIX_F32, 0>(a, n_sm, s);
+    if (pix == TFS_PIX_F16)
+      return fixed ? launch_harm_one<1, TFS_PIX_F16, kMixedPitch>(a, n_sm, s)
+                   : launch_harm_one<1, TFS_PIX_F16, 0>(a, n_sm, s);
+    return fixed ? launch_harm_one<1, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s)
+                 : launch_harm_one<1, TFS_PIX_BF16, 0>(a, n_sm, s);
   }
-  if (pix == TFS_PIX_F32) return launch_harm_one<2, TFS_PIX_F32>(a, n_sm, s);
-  if (pix == TFS_PIX_F16) return launch_harm_one<2, TFS_PIX_F16>(a, n_sm, s);
-  return launch_harm_one<2, TFS_PIX_BF16>(a, n_sm, s);
+  if (pix == TFS_PIX_F32)
+    return fixed ? launch_harm_one<2, TFS_PIX_F32, kMixedPitch>(a, n_sm, s)
+                 : launch_harm_one<2, TFS_PIX_F32, 0>(a, n_sm, s);
+  if (pix == TFS_PIX_F16)
+    return fixed ? launch_harm_one<2, TFS_PIX_F16, kMixedPitch>(a, n_sm, s)
+                 : launch_harm_one<2, TFS_PIX_F16, 0>(a, n_sm, s);
+  return fixed ? launch_harm_one<2, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s)
+               : launch_harm_one<2, TFS_PIX_BF16, 0>(a, n_sm, s);
 }
 
 }  // namespace tfs
