@@ -40,7 +40,33 @@ struct TrackH {
   float amp;   // (f / F0)^(2/3)
   float f;     // f_nm (FP32, for the TDI transfer)
   float fpA, fxA, fpE, fxE;  // long-wavelength F+, Fx of A and E
+  float ca, sa;              // orbital phase of the tranche (TDI transfer)
 };
+constexpr int kTrkF = 15;  // floats of a TrackH
+
+// A lane's TrackH in shared memory (field k at t[32 k]): held there across the
+// harmonic loop instead of in registers.
+__device__ __forceinline__ void put_track(float* t, const TrackH& k) {
+  const float v[kTrkF] = {k.x.hi, k.x.lo, k.S.hi, k.S.lo, k.fdot, k.amp, k.f, k.fpA, k.fxA, k.fpE,
+                          k.fxE, k.ca, k.sa, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 13; ++i) t[32 * i] = v[i];
+}
+__device__ __forceinline__ TrackH get_track(const float* t) {
+  TrackH k;
+  k.x = df{t[0], t[32]};
+  k.S = df{t[64], t[96]};
+  k.fdot = t[128];
+  k.amp = t[160];
+  k.f = t[192];
+  k.fpA = t[224];
+  k.fxA = t[256];
+  k.fpE = t[288];
+  k.fxE = t[320];
+  k.ca = t[352];
+  k.sa = t[384];
+  return k;
+}
 
 // One harmonic's window geometry and template factors T_alpha (amplitude, phase, c_h
 // and response included) in one tranche.
@@ -53,8 +79,7 @@ struct HarmM {
 
 template <bool TDI>
 __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
-                                         const TrancheF& tr, float2 Kh, int h, float sig_k,
-                                         float dTf) {
+                                         float2 Kh, int h, float sig_k, float dTf) {
   HarmM q;
   q.act = false;
   const df nu = {a.harm.nu_hi[h], a.harm.nu_lo[h]};
@@ -91,7 +116,7 @@ __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, co
       const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
       const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
       Cplx<float> TA, TE;
-      tdi_transfer<float>(nu.hi * tk.f, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
+      tdi_transfer<float>(nu.hi * tk.f, tk.ca, tk.sa, nq.x, nq.y, nq.z, pp, px, TA, TE);
       fpA = TA.re;
       fxA = -TA.im;
       fpE = TE.re;
@@ -110,16 +135,15 @@ __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, co
 // pair of harmonics whose windows share bins, in one tranche (bin by bin, general W'').
 template <int NCH, int PIX, bool TDI>
 __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
-                                          const TrancheF& tr, const float2* Kp, int m,
-                                          float sig_k, float dTf) {
+                                          const float2* Kp, int m, float sig_k, float dTf) {
   using Ld = PixLoad<PIX>;
   const typename Ld::P* PX = (const typename Ld::P*)a.Umix;
   float N = 0.0f;
   for (int ha = 0; ha < a.harm.n; ++ha) {
-    const HarmM A = harm_of<TDI>(a, tk, cptr, tr, Kp[ha], ha, sig_k, dTf);
+    const HarmM A = harm_of<TDI>(a, tk, cptr, Kp[ha], ha, sig_k, dTf);
     if (!A.act) continue;
     for (int hb = ha + 1; hb < a.harm.n; ++hb) {
-      const HarmM B = harm_of<TDI>(a, tk, cptr, tr, Kp[hb], hb, sig_k, dTf);
+      const HarmM B = harm_of<TDI>(a, tk, cptr, Kp[hb], hb, sig_k, dTf);
       if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
       // conj(T_a) T_b per channel
       const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
@@ -158,7 +182,9 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   using Ld = PixLoad<PIX>;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  float4* acc = s_acc + (size_t)warp * a.fine_cap;
+  // per warp: the fine-segment sums, then the lanes' TrackH (kTrkF x 32 floats)
+  float4* acc = s_acc + (size_t)warp * (a.fine_cap + kTrkF * 32 / 4);
+  float* tks = reinterpret_cast<float*>(acc + a.fine_cap) + lane;
   const GridDesc g = a.g;
   const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
   const int pitch = PITCH ? PITCH : a.pitch;
@@ -202,13 +228,14 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
       const int m = m0 + lane;
       const bool inr = m < m_hi;
       bool act = inr && a.mask[m];
+      {
       TrackH tk;
       tk.x = df{0.f, 0.f};
       tk.S = df{0.f, 0.f};
       tk.fdot = 1.f;
       tk.amp = tk.f = 0.f;
       tk.fpA = tk.fxA = tk.fpE = tk.fxE = 0.f;
-      TrancheF tr;
+      tk.ca = tk.sa = 0.f;
       if (act) {
         const float4* cq = reinterpret_cast<const float4*>(cptr);
         const float4 c0 = ldg_nc4(cq), c1 = ldg_nc4(cq + 1), c2 = ldg_nc4(cq + 2),
@@ -217,7 +244,9 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
         const df dopc = {c2.z, c2.w}, dops = {c3.x, c3.y};
         const float C2 = c3.z, fd_k = c3.w;
-        tr = a.tabF[m];
+        const TrancheF tr = a.tabF[m];
+        tk.ca = tr.ca_hi;
+        tk.sa = tr.sa_hi;
         const df tt = {tr.t_hi, tr.t_lo};
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (a.response) {
@@ -269,12 +298,14 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
           }
         }
       }
+      put_track(tks, tk);
+      }
       float Zr = 0.f, Zi = 0.f, Nn = 0.f;
       bool any = false;
       for (int h = 0; h < H; ++h) {
         HarmM q;
         q.act = false;
-        if (act) q = harm_of<TDI>(a, tk, cptr, tr, Kp[h], h, sig_k, dTf);
+        if (act) q = harm_of<TDI>(a, get_track(tks), cptr, Kp[h], h, sig_k, dTf);
         // general-bin range of the harmonic, joined over the warp (as in the mixed kernel)
         int jlo = 100, jhi = -100;
         if (q.act) {
@@ -349,10 +380,10 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         }
       }
       // cross terms of windows that share bins (a rare path, out of line)
-      if (any && tk.x.hi < x_ov) Nn += cross_terms<NCH, PIX, TDI>(a, tk, cptr, tr, Kp, m, sig_k, dTf);
+      if (any && tks[0] < x_ov) Nn += cross_terms<NCH, PIX, TDI>(a, get_track(tks), cptr, Kp, m, sig_k, dTf);
       if (any) {
         ++nact;
-        if (tk.fdot > ncomp) ++nnc;
+        if (tks[128] > ncomp) ++nnc;
       }
       // segmented (by finest segment) suffix sums across the warp; the first lane of
       // each run adds its segment's sum to shared memory
@@ -419,7 +450,7 @@ namespace {
 template <int NCH, int PIX, int PITCH>
 cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
   constexpr int kWarps = 8;
-  const size_t smem = (size_t)kWarps * a.fine_cap * sizeof(float4);
+  const size_t smem = (size_t)kWarps * (a.fine_cap * sizeof(float4) + kTrkF * 32 * sizeof(float));
   auto kern = a.response == 2 ? k_eval_harm<NCH, PIX, PITCH, true> : k_eval_harm<NCH, PIX, PITCH, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
