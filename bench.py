@@ -141,6 +141,18 @@ def oracle_sample_rate(D, theta, n_seg, threads=0):
     return theta.shape[1] / dt, dt
 
 
+def clocks_rejected(clocks):
+    """True for a timed region that saw hardware or thermal slowdown, or SM clocks well
+    below their maximum with no reason reported (a leftover clock lock)."""
+    if not clocks or clocks.get("samples", 0) == 0:
+        return False
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clocks.get("reasons", [])):
+        return True
+    mhz, top = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    return bool(mhz and top and mhz < 0.9 * top and not clocks.get("reasons"))
+
+
 def kernel_source_sha1():
     """SHA-1 over the sources the statistic kernel is compiled from."""
     h = hashlib.sha1()
@@ -241,26 +253,39 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    step_ms, kern_ms, launches = [], [], 0
-    stream = torch.cuda.current_stream()
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.eval_statistic(theta, N_SEG, out=stat)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(ctx.last_profile()["statistic"])
-        launches += ctx.last_launch_count()
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
+    def timed_region():
+        sampler = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        step_ms, kern_ms, launches = [], [], 0
+        stream = torch.cuda.current_stream()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.eval_statistic(theta, N_SEG, out=stat)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(ctx.last_profile()["statistic"])
+            launches += ctx.last_launch_count()
+        torch.cuda.synchronize()
+        barrier()
+        return step_ms, kern_ms, launches, sampler.stop()
+
+    step_ms, kern_ms, launches, clocks = timed_region()
+    rejected = None
+    again = clocks_rejected(clocks)
+    if world > 1:  # every rank re-measures if any rank's clocks were rejected
+        flag = torch.tensor([int(again)], device="cuda")
+        torch.distributed.all_reduce(flag, op=torch.distributed.ReduceOp.MAX)
+        again = bool(flag.item())
+    if again:
+        # a throttled or clock-locked run is measured once more
+        rejected = clocks
+        step_ms, kern_ms, launches, clocks = timed_region()
     ms = max_over_ranks(statistics.mean(step_ms))
     value = n_total / (ms / 1000.0)
 
@@ -290,6 +315,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rejected is not None:
+        result["clocks_rejected_first_run"] = rejected
 
     if rank == 0 and not args.no_plain and args.path == "mixed":
         ctx.set_options(path="plain", profile=1)
