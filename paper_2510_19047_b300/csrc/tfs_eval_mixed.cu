@@ -73,6 +73,14 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   const float dTf = (float)g.dT;
   const float sig_k = (float)(sqrt(2.0) * g.df);       // sigma = df sqrt(2/fdot)
   const float ncomp = (float)(10.0 * g.df / g.dT);      // fdot > 10 df / dT: non-compact
+  // FP32 pixels: the bin next to f_nm below it (x1 = f_nm/df - (k_c - 1)) and Psi are
+  // formed from rb = f_nm/df - rint(f_nm/df), which keeps full relative precision when
+  // f_nm is just above a bin. From aa = f_nm/df - k_c ~ -1 they keep ~6e-8 bins absolute
+  // only, against a sweep x2 - x1 = eps = 2/sigma^2 of ~5e-5 bins for slow chirps: a
+  // ~1e-3 relative error of W'' on that bin, invisible in one tranche's |Z|^2/N but not
+  // in a long segment's. The FP16/BF16 pixels' own rounding is larger, and those
+  // instantiations skip it (it costs registers in the hot loop).
+  constexpr bool kNear = PIX == TFS_PIX_F32;
 
   for (;;) {
     int t = 0;
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
       bool act = inr && a.mask[m];
       float Zr = 0.f, Zi = 0.f, Nn = 0.f;
       int kc = 0;
-      float aa = 0.f, eps = 0.f, sig = 1.f, spsi = 0.f, cpsi = 1.f;
+      float aa = 0.f, a1 = 0.f, eps = 0.f, sig = 1.f, spsi = 0.f, cpsi = 1.f;
       // T_alpha A e^{i phi}: response times amplitude and phase factor, per channel
       float Tr0 = 0.f, Ti0 = 0.f, Tr1 = 0.f, Ti1 = 0.f;
       if (act) {
@@ -161,9 +169,17 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
           // FMA-pipe ceiling below (n_bins < 2^22)
           const bool inband = x.hi > (float)kNFHalf && x.hi < (float)(g.n_bins - kNFHalf);
           float kcf = rint_small(inband ? x.hi : 0.0f);  // ceil(x) = rint(x) (+1 if below x)
-          if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
-          kc = int_small(kcf);
-          aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);  // f_nm/df - k_c, in (-1, 0]
+          // rb = x - rint(x) in [-1/2, 1/2]; rb > 0 exactly when ceil(x) = rint(x) + 1
+          const float rb = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
+          if (kNear) {
+            kc = int_small(rb > 0.f ? kcf + 1.0f : kcf);
+            aa = rb > 0.f ? rb - 1.0f : rb;  // f_nm/df - k_c, in (-1, 0]
+            a1 = rb > 0.f ? rb : rb + 1.0f;  // f_nm/df - (k_c - 1)
+          } else {
+            if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
+            kc = int_small(kcf);
+            aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);  // f_nm/df - k_c, in (-1, 0]
+          }
           if (!inband || !(fdot > 0.f) || kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) {
             act = false;
           } else {
@@ -188,7 +204,8 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             Ti0 = Ti1 = amp_s;
             sig = sig_k * rsqrt_approx(fdot);
             eps = fdot * dTf * dTf;  // fdot dT / df: sweep width in bins
-            const float psi = fmaf(2.0f, aa, eps);  // Psi / pi, reduced to [-1, 1]
+            // Psi / pi = 2 aa + eps = 2 rb + eps (mod 2), reduced to [-1, 1]
+            const float psi = fmaf(2.0f, kNear ? rb : aa, eps);
             __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &spsi, &cpsi);
             if (a.response) {
               float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
@@ -269,7 +286,9 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             const float c = kZero + (float)(j - kNFHalf);
             if (j == kNFHalf - 1 || j == kNFHalf) {
               float wr, wi;
-              w_general(aa - c, ae - c, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
+              const float x1 = kNear && j == kNFHalf - 1 ? a1 : aa - c;
+              const float x2 = kNear && j == kNFHalf - 1 ? a1 + eps : ae - c;
+              w_general(x1, x2, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
               acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
@@ -290,7 +309,8 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
             const float x1 = xx.x, x2 = xx.y;
             if (jp >= JLO && jp <= JHI) {
               float wr, wi;
-              w_general(x1, x2, sig, spi, cpsi, spsi, true, wr, wi);
+              const bool near = kNear && jp == -1;
+              w_general(near ? a1 : x1, near ? a1 + eps : x2, sig, spi, cpsi, spsi, true, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
               acc_asym(s, cur_r, cur_i, cur_w, xx, m2c);

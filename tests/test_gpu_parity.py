@@ -84,6 +84,73 @@ def test_week_one_channel(week, path, pixel):
     assert np.array_equal(diag[0], rnact) and np.array_equal(diag[1], rnnc)
 
 
+def test_week_long_coherent_segments(week):
+    """N_seg down to 1 (week-long coherent segments) on the slow chirps of the week grid
+    (sweep ~5e-5 bins per tranche), where the dominant bin's W'' is a difference across
+    2/sigma^2 bins that a per-tranche |Z|^2/N does not see but a long coherent sum does.
+    Mixed FP32 pixels (single-mode and harmonic kernels) keep the FP32 bound at every
+    level. The plain path evaluates the printed C(v2) - C(v1), S(v2) - S(v1) in FP32:
+    with C, S ~ 1/2 and differences ~1e-3 on the non-central bins it keeps ~6e-5 of
+    each, which adds up coherently over the segment; its bound at N_seg = 1 is 1e-3."""
+    th = synth.week_bank(1024, 0)
+    lev = [512, 64, 8, 1]
+    refs = [oracle.statistic(week.d, week.w, week.mask, th, L, week.dT)[0] for L in lev]
+    for path, harm, tol1 in (("mixed", False, 1e-4), ("mixed", True, 1e-4), ("plain", False, 1e-3)):
+        c = ctx_for(week, path, "f32")
+        if harm:
+            c.set_harmonics([1.0], [1.0])
+        got, _, _ = c.eval_statistic(th, lev)
+        for i, L in enumerate(lev):
+            mx, _ = rel_err(got[i], refs[i])
+            assert mx < (tol1 if L == 1 else 1e-4), (path, harm, L, mx)
+
+
+def _round_pixels(D, pixel):
+    """(d', w') whose u' = d' w' and w' are the pixels the mixed path stores: u = d w and
+    w scaled by the library's powers of two (largest |component| to 2^14 < 2^ceil(log2)),
+    rounded to FP32 and then to FP16 or BF16 (round to nearest even), scaled back."""
+    act = D.w > 0
+    u = np.where(act, D.d * D.w, 0)
+    umax = max(np.abs(u.real).max(), np.abs(u.imag).max())
+    su = 2.0 ** (14 - int(np.ceil(np.log2(umax))))
+    sw = 2.0 ** (14 - int(np.ceil(np.log2(D.w.max()))))
+
+    def rnd(x):
+        x = np.asarray(x, np.float64).astype(np.float32)
+        if pixel == "f16":
+            return x.astype(np.float16).astype(np.float64)
+        b = x.view(np.uint32).astype(np.uint64)
+        b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+    wq = np.where(act, rnd(D.w * sw) / sw, 0.0)
+    uq = (rnd(u.real * su) + 1j * rnd(u.imag * su)) / su
+    dq = np.where(wq > 0, uq / np.where(wq > 0, wq, 1.0), 0)
+    return dq, wq
+
+
+@pytest.mark.parametrize("pixel", ["f16", "bf16"])
+def test_reduced_precision_pixels_are_the_only_rounding(week, pixel):
+    """The FP16/BF16 paths against the oracle run on the same pixels rounded to the
+    storage type: apart from storing u and w, they compute at FP32 accuracy. At N_seg = 1
+    Upsilon is chi^2 with 2 degrees of freedom and can be ~1e-3 of its mean, so the pixel
+    rounding alone moves it by up to ~7e-3 (FP16) or ~7e-2 (BF16) against the unrounded
+    oracle. These instantiations form the offset of the bin below f_nm from aa = f_nm/df
+    - k_c (the FP32-pixel one from x - rint(x), at the cost of a register in the hot loop),
+    which leaves W'' of that bin ~1e-3 off when f_nm sits just above it and the chirp is
+    slow; over a week-long coherent segment that is ~7e-4, still ten times below the
+    pixel rounding, so the bound there is 1e-3."""
+    th = synth.week_bank(1024, 0)
+    lev = [512, 64, 8, 1]
+    dq, wq = _round_pixels(week, pixel)
+    c = ctx_for(week, "mixed", pixel)
+    got, _, _ = c.eval_statistic(th, lev)
+    for i, L in enumerate(lev):
+        ref = oracle.statistic(dq, wq, week.mask, th, L, week.dT)[0]
+        mx, _ = rel_err(got[i], ref)
+        assert mx < (1e-3 if L == 1 else 1e-4), (pixel, L, mx)
+
+
 @pytest.mark.parametrize("path,pixel", CASES)
 def test_two_channel_response_gaps_levels(ae45, ae45_bank, path, pixel):
     lev = [128, 32, 8]
