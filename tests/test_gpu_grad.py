@@ -29,14 +29,15 @@ def ae45_tdi():
                         response="tdi")
 
 
+@pytest.mark.parametrize("n_seg", [16, 1])
 @pytest.mark.parametrize("data", ["ae45", "ae45_tdi"])
-def test_gradient_matches_oracle(data, request):
+def test_gradient_matches_oracle(data, n_seg, request):
     D = request.getfixturevalue(data)
     th = synth.candidates_near(D.injections, 24, seed=3)
-    ref_u, ref_g = oracle.gradient(D.d, D.w, D.mask, th, 16, D.dT, pn_order=1,
+    ref_u, ref_g = oracle.gradient(D.d, D.w, D.mask, th, n_seg, D.dT, pn_order=1,
                                    response=D.response)
     c = ctx_for(D)
-    u, g = c.grad_statistic(th, 16)
+    u, g = c.grad_statistic(th, n_seg)
     np.testing.assert_allclose(u, ref_u, rtol=1e-4)
     # per component, relative to the component or to the gradient's own scale
     # (|dU/dtheta_p| * |theta range|), whichever is larger
