@@ -143,7 +143,11 @@ int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const i
  *   dUpsilon = sum_n [8 Re(conj(Z_n) dZ_n) / N_n - 4 |Z_n|^2 dN_n / N_n^2].
  * The window position and the Fresnel branch are held fixed (the almost-everywhere
  * derivative). FP32 arithmetic with a double-float phase track; with response 2 the
- * TDI-1.5 transfer's dependence on f and on the source direction is included. */
+ * TDI-1.5 transfer's dependence on f and on the source direction is included.
+ * A batch smaller than about three waves of the kernel (a few thousand templates on a
+ * B300) splits each template's segments into up to four work items whose partial sums
+ * are added in a fixed order: results are deterministic for a given batch size, and a
+ * template's values may differ in the last bits between a small and a large batch. */
 int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream);
 

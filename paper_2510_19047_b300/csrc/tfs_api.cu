@@ -46,6 +46,7 @@ struct tfs_ctx {
   // packed pixels
   DevBuf u64, w64, u32, w32, Umix;
   DevBuf Ugrad;            // FP32 mixed-layout plane for the gradient (when Umix is not FP32)
+  DevBuf gpart;            // the gradient's per-work-item partial sums (small batches)
   bool ugrad_ok = false;
   int pitch = 0;
   int pix_built = -1;
@@ -350,7 +351,7 @@ int tfs_destroy(tfs_ctx* c) {
   DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
-                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad,
+                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart,
                    &c->harmK};
   for (DevBuf* b : all) buf_free(c, *b);
   for (int i = 0; i < 5; ++i)
@@ -936,12 +937,15 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   }
   prof_record(c, 2, s);
   const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);
+  int parts = 1;
+  CUDA_TRY(c, grad_plan(c->opt.response, n_seg, c->n_sm, n_tpl, &parts));
+  if (parts > 1 && (r = buf_ensure(c, c->gpart, (size_t)parts * 9 * n_tpl * 8))) return r;
   CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
                           (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
                           (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og,
-                          (unsigned*)c->counter.p, perm, c->n_sm, s));
-  c->launches += 1;
+                          (unsigned*)c->counter.p, perm, parts, (double*)c->gpart.p, c->n_sm, s));
+  c->launches += parts > 1 ? 2 : 1;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));

@@ -278,6 +278,8 @@ struct GradArgs {
   double* out_grad;     // [8][n]
   unsigned* counter;    // work ticket of the persistent launch (zero at launch)
   const int32_t* perm;  // queue order (longest templates first), or null for 0..n-1
+  int parts;            // work items per template: contiguous groups of its segments
+  double* part_out;     // parts > 1: [parts][9][n] partial (Upsilon, gradient) sums
 };
 
 // The track at the start of tranche m: the mixed kernel's double-float evaluation
@@ -525,8 +527,12 @@ __device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, con
 
 // Statistic and gradient of template i by one warp. seg: this warp's n_seg float4
 // slots in shared memory; dsrc: its 8 x kSrcFields derivative table.
+// Work item (i, h): template i's segments split into a.parts contiguous groups of
+// (nearly) equal count; item h covers the tranches of group h inside [m_lo, m_hi).
+// Upsilon and the gradient are sums over segments, so the items' partial sums add up
+// to the template's (in a fixed order, by k_grad_reduce).
 template <bool TDI>
-__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane, float4* seg,
+__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, int lane, float4* seg,
                                          double (*dsrc)[kSrcFields]) {
   const int nch = a.g.n_chan;
   const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
@@ -534,6 +540,16 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
   for (int p = 0; p < 8; ++p) th[p] = a.theta[(int64_t)p * a.n_tpl + i];
   const TplConst tc = a.tpl[i];
   const TplMix* cp = a.tplm + i;
+  int mA = tc.m_lo, mB = tc.m_hi;
+  if (a.parts > 1 && mB > mA) {
+    const int s_lo = mA / a.seg_len, n_s = (mB - 1) / a.seg_len - s_lo + 1;
+    mA = max(mA, (s_lo + (h * n_s) / a.parts) * a.seg_len);
+    mB = min(mB, (s_lo + ((h + 1) * n_s) / a.parts) * a.seg_len);
+  }
+  if (mB <= mA) {  // empty group: zero partial sums
+    if (a.parts > 1 && lane < 9) a.part_out[((int64_t)h * 9 + lane) * a.n_tpl + i] = 0.0;
+    return;
+  }
   SrcF sf;
   sf.tc = (float)tc.tc;
   sf.tc_inv = (float)(1.0 / tc.tc);
@@ -570,9 +586,9 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
   __syncwarp();
 
   // ---- pass A: Z_n, N_n ----
-  for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
+  for (int m0 = mA; m0 < mB; m0 += 32) {
     const int m = m0 + lane;
-    const bool inr = m < tc.m_hi;
+    const bool inr = m < mB;
     float Zr = 0.f, Zi = 0.f, Nn = 0.f;
     Trk L;
     L.ok = false;
@@ -673,7 +689,12 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
     seg[q] = o;
   }
   for (int o = 16; o > 0; o >>= 1) ups += __shfl_xor_sync(kFullG, ups, o);
-  if (lane == 0) a.out_stat[i] = ups;
+  if (lane == 0) {
+    if (a.parts > 1)
+      a.part_out[(int64_t)h * 9 * a.n_tpl + i] = ups;
+    else
+      a.out_stat[i] = ups;
+  }
   __syncwarp();
 
   // ---- pass B: adjoints of the template constants ----
@@ -682,14 +703,14 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
   // t_c, P5, P3 (one FP64 add per lane and block: the FP64 pipe is slow)
   double Gown = 0.0;
   const float twopidT = (float)(2.0 * kPi * a.g.dT), pidT2 = (float)(kPi * a.g.dT * a.g.dT);
-  for (int m0 = tc.m_lo; m0 < tc.m_hi; m0 += 32) {
+  for (int m0 = mA; m0 < mB; m0 += 32) {
     const int m = m0 + lane;
     float gl[kSrcFields];
     for (int k = 0; k < kSrcFields; ++k) gl[k] = 0.0f;
     df gph[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     Trk L;
     L.ok = false;
-    if (m < tc.m_hi) L = track_df<TDI>(a, cp, m);
+    if (m < mB) L = track_df<TDI>(a, cp, m);
     int JLO, JHI;
     general_range(L.ok, L.aa, L.eps, L.sig, JLO, JHI);
     if (L.ok) {
@@ -873,7 +894,27 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int lane,
     if (k == 4) Gk += __shfl_sync(kFullG, Gown, kSrcFields + 2);
     if (lane < 8) v = fma(Gk, dsrc[lane][k], v);
   }
-  if (lane < 8) a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
+  if (lane < 8) {
+    if (a.parts > 1)
+      a.part_out[((int64_t)h * 9 + 1 + lane) * a.n_tpl + i] = v;
+    else
+      a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
+  }
+}
+
+// Sum of the work items' partial sums, h = 0 .. parts-1 in order (deterministic).
+__global__ void k_grad_reduce(const double* __restrict__ part, int parts, int64_t n,
+                              double* __restrict__ out_stat, double* __restrict__ out_grad) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 9 * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, i = t - r * n;
+    double v = 0.0;
+    for (int h = 0; h < parts; ++h) v += part[((int64_t)h * 9 + r) * n + i];
+    if (r == 0)
+      out_stat[i] = v;
+    else
+      out_grad[(r - 1) * n + i] = v;
+  }
 }
 
 #ifndef TFS_GRAD_MINB
@@ -893,19 +934,41 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
     unsigned t = 0;
     if (lane == 0) t = atomicAdd(a.counter, 1u);
     t = __shfl_sync(kFullG, t, 0);
-    if ((int64_t)t >= a.n_tpl) break;  // whole warp leaves together
-    const int64_t i = a.perm ? (int64_t)a.perm[t] : (int64_t)t;
-    grad_one<TDI>(a, i, lane, seg, s_dsrc[warp]);
+    if ((int64_t)t >= a.n_tpl * a.parts) break;  // whole warp leaves together
+    const int64_t q = (int64_t)(t / (unsigned)a.parts);
+    const int h = (int)(t - (unsigned)q * (unsigned)a.parts);
+    const int64_t i = a.perm ? (int64_t)a.perm[q] : q;
+    grad_one<TDI>(a, i, h, lane, seg, s_dsrc[warp]);
     __syncwarp();  // seg and dsrc are rewritten by the next template
   }
+}
+
+// Resident warps of the gradient kernel and the number of work items per template:
+// a small batch (fewer than ~3 waves of templates) splits each template's segments into
+// up to 4 groups so that the persistent queue still ends in a short tail.
+cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts) {
+  const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
+  auto kern = response == 2 ? k_grad<true> : k_grad<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t resident = (int64_t)n_sm * std::max(per_sm, 1) * kGradWarps;
+  int p = 1;
+  while (p < kGradMaxParts && p < n_seg && n * p < 3 * resident) ++p;
+  *parts = p;
+  return cudaSuccess;
 }
 
 cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int pn_order,
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        unsigned* counter, const int32_t* perm, int n_sm, cudaStream_t s) {
+                        unsigned* counter, const int32_t* perm, int parts, double* part_buf,
+                        int n_sm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf)) return cudaErrorInvalidValue;
   GradArgs a;
   a.g = g;
   a.mc = mc;
@@ -926,6 +989,8 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.out_grad = out_grad;
   a.counter = counter;
   a.perm = perm;
+  a.parts = parts;
+  a.part_out = part_buf;
   const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
   auto kern = response == 2 ? k_grad<true> : k_grad<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -933,11 +998,15 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
   if (e != cudaSuccess) return e;
-  const int64_t need = (n + kGradWarps - 1) / kGradWarps;
+  const int64_t need = (n * parts + kGradWarps - 1) / kGradWarps;
   const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)ctas, kGradWarps * 32, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || parts == 1) return e;
+  const int64_t blocks = std::min<int64_t>((9 * n + 255) / 256, (int64_t)n_sm * 8);
+  k_grad_reduce<<<(unsigned)blocks, 256, 0, s>>>(part_buf, parts, n, out_stat, out_grad);
   return cudaGetLastError();
 }
 

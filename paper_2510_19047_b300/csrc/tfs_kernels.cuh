@@ -98,10 +98,15 @@ struct AscentParams {
 cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const AscentParams& p,
                           cudaStream_t s);
 // Adjoint gradient at one N_seg: out_stat [n], out_grad [8][n] (device pointers).
+// Work items per template of the gradient kernel (1 .. kGradMaxParts) for a batch of n:
+// parts > 1 needs a [parts][9][n] FP64 buffer for the partial sums.
+constexpr int kGradMaxParts = 4;
+cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts);
 cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int pn_order,
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        unsigned* counter, const int32_t* perm, int n_sm, cudaStream_t s);
+                        unsigned* counter, const int32_t* perm, int parts, double* part_buf,
+                        int n_sm, cudaStream_t s);
 
 }  // namespace tfs
