@@ -136,10 +136,11 @@ def test_reduced_precision_pixels_are_the_only_rounding(week, pixel):
     Upsilon is chi^2 with 2 degrees of freedom and can be ~1e-3 of its mean, so the pixel
     rounding alone moves it by up to ~7e-3 (FP16) or ~7e-2 (BF16) against the unrounded
     oracle. These instantiations form the offset of the bin below f_nm from aa = f_nm/df
-    - k_c (the FP32-pixel one from x - rint(x), at the cost of a register in the hot loop),
+    - k_c (the FP32-pixel one from x - rint(x), which costs them 4 % of kernel time),
     which leaves W'' of that bin ~1e-3 off when f_nm sits just above it and the chirp is
-    slow; over a week-long coherent segment that is ~7e-4, still ten times below the
-    pixel rounding, so the bound there is 1e-3."""
+    slow. The error adds up over coherent tranches: measured 9.0e-5 at N_seg = 8 and
+    6.5e-4 at N_seg = 1 (5.8e-6 and 2.5e-5 with the x - rint(x) offsets), still ten times
+    below the pixel rounding; the bounds are 1e-4 for N_seg >= 64, 2e-4 at 8, 1e-3 at 1."""
     th = synth.week_bank(1024, 0)
     lev = [512, 64, 8, 1]
     dq, wq = _round_pixels(week, pixel)
@@ -148,7 +149,7 @@ def test_reduced_precision_pixels_are_the_only_rounding(week, pixel):
     for i, L in enumerate(lev):
         ref = oracle.statistic(dq, wq, week.mask, th, L, week.dT)[0]
         mx, _ = rel_err(got[i], ref)
-        assert mx < (1e-3 if L == 1 else 1e-4), (pixel, L, mx)
+        assert mx < {1: 1e-3, 8: 2e-4}.get(L, 1e-4), (pixel, L, mx)
 
 
 @pytest.mark.parametrize("path,pixel", CASES)
