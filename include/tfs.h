@@ -79,7 +79,8 @@ typedef enum tfs_pixel {
 
 typedef struct tfs_options {
   int path;          /* tfs_path used by tfs_eval_statistic (default MIXED) */
-  int pixel;         /* tfs_pixel: storage of d~/S and 1/S for the mixed path (default F16) */
+  int pixel;         /* tfs_pixel: storage of d~/S for the mixed path (default F16); 1/S is
+                        held in FP32 with every pixel type */
   int pn_order;      /* 0 Newtonian chirp, 1 1PN TaylorT3 (default 1) */
   int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1),
                         2 TDI-1.5 A/E */

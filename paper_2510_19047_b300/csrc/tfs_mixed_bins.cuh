@@ -13,8 +13,8 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Pixel loads: one element per (bin, tranche) holds both channels of u and w,
 // ur = (Re u_A, Re u_E), ui = (Im u_A, Im u_E), w = (w_A, w_E): one 128-bit load for
-// FP16/BF16 pixels, two for FP32. raw() loads, cvt() widens to FP32 at the point of use
-// (the prefetched element stays packed).
+// FP16/BF16 u (w is stored in FP32 in the same 16 bytes), two for FP32. raw() loads,
+// cvt() widens u to FP32 at the point of use (the prefetched element stays packed).
 template <int PIX>
 struct PixLoad;
 template <>
@@ -40,7 +40,7 @@ struct PixLoad<TFS_PIX_F16> {
   __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
     ur = cv(v.x);
     ui = cv(v.y);
-    w = cv(v.z);
+    w = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
   }
 };
 template <>
@@ -54,7 +54,7 @@ struct PixLoad<TFS_PIX_BF16> {
   __device__ static void cvt(const P& v, float2& ur, float2& ui, float2& w) {
     ur = cv(v.x);
     ui = cv(v.y);
-    w = cv(v.z);
+    w = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
   }
 };
 

@@ -140,9 +140,9 @@ __global__ void k_pack_ref(int64_t n, const double* d_re, const double* d_im, co
 // Mixed-path layout: one frequency-major plane P[k][m], m padded to `pitch`, so that
 // the 32 lanes of a warp, which handle 32 consecutive tranches of one template, read
 // consecutive elements. Each element holds both channels of u and w,
-// (Re u_A, Re u_E, Im u_A, Im u_E, w_A, w_E): one 16-byte element for FP16/BF16 (two
-// padding halves), 32 bytes for FP32; one conversion yields both channels and one
-// packed f32x2 operation updates both channels' sums.
+// (Re u_A, Re u_E, Im u_A, Im u_E, w_A, w_E): one 16-byte element for FP16/BF16 u (four
+// halves) with w in FP32 (two floats, which need no widening in the kernel), 32 bytes
+// for FP32; one packed f32x2 operation updates both channels' sums.
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -177,10 +177,10 @@ __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const do
       o[1] = make_float4(v[0][2], v[1][2], 0.f, 0.f);
     } else if (PIX == TFS_PIX_F16) {
       ((uint4*)out)[i] = make_uint4(pack_h2(v[0][0], v[1][0]), pack_h2(v[0][1], v[1][1]),
-                                    pack_h2(v[0][2], v[1][2]), 0u);
+                                    __float_as_uint(v[0][2]), __float_as_uint(v[1][2]));
     } else {
       ((uint4*)out)[i] = make_uint4(pack_b2(v[0][0], v[1][0]), pack_b2(v[0][1], v[1][1]),
-                                    pack_b2(v[0][2], v[1][2]), 0u);
+                                    __float_as_uint(v[0][2]), __float_as_uint(v[1][2]));
     }
   }
 }

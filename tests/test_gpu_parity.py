@@ -10,9 +10,9 @@ Tolerances (relative error of Upsilon per template and level):
   mixed, FP32 pixels 1e-4
   mixed, FP16 pixels max 1.5e-3, p99 1e-3   (3x and 2x the FP16 unit roundoff 2^-11)
   mixed, BF16 pixels max 1.2e-2, p99 8e-3   (3x and 2x the BF16 unit roundoff 2^-8)
-The reduced-precision bounds follow from rounding u = d~/S and w = 1/S once to the
-storage type: each pixel carries an independent relative error below the unit
-roundoff, so |Z_n| and N_n move by a random fraction of it and Upsilon by about twice
+The reduced-precision bounds follow from rounding u = d~/S once to the storage type
+(w = 1/S is stored in FP32): each pixel carries an independent relative error below the
+unit roundoff, so |Z_n| moves by a random fraction of it and Upsilon by about twice
 that.
 """
 import numpy as np
@@ -108,7 +108,8 @@ def test_week_long_coherent_segments(week):
 def _round_pixels(D, pixel):
     """(d', w') whose u' = d' w' and w' are the pixels the mixed path stores: u = d w and
     w scaled by the library's powers of two (largest |component| to 2^14 < 2^ceil(log2)),
-    rounded to FP32 and then to FP16 or BF16 (round to nearest even), scaled back."""
+    rounded to FP32, u then to FP16 or BF16 (round to nearest even; w stays FP32),
+    scaled back."""
     act = D.w > 0
     u = np.where(act, D.d * D.w, 0)
     umax = max(np.abs(u.real).max(), np.abs(u.imag).max())
@@ -123,7 +124,7 @@ def _round_pixels(D, pixel):
         b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
         return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
-    wq = np.where(act, rnd(D.w * sw) / sw, 0.0)
+    wq = np.where(act, (D.w * sw).astype(np.float32).astype(np.float64) / sw, 0.0)
     uq = (rnd(u.real * su) + 1j * rnd(u.imag * su)) / su
     dq = np.where(wq > 0, uq / np.where(wq > 0, wq, 1.0), 0)
     return dq, wq
