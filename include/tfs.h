@@ -67,7 +67,7 @@ typedef enum tfs_path {
   TFS_PATH_PLAIN = 1, /* the paper's mapping: one thread per template, Eq. fresnel-ft
                          evaluated bin by bin as printed, FP32 pixels, FP64 phase */
   TFS_PATH_MIXED = 2  /* warp per template, lane per tranche, phase-cancelled Fresnel
-                         kernel, FP16/BF16 pixels, FP32 accumulation, double-float
+                         kernel, FP16/BF16 u with FP32 w, FP32 accumulation, double-float
                          phase track, length-sorted persistent launch */
 } tfs_path;
 
