@@ -210,10 +210,11 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
   const int pitch = PITCH ? PITCH : a.pitch;
   const int H = a.harm.n;
-  const df dTd = df_make(g.dT);
-  const float dTf = (float)g.dT;
-  const float sig_k = (float)(sqrt(2.0) * g.df);   // sigma = df sqrt(2/fdot)
-  const float ncomp = (float)(10.0 * g.df / g.dT);  // fdot > 10 df / dT: non-compact
+  // grid constants as FP32 launch parameters (as in the single-mode kernel)
+  const df dTd = {a.mc.dT_hi, a.mc.dT_lo};
+  const float dTf = a.mc.dTf;
+  const float sig_k = a.mc.sig_k;  // sigma = df sqrt(2/fdot)
+  const float ncomp = a.mc.ncomp;  // fdot > 10 df / dT: non-compact
   // windows of two harmonics can share bins only below x = 21 / dnu_min (+ margin);
   // equal nu (dnu_min tiny) always, a single harmonic never
   const float x_ov = H > 1 ? 21.5f / a.harm.dnu_min : 0.0f;

@@ -69,10 +69,12 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   const GridDesc g = a.g;
   const typename Ld::P* __restrict__ PX = (const typename Ld::P*)a.Umix;
   const int pitch = PITCH ? PITCH : a.pitch;
-  const df dTd = df_make(g.dT);
-  const float dTf = (float)g.dT;
-  const float sig_k = (float)(sqrt(2.0) * g.df);       // sigma = df sqrt(2/fdot)
-  const float ncomp = (float)(10.0 * g.df / g.dT);      // fdot > 10 df / dT: non-compact
+  // grid constants as FP32 launch parameters: derived from the FP64 grid here, the
+  // compiler re-derives them inside the tranche loop on the narrow FP64 pipe
+  const df dTd = {a.mc.dT_hi, a.mc.dT_lo};
+  const float dTf = a.mc.dTf;
+  const float sig_k = a.mc.sig_k;  // sigma = df sqrt(2/fdot)
+  const float ncomp = a.mc.ncomp;  // fdot > 10 df / dT: non-compact
   // FP32 pixels: the bin next to f_nm below it (x1 = f_nm/df - (k_c - 1)) and Psi are
   // formed from rb = f_nm/df - rint(f_nm/df), which keeps full relative precision when
   // f_nm is just above a bin. From aa = f_nm/df - k_c ~ -1 they keep ~6e-8 bins absolute
