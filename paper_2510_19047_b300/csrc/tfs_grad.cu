@@ -274,6 +274,7 @@ struct GradArgs {
   int64_t n_tpl;
   int seg_len, n_seg;
   double scale;         // Upsilon = scale * sum |Z|^2 / N
+  float twopidT, pidT2;  // 2 pi dT and pi dT^2 (FP32, formed on the host)
   double* out_stat;
   double* out_grad;     // [8][n]
   unsigned* counter;    // work ticket of the persistent launch (zero at launch)
@@ -681,10 +682,11 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v.z > 0.f) {
       const double zz = (double)v.x * v.x + (double)v.y * v.y;
-      ups += a.scale * zz / v.z;
-      o.x = (float)(2.0 * a.scale * v.x / v.z);  // lambda = 2 s conj(Z)/N
-      o.y = (float)(-2.0 * a.scale * v.y / v.z);
-      o.z = (float)(-a.scale * zz / ((double)v.z * v.z));  // mu
+      const double inz = 1.0 / (double)v.z, t = a.scale * inz;
+      ups += t * zz;
+      o.x = (float)(2.0 * t * v.x);  // lambda = 2 s conj(Z)/N
+      o.y = (float)(-2.0 * t * v.y);
+      o.z = (float)(-t * zz * inz);  // mu
     }
     seg[q] = o;
   }
@@ -702,7 +704,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
   // k < 21 accumulates field k across blocks in FP64, lanes 21-23 the phase shares of
   // t_c, P5, P3 (one FP64 add per lane and block: the FP64 pipe is slow)
   double Gown = 0.0;
-  const float twopidT = (float)(2.0 * kPi * a.g.dT), pidT2 = (float)(kPi * a.g.dT * a.g.dT);
+  const float twopidT = a.twopidT, pidT2 = a.pidT2;
   for (int m0 = mA; m0 < mB; m0 += 32) {
     const int m = m0 + lane;
     float gl[kSrcFields];
@@ -985,6 +987,8 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.n_seg = n_seg;
   a.seg_len = g.n_tranche / n_seg;
   a.scale = scale;
+  a.twopidT = (float)(2.0 * kPi * g.dT);
+  a.pidT2 = (float)(kPi * g.dT * g.dT);
   a.out_stat = out_stat;
   a.out_grad = out_grad;
   a.counter = counter;
