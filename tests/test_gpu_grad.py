@@ -60,6 +60,21 @@ def test_gradient_per_template_is_independent_of_batch(ae45):
     assert np.array_equal(u_all[7:8], u_one) and np.array_equal(g_all[:, 7:8], g_one)
 
 
+def test_split_work_items_match_one_item_per_template(ae45):
+    # a small batch splits each template's segments into work items whose partial sums
+    # are added afterwards; inside a large batch every template is one item. Both give
+    # the same FP32 segment sums, combined in another FP64 order
+    D = ae45
+    th = synth.candidates_near(D.injections, 24, seed=11)
+    c = ctx_for(D)
+    u_small, g_small = c.grad_statistic(th, 16)
+    big = np.concatenate([th, synth.candidates_near(D.injections, 7976, seed=12)], axis=1)
+    u_big, g_big = c.grad_statistic(big, 16)
+    np.testing.assert_allclose(u_small, u_big[:24], rtol=1e-12)
+    scale = np.abs(g_big[:, :24]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g_small - g_big[:, :24]) <= 1e-9 * scale)
+
+
 def test_autograd_and_ascent(ae45):
     import torch
     from paper_2510_19047_b300.autograd import statistic
