@@ -18,5 +18,5 @@ from .build import load_library, build  # noqa: F401
 from .api import (  # noqa: F401
     statistic, gradient, segments, fresnel, tranche_ft, source_constants, track, response,
     detector_tensors, polarisation, max_threads, response_tdi, spacecraft_offsets,
-    statistic_harm, segments_harm,
+    statistic_harm, segments_harm, gradient_scale,
 )

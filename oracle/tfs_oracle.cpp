@@ -339,30 +339,40 @@ struct Source {
   R nhat[3];             // direction to the source (cos b cos l, cos b sin l, sin b)
 };
 
+// Chirp constants are evaluated at the precision of R with the exact rational
+// exponents and coefficients (-3/5, -8/3, -5/3, 743/2688, ...) and pi and G M_sun/c^3
+// to extended precision: their double roundings would bias t_c and P5 by ~1e-16
+// relative, which a two-year phase of ~1e7 rad turns into ~1e-9 rad.
+constexpr long double PI_L = 3.141592653589793238462643383279502884L;
+constexpr long double GMSUN_S_L = 4.925490947e-6L;
+static inline double powq(double x, long double p) { return std::pow(x, (double)p); }
+static inline long double powq(long double x, long double p) { return std::pow(x, p); }
+static inline Dual powq(const Dual& x, long double p) { return pow_(x, (double)p); }
+
 // 1PN TaylorT3 coefficients (GW phase = 2 x orbital phase; Theta = eta (t_c - t)/(5M)):
 //   f   = Theta^(-3/8) / (8 pi M) [1 + (743/2688 + 11 eta/32) Theta^(-1/4)]
 //   Phi = phi_c - (2/eta) Theta^(5/8) [1 + (3715/8064 + 55 eta/96) Theta^(-1/4)]
 template <class R>
 static Source<R> make_source(const R th[NPAR], int pn_order) {
   Source<R> s;
-  const R Mc = th[0] * GMSUN_S;
+  const R Mc = th[0] * R(GMSUN_S_L);
   const R eta = th[1];
   const R f0 = th[2];
   s.phi0 = th[3];
   if (pn_order == 0) {
     // Newtonian chirp: tau0 = (5/256) (pi f0)^(-8/3) Mc^(-5/3),
     // f = f0 (1 - t/tau0)^(-3/8), Phi = phi0 + (16 pi/5) f0 tau0 [1 - (1 - t/tau0)^(5/8)].
-    const R tau0 = (5.0 / 256.0) * pow_(PI * f0, -8.0 / 3.0) * pow_(Mc, -5.0 / 3.0);
+    const R tau0 = (5.0 / 256.0) * powq(R(PI_L) * f0, -8.0L / 3.0L) * powq(Mc, -5.0L / 3.0L);
     s.tc = tau0;
     s.F0 = f0;
     s.C2 = R(0.0);
-    s.P5 = (16.0 * PI / 5.0) * f0 * tau0;
+    s.P5 = R(16.0L * PI_L / 5.0L) * f0 * tau0;
     s.P3 = R(0.0);
   } else {
-    const R M = Mc * pow_(eta, -0.6);
-    const R cf = 743.0 / 2688.0 + (11.0 / 32.0) * eta;
-    const R cp = 3715.0 / 8064.0 + (55.0 / 96.0) * eta;
-    const R y = 8.0 * PI * M * f0;  // x^3 + cf x^5 = y, x = Theta^(-1/8)
+    const R M = Mc * powq(eta, -3.0L / 5.0L);
+    const R cf = R(743.0L / 2688.0L) + (11.0 / 32.0) * eta;
+    const R cp = R(3715.0L / 8064.0L) + R(55.0L / 96.0L) * eta;
+    const R y = R(8.0L * PI_L) * M * f0;  // x^3 + cf x^5 = y, x = Theta^(-1/8)
     // Newton iterations on the value, then two on R so that derivatives follow the
     // implicit function theorem exactly.
     double xv = std::cbrt(val(y));
@@ -381,7 +391,7 @@ static Source<R> make_source(const R th[NPAR], int pn_order) {
     }
     const R Theta0 = pow_(x, -8.0);
     s.tc = 5.0 * M * Theta0 / eta;
-    s.F0 = x * x * x / (8.0 * PI * M);
+    s.F0 = x * x * x / (R(8.0L * PI_L) * M);
     s.C2 = cf * x * x;
     s.P5 = (2.0 / eta) * pow_(Theta0, 0.625);
     s.P3 = (2.0 / eta) * cp * pow_(Theta0, 0.375);
@@ -635,7 +645,8 @@ struct Diag {
 template <class R>
 static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp, int fmode,
                          int n_seg, R& out, Diag* diag, double* seg_zr = nullptr,
-                         double* seg_zi = nullptr, double* seg_n = nullptr) {
+                         double* seg_zi = nullptr, double* seg_n = nullptr,
+                         R* seg_full = nullptr) {
   const Source<R> src = make_source(th, pn_order);
   const int seg_len = g.n_tranche / n_seg;
   R ups(0.0);
@@ -688,6 +699,11 @@ static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp
       seg_zr[n] = val(Z.re);
       seg_zi[n] = val(Z.im);
       seg_n[n] = val(N);
+    }
+    if (seg_full) {
+      seg_full[3 * n] = Z.re;
+      seg_full[3 * n + 1] = Z.im;
+      seg_full[3 * n + 2] = N;
     }
     if (val(N) > 0.0) {
       ups += 4.0 * (Z.re * Z.re + Z.im * Z.im) / N;
@@ -872,6 +888,48 @@ int oracle_gradient(int n_chan, int n_tranche, int n_bins, double dT, double t0,
     statistic_one<Dual>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, nullptr);
     out_stat[i] = ups.v;
     for (int p = 0; p < NPAR; ++p) out_grad[p * n_tpl + i] = ups.d[p];
+  }
+  return ORC_OK;
+}
+
+// Term scale of each gradient component: dUpsilon/dtheta_p is the sum over segments of
+//   8 Re(conj(Z_n) dZ_n/dtheta_p) / N_n  -  4 |Z_n|^2 (dN_n/dtheta_p) / N_n^2
+// (Eq. Upsilon-seg differentiated); out_scale[p][i] is the sum of the absolute values of
+// those 2 N_seg terms. A component much smaller than its term scale is a cancelling sum,
+// which arithmetic of unit roundoff u resolves only to ~u times the scale.
+int oracle_gradient_scale(int n_chan, int n_tranche, int n_bins, double dT, double t0,
+                          const double* d_re, const double* d_im, const double* w,
+                          const uint8_t* mask, int pn_order, int resp, int fresnel_mode,
+                          const double* theta, int64_t n_tpl, int n_seg, double* out_scale,
+                          int n_threads) {
+  if (!grid_ok(n_chan, n_tranche, n_bins, dT) || n_tpl < 0 || !theta || !out_scale)
+    return ORC_ERR_ARG;
+  if (n_seg < 1 || n_tranche % n_seg != 0) return ORC_ERR_NSEG;
+  Grid g{n_chan, n_tranche, n_bins, dT, t0, 1.0 / dT, d_re, d_im, w, mask};
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t i = 0; i < n_tpl; ++i) {
+    Dual th[NPAR];
+    for (int p = 0; p < NPAR; ++p) {
+      th[p] = Dual(theta[p * n_tpl + i]);
+      th[p].d[p] = 1.0;
+    }
+    Dual ups;
+    std::vector<Dual> seg(3 * (size_t)n_seg);
+    statistic_one<Dual>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, nullptr, nullptr,
+                        nullptr, nullptr, seg.data());
+    for (int p = 0; p < NPAR; ++p) {
+      double sc = 0.0;
+      for (int n = 0; n < n_seg; ++n) {
+        const Dual &zr = seg[3 * n], &zi = seg[3 * n + 1], &nn = seg[3 * n + 2];
+        if (!(nn.v > 0.0)) continue;
+        sc += std::fabs(8.0 * (zr.v * zr.d[p] + zi.v * zi.d[p]) / nn.v) +
+              std::fabs(4.0 * (zr.v * zr.v + zi.v * zi.v) * nn.d[p] / (nn.v * nn.v));
+      }
+      out_scale[p * n_tpl + i] = sc;
+    }
   }
   return ORC_OK;
 }
