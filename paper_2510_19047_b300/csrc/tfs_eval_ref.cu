@@ -4,8 +4,8 @@
 // the waveform:
 //
 //   k_eval_fp64  - FP64 throughout, the Fresnel-kernel transform in the
-//                  phase-cancelled form (see below), phase accumulated per tranche
-//                  with compensated summation. The parity path.
+//                  phase-cancelled form (see below), the absolute phase of each
+//                  tranche from double-double chirp constants. The parity path.
 //   k_eval_plain - the printed Eq. fresnel-ft evaluated bin by bin: Fresnel C, S of
 //                  v_1, v_2 and the factor exp(i(phi - pi fdot zeta^2)), with FP32
 //                  pixels and FP32 Fresnel/trig; the large trig arguments are reduced
@@ -21,6 +21,7 @@
 // bins of a tranche: the two ~1e5-rad arguments cancel exactly instead of numerically.
 #include <math.h>
 
+#include "tfs_dd.cuh"
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
 #include "tfs_tdi.cuh"
@@ -53,7 +54,8 @@ __device__ __forceinline__ TrackD track_fp64(const TplConst& c, const TrancheD& 
   return r;
 }
 
-// Phase advanced, in cycles, from barycentre time ta to ta + dt (both before t_c):
+// Phase advanced, in cycles, from barycentre time ta to ta + dt (both before t_c), for
+// the plain path's FP64 phase track:
 // [P5 (ua^(5/8) - ub^(5/8)) + P3 (ua^(3/8) - ub^(3/8))] / 2 pi with ub = ua (1 + rho),
 // rho = -dt / (t_c - ta), written with log1p/expm1 so that it keeps full relative
 // precision for small steps.
@@ -177,8 +179,8 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
     cur[l] = -1;
   }
   int nact = 0, nnc = 0;
-  int blk = -1, m_prev = 0;
-  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0;
+  const dd tcd = {c.tc, c.tc_lo}, P5d = {c.P5, c.P5_lo}, P3d = {c.P3, c.P3_lo};
+  const dd ph0 = dd_mul_d(kInv2PiDD, c.phi0);
   for (int m = c.m_lo; m < c.m_hi; ++m) {
     for (int l = 0; l < L.n; ++l) {
       const int s = m / L.seg_len[l];
@@ -200,23 +202,9 @@ __global__ void __launch_bounds__(128) k_eval_fp64(EvalArgs a) {
     const double kcd = ceil(x);
     const int kc = (int)kcd;
     if (kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) continue;
-    // phase in cycles since the start of this anchor block (a block holds whole
-    // segments of every level, so a constant offset per block is maximised away)
-    const int b = m / L.anchor;
-    if (b != blk) {
-      blk = b;
-      m_prev = b * L.anchor;
-      const TrancheD ta = a.tabD[m_prev];
-      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
-      tp_prev = ta.t + d0_prev;
-      acc = comp = 0.0;
-    }
-    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
-    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
-    tp_prev = tk.tp;
-    d0_prev = tk.d0;
-    m_prev = m;
-    const double cyc = (acc - floor(acc)) - comp;
+    // absolute phase Phi(t'_nm) / 2 pi in cycles, formed in double-double and reduced
+    // to [0, 1): ~1e-16 cycles however far the track has advanced
+    const double cyc = dd_frac(dd_add(chirp_cycles_dd(tcd, P5d, P3d, tr.t, tk.d0), ph0));
     ++nact;
     if (tk.fdot * g.dT > 10.0 * g.df) ++nnc;
 
@@ -297,8 +285,8 @@ struct HarmD {
 template <bool TDI>
 __device__ __forceinline__ HarmD harm_fp64(const EvalArgs& a, const TplConst& c,
                                            const TrancheD& tr, const TrackD& tk, double amp,
-                                           double ph_int, double ph_frac, const double Tlr[2],
-                                           const double Tli[2], int h) {
+                                           dd cyc_abs, const double Tlr[2], const double Tli[2],
+                                           int h) {
   HarmD r;
   r.on = false;
   const GridDesc& g = a.g;
@@ -315,11 +303,8 @@ __device__ __forceinline__ HarmD harm_fp64(const EvalArgs& a, const TplConst& c,
   sincospi(2.0 * r.aa + fdh * g.dT * g.dT, &r.spsi, &r.cpsi);
   double Tr[2] = {Tlr[0], Tlr[1]}, Ti[2] = {Tli[0], Tli[1]};
   if (TDI) response_factors<double, true>(c, tr, fh, a.response, Tr, Ti);
-  // nu (I + F) cycles, Phi / 2 pi = I + F: nu I split exactly into product and error
-  const double p = nu * ph_int;
-  const double pe = fma(nu, ph_int, -p);
-  double cyc = (p - floor(p)) + pe + nu * ph_frac;
-  cyc -= floor(cyc);
+  // nu Phi / 2 pi, reduced to [0, 1) in double-double
+  const double cyc = dd_frac(dd_mul_d(cyc_abs, nu));
   double sph, cph;
   sincospi(2.0 * cyc, &sph, &cph);
   const double P = amp / sqrt(2.0 * fdh);
@@ -351,9 +336,8 @@ __global__ void __launch_bounds__(128) k_eval_fp64_harm(EvalArgs a) {
     cur[l] = -1;
   }
   int nact = 0, nnc = 0;
-  int blk = -1, m_prev = 0;
-  double acc = 0.0, comp = 0.0, tp_prev = 0.0, d0_prev = 0.0;
-  double ph_a = 0.0;  // Phi / 2 pi at the anchor block's first tranche
+  const dd tcd = {c.tc, c.tc_lo}, P5d = {c.P5, c.P5_lo}, P3d = {c.P3, c.P3_lo};
+  const dd ph0 = dd_mul_d(kInv2PiDD, c.phi0);
   HarmD hd[TFS_MAX_HARMONICS];
   for (int m = c.m_lo; m < c.m_hi; ++m) {
     for (int l = 0; l < L.n; ++l) {
@@ -372,24 +356,8 @@ __global__ void __launch_bounds__(128) k_eval_fp64_harm(EvalArgs a) {
     const TrackD tk = track_fp64(c, tr, a.response);
     if (!(tk.tp < c.tc)) break;
     if (!(tk.fdot > 0.0)) continue;
-    const int b = m / L.anchor;
-    if (b != blk) {
-      blk = b;
-      m_prev = b * L.anchor;
-      const TrancheD ta = a.tabD[m_prev];
-      d0_prev = a.response ? c.dop_c * ta.ca + c.dop_s * ta.sa : 0.0;
-      tp_prev = ta.t + d0_prev;
-      acc = comp = 0.0;
-      ph_a = c.phi0 * (0.5 / kPi) + phase_step_cycles(c, 0.0, tp_prev);
-    }
-    const double dt_ab = (double)(m - m_prev) * g.dT + (tk.d0 - d0_prev);
-    kahan_add(acc, comp, phase_step_cycles(c, tp_prev, dt_ab));
-    tp_prev = tk.tp;
-    d0_prev = tk.d0;
-    m_prev = m;
-    // Phi / 2 pi = ph_int + ph_frac with ph_int an integer
-    const double ph_int = floor(ph_a) + floor(acc);
-    const double ph_frac = (ph_a - floor(ph_a)) + ((acc - floor(acc)) - comp);
+    // absolute phase Phi(t'_nm) / 2 pi in cycles (double-double, not reduced)
+    const dd cyc = dd_add(chirp_cycles_dd(tcd, P5d, P3d, tr.t, tk.d0), ph0);
 
     double Tlr[2] = {1.0, 1.0}, Tli[2] = {0.0, 0.0};
     if (!TDI) response_factors<double, false>(c, tr, tk.f, a.response, Tlr, Tli);
@@ -397,7 +365,7 @@ __global__ void __launch_bounds__(128) k_eval_fp64_harm(EvalArgs a) {
     double Zr = 0.0, Zi = 0.0, N = 0.0;
     bool any = false;
     for (int h = 0; h < H; ++h) {
-      hd[h] = harm_fp64<TDI>(a, c, tr, tk, amp, ph_int, ph_frac, Tlr, Tli, h);
+      hd[h] = harm_fp64<TDI>(a, c, tr, tk, amp, cyc, Tlr, Tli, h);
       const HarmD& q = hd[h];
       if (!q.on) continue;
       any = true;

@@ -65,6 +65,8 @@ struct __align__(16) TplConst {
   uint32_t key;         // sort key (longer tracks first, then start frequency)
   int kc_lo;            // window centre bin at m_lo
   double nz;            // sin(beta): z component of the direction to the source
+  double tc_lo, P5_lo, P3_lo;  // t_c, P5, P3 as double-doubles (tc + tc_lo, ...): the
+                               // FP64 path's absolute phase needs them beyond FP64
 };
 
 // The same constants split for the mixed path's double-float / FP32 arithmetic

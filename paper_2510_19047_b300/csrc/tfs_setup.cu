@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "tfs_dd.cuh"
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
 #include "tfs_source.cuh"
@@ -210,18 +211,22 @@ __device__ __forceinline__ void split(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
+// The template's constant phase K = (phi0 + P5 + P3) / 2 pi in cycles (dd).
+__device__ __forceinline__ dd const_cycles(const TplConst& c) {
+  const dd B = dd_add_d(dd_add(dd{c.P5, c.P5_lo}, dd{c.P3, c.P3_lo}), c.phi0);
+  return dd_mul(B, kInv2PiDD);
+}
+
 __device__ TplMix mix_of(const TplConst& c) {
   TplMix t;
   split(1.0 / c.tc, t.tcinv_hi, t.tcinv_lo);
   split(c.F0, t.F0_hi, t.F0_lo);
-  split(c.P5 * (0.5 / kPi), t.P5_hi, t.P5_lo);
-  split(c.P3 * (0.5 / kPi), t.P3_hi, t.P3_lo);
+  const dd P5c = dd_mul(dd{c.P5, c.P5_lo}, kInv2PiDD), P3c = dd_mul(dd{c.P3, c.P3_lo}, kInv2PiDD);
+  split(P5c.hi, t.P5_hi, t.P5_lo);
+  split(P3c.hi, t.P3_hi, t.P3_lo);
   // Phi/2pi = phi0/2pi + P5 (1 - u^5/8) + P3 (1 - u^3/8) = K - P5 u^5/8 - P3 u^3/8; the
   // integer part of K is irrelevant
-  const double ph = c.phi0 * (0.5 / kPi);
-  const double P5c = c.P5 * (0.5 / kPi), P3c = c.P3 * (0.5 / kPi);
-  const double K = (ph - floor(ph)) + (P5c - floor(P5c)) + (P3c - floor(P3c));
-  split(K - floor(K), t.K_hi, t.K_lo);
+  split(dd_frac(const_cycles(c)), t.K_hi, t.K_lo);
   split(c.dop_c, t.dopc_hi, t.dopc_lo);
   split(c.dop_s, t.dops_hi, t.dops_lo);
   t.C2 = (float)c.C2;
@@ -261,11 +266,17 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
     return;
   }
   const SrcT<double> src = source_of<double>(th, pn_order);
-  c.tc = src.tc;
+  // t_c, P5, P3 to double-double precision (their FP64 roundings would move a two-year
+  // phase by ~1e-9 rad); the FP64 values are the dd values' leading parts
+  const ChirpDD cd = chirp_dd(th[0], eta, f0, pn_order);
+  c.tc = cd.tc.hi;
+  c.tc_lo = cd.tc.lo;
   c.F0 = src.F0;
   c.C2 = src.C2;
-  c.P5 = src.P5;
-  c.P3 = src.P3;
+  c.P5 = cd.P5.hi;
+  c.P5_lo = cd.P5.lo;
+  c.P3 = cd.P3.hi;
+  c.P3_lo = cd.P3.lo;
   c.phi0 = src.phi0;
   for (int k = 0; k < 6; ++k) {
     c.pp[k] = src.pp[k];
@@ -367,8 +378,7 @@ cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int*
 
 // Constant phase of each harmonic of each template: with Phi / 2 pi = K - S,
 // K = (phi0 + P5 + P3) / 2 pi and S = (P5 u^(5/8) + P3 u^(3/8)) / 2 pi, harmonic h has
-// phase nu_h K - nu_h S cycles; K[i][h] = frac(nu_h K) (the product split into its
-// rounded value and exact error before the fraction is taken).
+// phase nu_h K - nu_h S cycles; K[i][h] = frac(nu_h K), formed in double-double.
 __global__ void k_harm_phase(const TplConst* __restrict__ tpl, int64_t n, HarmSet h,
                              float2* __restrict__ K) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -376,12 +386,7 @@ __global__ void k_harm_phase(const TplConst* __restrict__ tpl, int64_t n, HarmSe
   const int64_t i = t / h.n;
   const int q = (int)(t - i * h.n);
   const TplConst c = tpl[i];
-  const double B = (c.phi0 + c.P5 + c.P3) * (0.5 / kPi);
-  const double nu = h.nu[q];
-  const double p = nu * B;
-  double r = (p - floor(p)) + fma(nu, B, -p);
-  r -= floor(r);
-  const df v = df_make(r);
+  const df v = df_make(dd_frac(dd_mul_d(const_cycles(c), h.nu[q])));
   K[t] = make_float2(v.hi, v.lo);
 }
 
