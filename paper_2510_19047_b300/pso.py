@@ -2,92 +2,66 @@
 
 The paper finds the maximum of Upsilon in each parameter tile with a particle swarm
 optimiser (Sec. "Implementation details"). This is a standard global-best swarm with an
-inertia weight. For each particle:
+inertia weight; for each particle and coordinate
 
     v <- w v + c1 r1 (p - x) + c2 r2 (g - x),    x <- x + v,
 
 where p is the particle's best position, g is its swarm's best, and r1, r2 ~ U(0, 1)
-are drawn per coordinate (for wrapped angles p - x and g - x take the shorter way
-round). Positions are wrapped for the angles (phi_0 and lambda mod 2 pi, psi mod pi)
-where the tile spans the whole period, and clipped to the tile otherwise and for the
-other parameters; clipping a coordinate stops its velocity. A parameter with lo == hi
-stays fixed.
+(for wrapped angles p - x and g - x take the shorter way round). Positions are wrapped
+for the angles (phi_0 and lambda mod 2 pi, psi mod pi) where the tile spans the whole
+period, and clipped to the tile otherwise and for the other parameters; clipping a
+coordinate stops its velocity. A parameter with lo == hi stays fixed.
 
 Many swarms, one per tile, run together. Every iteration evaluates all particles of all
-swarms with one call of the objective on the device; the bookkeeping is elementwise
-torch work on the same device.
+swarms with one call of the objective on the device (normally tfs_eval_statistic), and
+one tfs_pso_step launch updates the bests and moves the swarm: the random draws
+(Philox4x32-10 keyed by the seed) and the bookkeeping run in libtfs. This module only
+allocates the device state and sequences the calls.
 """
-import math
-
 import numpy as np
 
-PERIOD = {3: 2 * math.pi, 4: 2 * math.pi, 6: math.pi}  # phi_0, lambda, psi
+PERIOD = {3: 2 * np.pi, 4: 2 * np.pi, 6: np.pi}  # phi_0, lambda, psi
 
 
 def swarm(objective, lo, hi, n_particles, n_iter, seed=0, inertia=0.72, c1=1.49, c2=1.49,
-          device=None, history=None):
+          device=0, history=None, tfs=None):
     """Maximise `objective` over boxes.
 
-    objective: callable taking theta [8, N] (float64 tensor on `device`) and returning
-    [N] values. lo, hi: [n_swarms, 8] (or [8]) box corners per swarm. Returns
-    (best_theta [n_swarms, 8], best_value [n_swarms]) as tensors on `device`; if
-    `history` is a list, the best value per swarm after every iteration is appended.
+    objective: callable taking theta [8, S*P] (float64 CUDA tensor; particle i of swarm
+    s in column s*P + i) and returning the [S*P] values as a float64 CUDA tensor.
+    lo, hi: [n_swarms, 8] (or [8]) box corners per swarm. tfs: a binding.TFS context for
+    the swarm kernels (a new one on `device` if None). Returns (best_theta [S, 8],
+    best_value [S]) as CUDA tensors; if `history` is a list, the swarm bests after
+    every step (n_iter + 1 rows of [S], the initial evaluation first) are appended.
     """
     import torch
-    dev = torch.device(device) if device is not None else torch.device("cpu")
-    lo = torch.as_tensor(np.atleast_2d(lo), dtype=torch.float64, device=dev)
-    hi = torch.as_tensor(np.atleast_2d(hi), dtype=torch.float64, device=dev)
-    S = lo.shape[0]
-    P = int(n_particles)
-    g = torch.Generator(device=dev)
-    g.manual_seed(int(seed))
-    span = (hi - lo)[:, None, :]                         # [S, 1, 8]
-    x = lo[:, None, :] + span * torch.rand((S, P, 8), generator=g, dtype=torch.float64, device=dev)
-    v = 0.1 * span * (2 * torch.rand((S, P, 8), generator=g, dtype=torch.float64, device=dev) - 1)
-    fixed = (span == 0)
-    per = torch.zeros(8, dtype=torch.float64, device=dev)
-    for k, T in PERIOD.items():
-        per[k] = T
-    # an angle wraps only where the tile spans its whole period; otherwise it is clipped
-    periodic = (per > 0) & (span >= per * (1 - 1e-12))      # [S, 1, 8]
-
-    def toward(d):
-        # the shorter way round for wrapped angles
-        half = 0.5 * per
-        dw = torch.remainder(d + half, torch.where(per > 0, per, torch.ones_like(per))) - half
-        return torch.where(periodic, dw, d)
-
-    def evaluate(pos):
-        th = pos.reshape(S * P, 8).T.contiguous()
-        return objective(th).reshape(S, P)
-
-    f = evaluate(x)
-    pbest, pval = x.clone(), f.clone()
-    gi = torch.argmax(pval, dim=1)
-    gbest = pbest[torch.arange(S, device=dev), gi].clone()   # [S, 8]
-    gval = pval[torch.arange(S, device=dev), gi].clone()
-    for _ in range(int(n_iter)):
-        r1 = torch.rand((S, P, 8), generator=g, dtype=torch.float64, device=dev)
-        r2 = torch.rand((S, P, 8), generator=g, dtype=torch.float64, device=dev)
-        v = inertia * v + c1 * r1 * toward(pbest - x) + c2 * r2 * toward(gbest[:, None, :] - x)
-        v = torch.where(fixed, torch.zeros_like(v), v)
-        x = x + v
-        # angles wrap; everything else is clipped to the tile and loses its velocity there
-        wrapped = x - per * torch.floor(x / torch.where(per > 0, per, torch.ones_like(per)))
-        wrapped = torch.where(periodic, wrapped, x)
-        clipped = torch.minimum(torch.maximum(wrapped, lo[:, None, :]), hi[:, None, :])
-        hit = (clipped != wrapped) & ~periodic
-        v = torch.where(hit, torch.zeros_like(v), v)
-        x = torch.where(periodic & ~fixed, wrapped, clipped)
-        f = evaluate(x)
-        better = f > pval
-        pbest = torch.where(better[..., None], x, pbest)
-        pval = torch.where(better, f, pval)
-        gi = torch.argmax(pval, dim=1)
-        gv = pval[torch.arange(S, device=dev), gi]
-        upd = gv > gval
-        gbest = torch.where(upd[:, None], pbest[torch.arange(S, device=dev), gi], gbest)
-        gval = torch.where(upd, gv, gval)
-        if history is not None:
-            history.append(gval.clone())
-    return gbest, gval
+    from .binding import TFS, Swarm, _ptr
+    ctx = tfs if tfs is not None else TFS(device)
+    dev = torch.device("cuda", ctx.device)
+    lo = np.ascontiguousarray(np.atleast_2d(np.asarray(lo, dtype=np.float64)))
+    hi = np.ascontiguousarray(np.atleast_2d(np.asarray(hi, dtype=np.float64)))
+    if lo.shape != hi.shape or lo.shape[1] != 8:
+        raise ValueError("lo and hi must be [n_swarms, 8]")
+    S, P = lo.shape[0], int(n_particles)
+    f64 = dict(dtype=torch.float64, device=dev)
+    lo_d = torch.from_numpy(lo).to(dev)
+    hi_d = torch.from_numpy(hi).to(dev)
+    x = torch.empty((8, S * P), **f64)
+    v = torch.empty((8, S * P), **f64)
+    pbest = torch.empty((8, S * P), **f64)
+    pval = torch.empty(S * P, **f64)
+    gbest = torch.empty((8, S), **f64)
+    gval = torch.empty(S, **f64)
+    hist = torch.empty((int(n_iter) + 1, S), **f64) if history is not None else None
+    p = lambda t: _ptr(t)[0].value  # noqa: E731
+    sw = Swarm(S, P, p(lo_d), p(hi_d), float(inertia), float(c1), float(c2), int(seed),
+               p(x), p(v), p(pbest), p(pval), p(gbest), p(gval))
+    ctx.pso_init(sw, x)
+    for it in range(int(n_iter) + 1):
+        f = objective(x)
+        if not (f.is_cuda and f.dtype == torch.float64 and f.numel() == S * P):
+            raise ValueError("the objective must return S*P float64 values on the device")
+        ctx.pso_step(sw, f.contiguous(), it, it < int(n_iter), hist)
+    if history is not None:
+        history.extend(hist.unbind(0))
+    return gbest.T.contiguous(), gval
