@@ -37,7 +37,8 @@ def _lib():
             _D, _D, _D, _U8, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             _D, ctypes.c_int64, ctypes.c_int, _D, _D, ctypes.c_int]
         lib.oracle_gradient_scale.restype = ctypes.c_int
-        lib.oracle_gradient_scale.argtypes = lib.oracle_gradient.argtypes[:-3] + [_D, ctypes.c_int]
+        lib.oracle_gradient_scale.argtypes = lib.oracle_gradient.argtypes[:-3] + [
+            _D, ctypes.c_int, ctypes.c_int]
         lib.oracle_segments.restype = ctypes.c_int
         lib.oracle_segments.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -151,11 +152,15 @@ def gradient(d, w, mask, theta, n_seg, dT, t0=0.0, pn_order=PN_NEWTONIAN, respon
 
 
 def gradient_scale(d, w, mask, theta, n_seg, dT, t0=0.0, pn_order=PN_NEWTONIAN,
-                   response=RESP_NONE, fresnel_mode=FRESNEL_PAPER, n_threads=0):
-    """Term scale [8, n] of each gradient component: the sum over segments of the
-    absolute values of 8 Re(conj(Z_n) dZ_n)/N_n and 4 |Z_n|^2 dN_n/N_n^2, whose signed
-    sum is dUpsilon/dtheta_p (Eq. Upsilon-seg). A finite-precision evaluation resolves
-    a component only to about its unit roundoff times this scale."""
+                   response=RESP_NONE, fresnel_mode=FRESNEL_PAPER, tranche_level=False,
+                   n_threads=0):
+    """Term scale [8, n] of each gradient component, whose signed sum of terms is
+    dUpsilon/dtheta_p (Eq. Upsilon-seg differentiated): the sum over segments of the
+    absolute values of 8 Re(conj(Z_n) dZ_n)/N_n and 4 |Z_n|^2 dN_n/N_n^2, or with
+    tranche_level=True the sum over every (segment, tranche) of
+    |8 Re(conj(Z_n) dz_m)/N_n - 4 |Z_n|^2 dn_m/N_n^2| with z_m, n_m the tranche's shares.
+    An evaluation that forms those terms with unit roundoff u resolves a component only
+    to about u times its scale."""
     d_re, d_im, w, m = _grid(d, w, mask)
     th = np.ascontiguousarray(theta, dtype=np.float64)
     n = th.shape[1]
@@ -163,7 +168,7 @@ def gradient_scale(d, w, mask, theta, n_seg, dT, t0=0.0, pn_order=PN_NEWTONIAN,
     rc = _lib().oracle_gradient_scale(
         d_re.shape[0], d_re.shape[1], d_re.shape[2], float(dT), float(t0),
         _p(d_re), _p(d_im), _p(w), _p(m, _U8), int(pn_order), int(response), int(fresnel_mode),
-        _p(th), n, int(n_seg), _p(out), int(n_threads))
+        _p(th), n, int(n_seg), _p(out), int(bool(tranche_level)), int(n_threads))
     if rc != 0:
         raise ValueError(f"oracle_gradient_scale failed with code {rc}")
     return out

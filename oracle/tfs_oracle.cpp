@@ -646,7 +646,8 @@ template <class R>
 static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp, int fmode,
                          int n_seg, R& out, Diag* diag, double* seg_zr = nullptr,
                          double* seg_zi = nullptr, double* seg_n = nullptr,
-                         R* seg_full = nullptr) {
+                         R* seg_full = nullptr, std::vector<R>* tr_vals = nullptr,
+                         std::vector<int>* tr_seg = nullptr) {
   const Source<R> src = make_source(th, pn_order);
   const int seg_len = g.n_tranche / n_seg;
   R ups(0.0);
@@ -690,9 +691,19 @@ static int statistic_one(const Grid& g, const R th[NPAR], int pn_order, int resp
           nc[c] += hh * wr;
         }
       }
+      Cx<R> zt = {R(0.0), R(0.0)};
+      R nt(0.0);
       for (int c = 0; c < g.n_chan; ++c) {
-        Z = cadd(Z, cmul(T[c], zc[c]));
-        N += (T[c].re * T[c].re + T[c].im * T[c].im) * nc[c];
+        zt = cadd(zt, cmul(T[c], zc[c]));
+        nt += (T[c].re * T[c].re + T[c].im * T[c].im) * nc[c];
+      }
+      Z = cadd(Z, zt);
+      N += nt;
+      if (tr_vals) {  // this tranche's share of Z_n and N_n
+        tr_vals->push_back(zt.re);
+        tr_vals->push_back(zt.im);
+        tr_vals->push_back(nt);
+        tr_seg->push_back(n);
       }
     }
     if (seg_zr) {
@@ -894,14 +905,17 @@ int oracle_gradient(int n_chan, int n_tranche, int n_bins, double dT, double t0,
 
 // Term scale of each gradient component: dUpsilon/dtheta_p is the sum over segments of
 //   8 Re(conj(Z_n) dZ_n/dtheta_p) / N_n  -  4 |Z_n|^2 (dN_n/dtheta_p) / N_n^2
-// (Eq. Upsilon-seg differentiated); out_scale[p][i] is the sum of the absolute values of
-// those 2 N_seg terms. A component much smaller than its term scale is a cancelling sum,
-// which arithmetic of unit roundoff u resolves only to ~u times the scale.
+// (Eq. Upsilon-seg differentiated). tranche_level == 0: out_scale[p][i] is the sum of
+// the absolute values of those 2 N_seg terms; tranche_level == 1: Z_n and N_n are split
+// into their tranches' shares z_m, n_m (Eq. inner-tranche-tf) and out_scale is the sum
+// over every (segment, tranche) of |8 Re(conj(Z_n) dz_m)/N_n - 4 |Z_n|^2 dn_m/N_n^2|.
+// A component much smaller than its term scale is a cancelling sum, which arithmetic of
+// unit roundoff u that forms those terms resolves only to ~u times the scale.
 int oracle_gradient_scale(int n_chan, int n_tranche, int n_bins, double dT, double t0,
                           const double* d_re, const double* d_im, const double* w,
                           const uint8_t* mask, int pn_order, int resp, int fresnel_mode,
                           const double* theta, int64_t n_tpl, int n_seg, double* out_scale,
-                          int n_threads) {
+                          int tranche_level, int n_threads) {
   if (!grid_ok(n_chan, n_tranche, n_bins, dT) || n_tpl < 0 || !theta || !out_scale)
     return ORC_ERR_ARG;
   if (n_seg < 1 || n_tranche % n_seg != 0) return ORC_ERR_NSEG;
@@ -917,16 +931,30 @@ int oracle_gradient_scale(int n_chan, int n_tranche, int n_bins, double dT, doub
       th[p].d[p] = 1.0;
     }
     Dual ups;
-    std::vector<Dual> seg(3 * (size_t)n_seg);
+    std::vector<Dual> seg(3 * (size_t)n_seg), trv;
+    std::vector<int> trs;
     statistic_one<Dual>(g, th, pn_order, resp, fresnel_mode, n_seg, ups, nullptr, nullptr,
-                        nullptr, nullptr, seg.data());
+                        nullptr, nullptr, seg.data(), tranche_level ? &trv : nullptr,
+                        tranche_level ? &trs : nullptr);
     for (int p = 0; p < NPAR; ++p) {
       double sc = 0.0;
-      for (int n = 0; n < n_seg; ++n) {
-        const Dual &zr = seg[3 * n], &zi = seg[3 * n + 1], &nn = seg[3 * n + 2];
-        if (!(nn.v > 0.0)) continue;
-        sc += std::fabs(8.0 * (zr.v * zr.d[p] + zi.v * zi.d[p]) / nn.v) +
-              std::fabs(4.0 * (zr.v * zr.v + zi.v * zi.v) * nn.d[p] / (nn.v * nn.v));
+      if (tranche_level) {
+        // every (segment, tranche) term 8 Re(conj(Z_n) dz_m)/N_n - 4 |Z_n|^2 dn_m / N_n^2
+        for (size_t t = 0; t < trs.size(); ++t) {
+          const int n = trs[t];
+          const Dual &zr = seg[3 * n], &zi = seg[3 * n + 1], &nn = seg[3 * n + 2];
+          if (!(nn.v > 0.0)) continue;
+          const Dual &mr = trv[3 * t], &mi = trv[3 * t + 1], &mn = trv[3 * t + 2];
+          sc += std::fabs(8.0 * (zr.v * mr.d[p] + zi.v * mi.d[p]) / nn.v -
+                          4.0 * (zr.v * zr.v + zi.v * zi.v) * mn.d[p] / (nn.v * nn.v));
+        }
+      } else {
+        for (int n = 0; n < n_seg; ++n) {
+          const Dual &zr = seg[3 * n], &zi = seg[3 * n + 1], &nn = seg[3 * n + 2];
+          if (!(nn.v > 0.0)) continue;
+          sc += std::fabs(8.0 * (zr.v * zr.d[p] + zi.v * zi.d[p]) / nn.v) +
+                std::fabs(4.0 * (zr.v * zr.v + zi.v * zi.v) * nn.d[p] / (nn.v * nn.v));
+        }
       }
       out_scale[p * n_tpl + i] = sc;
     }

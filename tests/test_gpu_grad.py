@@ -1,5 +1,19 @@
-"""Adjoint gradient kernel against the oracle's dual-number gradient and central
-differences of the CUDA FP64 path; the autograd wrapper and an ascent step."""
+"""Adjoint gradient kernel (tfs_grad_statistic) against the oracle's dual-number
+gradient, and against 5-point central differences (step 1e-6 relative) of the GPU's own
+FP64 statistic path; the autograd wrapper and the refinement steps.
+
+Bound. dUpsilon/dtheta_p is a sum, over every (segment n, tranche m), of the terms
+t_nm = 8 Re(conj(Z_n) dz_m)/N_n - 4 |Z_n|^2 dn_m/N_n^2 (Eq. Upsilon-seg differentiated,
+z_m and n_m the tranche's shares of Z_n and N_n). The kernel forms each tranche's share
+in FP32, so it resolves the component to ~u32 = 6e-8 of S_p = sum |t_nm|, the oracle's
+tranche-level term scale, and no better: where the terms cancel (dUpsilon/dpsi is
+exactly zero for circular polarisation, iota = 0 or pi, while its per-tranche terms are
+of the order of Upsilon) no FP32 evaluation has a relative error below 1. Each
+component is therefore held to 2e-5 S_p (~340 u32; measured <= 2.3e-6 S_p on these
+candidates), which is a relative bound of 1e-4 wherever the component is at least a
+fifth of its scale. phi_0 is maximised away (zero exactly); its value is held to 2e-5 of
+the statistic (measured <= 2.2e-6).
+"""
 import numpy as np
 import pytest
 
@@ -29,26 +43,70 @@ def ae45_tdi():
                         response="tdi")
 
 
+GRAD_TOL = 2e-5   # of the tranche-level term scale
+PHI0_TOL = 2e-5   # of Upsilon
+
+
 @pytest.mark.parametrize("n_seg", [16, 1])
 @pytest.mark.parametrize("data", ["ae45", "ae45_tdi"])
 def test_gradient_matches_oracle(data, n_seg, request):
     D = request.getfixturevalue(data)
     th = synth.candidates_near(D.injections, 24, seed=3)
-    ref_u, ref_g = oracle.gradient(D.d, D.w, D.mask, th, n_seg, D.dT, pn_order=1,
-                                   response=D.response)
+    kw = dict(pn_order=1, response=D.response)
+    ref_u, ref_g = oracle.gradient(D.d, D.w, D.mask, th, n_seg, D.dT, **kw)
+    S = oracle.gradient_scale(D.d, D.w, D.mask, th, n_seg, D.dT, tranche_level=True, **kw)
     c = ctx_for(D)
     u, g = c.grad_statistic(th, n_seg)
     np.testing.assert_allclose(u, ref_u, rtol=1e-4)
-    # per component, relative to the component or to the gradient's own scale
-    # (|dU/dtheta_p| * |theta range|), whichever is larger
-    for p in range(8):
-        if p == 3:
-            assert np.all(np.abs(g[3]) < 1e-3 * ref_u)  # phi_0 is maximised away
-            continue
-        scale = np.maximum(np.abs(ref_g[p]), 1e-3 * np.abs(ref_g[p]).max())
-        err = np.abs(g[p] - ref_g[p]) / scale
-        assert err.max() < 2e-3, (p, err.max())
-        assert np.median(np.abs(g[p] - ref_g[p]) / np.maximum(np.abs(ref_g[p]), 1e-300)) < 1e-4, p
+    assert np.all(np.abs(g[3]) <= PHI0_TOL * ref_u)  # phi_0 is maximised away
+    n_rel = 0
+    for p in (0, 1, 2, 4, 5, 6, 7):
+        err = np.abs(g[p] - ref_g[p])
+        assert np.all(err <= GRAD_TOL * S[p]), (p, (err / S[p]).max())
+        # where the component is not a cancelling sum the bound is relative
+        big = np.abs(ref_g[p]) >= 0.2 * S[p]
+        assert np.all(err[big] <= 1e-4 * np.abs(ref_g[p][big])), p
+        n_rel += int(big.sum())
+    assert n_rel >= 10  # the relative form is exercised
+
+
+@pytest.mark.parametrize("data", ["ae45", "ae45_tdi"])
+def test_gradient_matches_central_differences(data, request):
+    """Config 5's check: 5-point central differences with step h = 1e-6 relative
+    (1e-6 rad where an angle is below 1) of the FP64 statistic path, at N_seg = 16.
+    Where the stencils at h and h/2 disagree, a window or Fresnel-branch switch lies
+    inside the stencil and the almost-everywhere derivative is not what the differences
+    see (reading Q16): such pairs are excluded and counted. The differences agree with
+    the oracle to 1e-5 relative plus 2e-6 of the term scale (measured <= 6.8e-7 S), and
+    the adjoint kernel agrees with them within its own bound."""
+    D = request.getfixturevalue(data)
+    n_seg = 16
+    th = synth.candidates_near(D.injections, 24, seed=3)
+    kw = dict(pn_order=1, response=D.response)
+    _, ref_g = oracle.gradient(D.d, D.w, D.mask, th, n_seg, D.dT, **kw)
+    S = oracle.gradient_scale(D.d, D.w, D.mask, th, n_seg, D.dT, tranche_level=True, **kw)
+    _, g = ctx_for(D).grad_statistic(th, n_seg)
+    c64 = ctx_for(D, path="fp64")
+
+    def fd5(p, h):
+        vals = []
+        for k in (2, 1, -1, -2):
+            t = th.copy()
+            t[p] += k * h
+            vals.append(c64.eval_statistic(t, n_seg)[0])
+        return (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * h)
+
+    checked = flipped = 0
+    for p in (0, 1, 2, 4, 5, 6, 7):
+        h = 1e-6 * np.maximum(np.abs(th[p]), 1.0)
+        fd, fd2 = fd5(p, h), fd5(p, 0.5 * h)
+        smooth = np.abs(fd - fd2) <= 1e-6 * S[p]
+        flipped += int((~smooth).sum())
+        e_ref = np.abs(fd - ref_g[p])[smooth]
+        assert np.all(e_ref <= 1e-5 * np.abs(ref_g[p][smooth]) + 2e-6 * S[p][smooth]), p
+        assert np.all(np.abs(g[p] - fd)[smooth] <= GRAD_TOL * S[p][smooth]), p
+        checked += int(smooth.sum())
+    assert checked >= 100 and flipped <= checked // 2, (checked, flipped)
 
 
 def test_gradient_per_template_is_independent_of_batch(ae45):

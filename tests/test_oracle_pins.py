@@ -441,6 +441,25 @@ def test_sky_and_polarisation_average_of_antenna_power():
 # Gradient
 # ---------------------------------------------------------------------------------------
 
+def test_gradient_term_scales(small_ae):
+    """The term scales that bound a finite-precision gradient: each is a sum of absolute
+    values whose signed sum is the gradient component (so it is at least |g|); both scale
+    like Upsilon under d -> c d; and a parameter that does not enter the template (psi,
+    lambda, beta, iota without a response) has scale zero."""
+    D = small_ae
+    th = synth.candidates_near(D.injections, 6, seed=3)
+    kw = dict(pn_order=PN_1PN, response=RESP_LW)
+    u, g = oracle.gradient(D.d, D.w, D.mask, th, 16, D.dT, **kw)
+    for tl in (False, True):
+        S = oracle.gradient_scale(D.d, D.w, D.mask, th, 16, D.dT, tranche_level=tl, **kw)
+        assert np.all(S >= np.abs(g) * (1 - 1e-12))
+        S3 = oracle.gradient_scale(3 * D.d, D.w, D.mask, th, 16, D.dT, tranche_level=tl, **kw)
+        np.testing.assert_allclose(S3, 9 * S, rtol=1e-10)
+    S0 = oracle.gradient_scale(D.d, D.w, D.mask, th, 16, D.dT, pn_order=PN_1PN, response=0,
+                               tranche_level=True)
+    assert np.all(S0[[4, 5, 6, 7]] == 0) and np.all(S0[[0, 2]] > 0)
+
+
 @pytest.mark.parametrize("resp", [RESP_LW, 2])
 def test_gradient_against_central_differences(small_ae, resp):
     D = small_ae
