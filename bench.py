@@ -9,11 +9,13 @@ isotropic sky, random psi, cos iota, phi_0), each evaluated at N_seg = 256, 64 a
 in one pass. All inputs are seeded synthetic data.
 
 One step = one eval_statistic call over the whole bank (set-up, length sort, the
-mixed-precision statistic kernel, output) with inputs resident in HBM; the L2 cache is
-flushed (a 256 MB write) between timed steps. The plain FP32 path (the paper's
-one-thread-per-template mapping) is timed on a subset of the same bank for the
-mixed-vs-plain ratio, and the FP64 CPU oracle on a bounded sample for the CPU
-baseline. `--impl reference` times the oracle itself as the reference arm.
+mixed-precision statistic kernel, output) with inputs resident in HBM, replayed as a
+CUDA graph; the L2 cache is flushed (a 256 MB write) between timed steps. The plain
+FP32 path (the paper's one-thread-per-template mapping) and the FP64 path are timed on
+prefixes of the same bank of at least a few full waves of their launches, and the
+mixed path with FP32 pixels on the whole bank, for the mixed-vs-plain ratios at the
+FP16 bound and at equal (1e-4) accuracy; the FP64 CPU oracle runs on a bounded sample
+for the CPU baseline. `--impl reference` times the oracle itself as the reference arm.
 
 Prints one JSON line (rank 0).
 """
@@ -61,8 +63,15 @@ def parse():
     p.add_argument("--n-templates", type=int, default=1_000_000)
     p.add_argument("--path", default="mixed", choices=["mixed", "plain", "fp64"])
     p.add_argument("--pixel", default="f16", choices=["f16", "bf16", "f32"])
-    p.add_argument("--plain-templates", type=int, default=20_000)
-    p.add_argument("--fp64-templates", type=int, default=5_000)
+    p.add_argument("--plain-waves", type=int, default=4,
+                   help="plain leg: at least this many full waves of its launch")
+    p.add_argument("--fp64-waves", type=int, default=1,
+                   help="FP64 leg: at least this many full waves of its launch")
+    p.add_argument("--leg-seconds", type=float, default=4.0,
+                   help="comparison legs: grow the batch (up to the whole bank) while a call "
+                        "is estimated to stay under this")
+    p.add_argument("--no-graph", action="store_true",
+                   help="headline step without CUDA-graph replay")
     p.add_argument("--cpu-sample", type=int, default=1200)  # ~10-20 s of oracle work
     p.add_argument("--ref-sample", type=int, default=48)    # per reference-arm step
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -177,6 +186,73 @@ def traffic_record(units):
     return rec
 
 
+def _timed_calls(ctx, th, reps, stream, flush):
+    """CUDA-event times [ms] of `reps` eval_statistic calls on device-resident theta."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.eval_statistic(th, N_SEG)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def _sized_leg(ctx, theta, waves, seconds, stream, flush, reps=2):
+    """Time the context's current path on a prefix of the bank: at least `waves` full
+    waves of its one-thread-per-template launch, grown towards the whole bank while one
+    call is estimated to stay under `seconds`. Returns the leg's record."""
+    n_all = theta.shape[1]
+    probe = theta[:, : min(n_all, 2048)].contiguous()
+    ctx.eval_statistic(probe, N_SEG)
+    shp = ctx.last_launch_shape()
+    per_wave = shp["ctas_per_sm"] * shp["sms"] * shp["threads_per_cta"]
+    n = min(n_all, waves * per_wave)
+    sub = theta[:, :n].contiguous()
+    ms = _timed_calls(ctx, sub, 1, stream, flush)  # also the untimed warm-up
+    rate = n / (ms[0] / 1000.0)
+    n_big = min(n_all, max(n, int(rate * seconds) // per_wave * per_wave))
+    if n_big > n:
+        n = n_big
+        sub = theta[:, :n].contiguous()
+    ms = _timed_calls(ctx, sub, reps, stream, flush)
+    shp = ctx.last_launch_shape()
+    return {"value": n / (statistics.mean(ms) / 1000.0), "unit": "templates/s",
+            "n_templates": n, "ms_per_step": statistics.mean(ms),
+            "launch": {"threads_per_cta": shp["threads_per_cta"], "ctas": shp["ctas"],
+                       "ctas_per_sm": shp["ctas_per_sm"],
+                       "warps_per_sm": shp["ctas_per_sm"] * shp["threads_per_cta"] // 32,
+                       "waves": shp["ctas"] / (shp["ctas_per_sm"] * shp["sms"])}}
+
+
+def comparison_legs(ctx, theta, args, stream, flush):
+    """The plain path (the paper's one-thread-per-template mapping, FP32 pixels, FP64
+    phase), the FP64 parity path, and the mixed path with FP32 pixels (the variant
+    that meets the plain path's 1e-4 bound) on the same bank and N_seg levels."""
+    out = {}
+    ctx.set_options(path="plain", profile=0, use_graph=0)
+    out["plain"] = dict(_sized_leg(ctx, theta, args.plain_waves, args.leg_seconds, stream, flush),
+                        dtype="f32 pixels, f64 phase")
+    ctx.set_options(path="fp64", profile=0, use_graph=0)
+    out["fp64"] = dict(_sized_leg(ctx, theta, args.fp64_waves, args.leg_seconds, stream, flush),
+                       dtype="f64")
+    ctx.set_options(path="mixed", pixel="f32", profile=0, use_graph=0)
+    ctx.eval_statistic(theta, N_SEG)  # autotune and pack the FP32 plane (untimed)
+    ms = _timed_calls(ctx, theta, 3, stream, flush)
+    shp = ctx.last_launch_shape()
+    out["mixed_f32"] = {"value": theta.shape[1] / (statistics.mean(ms) / 1000.0),
+                        "unit": "templates/s", "n_templates": theta.shape[1],
+                        "ms_per_step": statistics.mean(ms), "dtype": "f32 pixels",
+                        "launch": {"variant": shp["variant"],
+                                   "warps_per_cta": shp["threads_per_cta"] // 32,
+                                   "ctas_per_sm": shp["ctas_per_sm"]}}
+    return out
+
+
 def run_reference(args):
     """The oracle as the reference arm (FP64 CPU, all host cores)."""
     rank, world, _ = dist_env()
@@ -237,7 +313,8 @@ def main():
     theta_np = np.ascontiguousarray(synth.two_year_bank(n_total, seed=2002)[:, lo:hi])
     n = hi - lo
     theta = torch.from_numpy(theta_np).cuda()
-    ctx = TFS(local, path=args.path, pixel=args.pixel, profile=1)
+    use_graph = 0 if args.no_graph else 1
+    ctx = TFS(local, path=args.path, pixel=args.pixel, profile=1, use_graph=use_graph)
     ctx.load_tf_data(D.d, D.dt, D.dT)
     ctx.set_noise_weights(D.w, D.mask)
     stat = torch.empty((len(N_SEG), n), dtype=torch.float64, device="cuda")
@@ -249,6 +326,7 @@ def main():
     for _ in range(args.warmup):
         ctx.eval_statistic(theta, N_SEG, out=stat)
     torch.cuda.synchronize()
+    shape = ctx.last_launch_shape()
 
     def barrier():
         if world > 1:
@@ -312,6 +390,10 @@ def main():
                                "N_seg 256/64/16 in one pass)",
                    "n_templates_per_gpu": n, "n_seg": N_SEG, "path": args.path,
                    "pixel": args.pixel, "phase": "double-float", "l2": "flushed between steps",
+                   "graph": bool(use_graph and args.path == "mixed"),
+                   "launch": {"variant": shape["variant"], "warps_per_cta": shape["threads_per_cta"] // 32,
+                              "ctas": shape["ctas"], "ctas_per_sm": shape["ctas_per_sm"],
+                              "autotuner_trials": shape["tune_trials"]},
                    "parallelism": f"templates sharded, {world} GPU(s)"},
         "roofline": roof,
         "gpu_launches": launches,
@@ -321,41 +403,13 @@ def main():
         result["clocks_rejected_first_run"] = rejected
 
     if rank == 0 and not args.no_plain and args.path == "mixed":
-        ctx.set_options(path="plain", profile=1)
-        sub = theta[:, : args.plain_templates].contiguous()
-        ctx.eval_statistic(sub, N_SEG)
-        pms = []
-        for _ in range(2):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.eval_statistic(sub, N_SEG)
-            e1.record(stream)
-            e1.synchronize()
-            pms.append(e0.elapsed_time(e1))
-        pv = sub.shape[1] / (statistics.mean(pms) / 1000.0)
-        result["plain"] = {"value": pv, "unit": "templates/s", "n_templates": sub.shape[1],
-                           "ms_per_step": statistics.mean(pms), "dtype": "f32 pixels, f64 phase"}
-        result["mixed_vs_plain"] = (n / (statistics.mean(step_ms) / 1000.0)) / pv
-        # the FP64 parity path on a subset of the same bank
-        ctx.set_options(path="fp64", profile=1)
-        sub = theta[:, : args.fp64_templates].contiguous()
-        ctx.eval_statistic(sub, N_SEG)
-        fms = []
-        for _ in range(2):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.eval_statistic(sub, N_SEG)
-            e1.record(stream)
-            e1.synchronize()
-            fms.append(e0.elapsed_time(e1))
-        result["fp64"] = {"value": sub.shape[1] / (statistics.mean(fms) / 1000.0),
-                          "unit": "templates/s", "n_templates": sub.shape[1],
-                          "ms_per_step": statistics.mean(fms), "dtype": "f64"}
-        ctx.set_options(path=args.path, pixel=args.pixel, profile=1)
+        mixed_rate = n / (statistics.mean(step_ms) / 1000.0)
+        legs = comparison_legs(ctx, theta, args, stream, flush)
+        result.update(legs)
+        # FP16 pixels at their stated bound, and FP32 pixels at the plain path's 1e-4
+        result["mixed_vs_plain"] = mixed_rate / legs["plain"]["value"]
+        result["mixed_f32_vs_plain"] = legs["mixed_f32"]["value"] / legs["plain"]["value"]
+        ctx.set_options(path=args.path, pixel=args.pixel, profile=1, use_graph=use_graph)
 
     if rank == 0 and not args.no_e2e:
         ctx.set_options(path=args.path, pixel=args.pixel, profile=0)

@@ -46,8 +46,10 @@ def precision(args):
     D = synth.week_one_channel(seed=0)
     bank = synth.week_bank(1024, 0)
     ref = oracle.statistic(D.d, D.w, D.mask, bank, 8, D.dT)[0]
+    # the FP64 path carries the phase in FP64 (double-double), the mixed paths in
+    # double-float; f16all / bf16all hold u, w and the template values in 16 bits
     variants = [("fp64", "f32"), ("plain", "f32"), ("mixed", "f32"), ("mixed", "f16"),
-                ("mixed", "bf16")]
+                ("mixed", "bf16"), ("mixed", "f16all"), ("mixed", "bf16all")]
     errors = {}
     ctxs = {}
     for path, pix in variants:
@@ -218,13 +220,13 @@ def pso(args):
     def obj(th):
         evals[0] += th.shape[1]
         return c.eval_statistic(th, n_seg)[0]
-    # an untimed two-iteration swarm first (one-time kernel loading of the swarm's
-    # elementwise device work and of the statistic launch shape)
-    P.swarm(obj, lo, hi, n_particles=n_part, n_iter=2, seed=2006, device="cuda")
+    # an untimed two-iteration swarm first (one-time loading of the swarm kernels and
+    # of the statistic launch shape)
+    P.swarm(obj, lo, hi, n_particles=n_part, n_iter=2, seed=2006, tfs=c)
     evals[0] = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, fx = P.swarm(obj, lo, hi, n_particles=n_part, n_iter=n_iter, seed=2007, device="cuda")
+    x, fx = P.swarm(obj, lo, hi, n_particles=n_part, n_iter=n_iter, seed=2007, tfs=c)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     ratio = fx.cpu().numpy() / u_inj

@@ -72,15 +72,20 @@ typedef enum tfs_path {
 } tfs_path;
 
 typedef enum tfs_pixel {
-  TFS_PIX_F32 = 0,
-  TFS_PIX_F16 = 1,
-  TFS_PIX_BF16 = 2
+  TFS_PIX_F32 = 0,      /* u = d~/S and w = 1/S in FP32 */
+  TFS_PIX_F16 = 1,      /* u in FP16, w in FP32 */
+  TFS_PIX_BF16 = 2,     /* u in BF16, w in FP32 */
+  TFS_PIX_F16_ALL = 3,  /* u and w in FP16, and the template's per-bin kernel values and
+                           per-tranche prefactor (response x amplitude x phase factor)
+                           rounded to FP16 before the products; FP32 accumulation */
+  TFS_PIX_BF16_ALL = 4  /* u and w in BF16, template values rounded to FP16 as above */
 } tfs_pixel;
 
 typedef struct tfs_options {
   int path;          /* tfs_path used by tfs_eval_statistic (default MIXED) */
-  int pixel;         /* tfs_pixel: storage of d~/S for the mixed path (default F16); 1/S is
-                        held in FP32 with every pixel type */
+  int pixel;         /* tfs_pixel: storage of d~/S and 1/S for the mixed path (default F16);
+                        the _ALL types (precision studies) also round the template values to
+                        FP16 and are not available with harmonics */
   int pn_order;      /* 0 Newtonian chirp, 1 1PN TaylorT3 (default 1) */
   int response;      /* 0 none (T = 1, t' = t), 1 long-wavelength A/E (default 1),
                         2 TDI-1.5 A/E */
@@ -173,8 +178,9 @@ int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t
 int tfs_set_harmonics(tfs_ctx* ctx, int n_harm, const double* nu, const double* c_re,
                       const double* c_im);
 
-/* Indices of the k largest values of stat[n] (ties broken by the lower index), in
- * decreasing order of stat, into out_index int64 [k]: the survivors of one stage of
+/* Indices of the k largest values of stat[n] (ties broken by the lower index; -0.0
+ * equals +0.0; NaN ranks below every number), in decreasing order of stat, into
+ * out_index int64 [k]: the survivors of one stage of
  * the adaptive N_seg ladder (Sec. "Time-frequency search statistic": N_seg is reduced
  * as the search progresses). stat and out_index may be host or device pointers. */
 int tfs_select_top(tfs_ctx* ctx, const double* stat, int64_t n, int64_t k, int64_t* out_index,
@@ -192,7 +198,9 @@ int tfs_select_top(tfs_ctx* ctx, const double* stat, int64_t n, int64_t k, int64
  *   device; n > 65536, host pointers or k outside [0, n] return TFS_ERR_ARG; a CUDA
  *   failure returns TFS_ERR_CUDA (no message: there is no context).
  * The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture. Every
+ * with that device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call this function again on a device
+ * after cudaDeviceReset there (the kept address belongs to the destroyed context). Every
  * call reuses the same array and overwrites every byte it reads, so nothing carries
  * over from the previous call, but calls whose GPU work overlaps (two streams, or two
  * host threads on one device) race on it: serialise them. Asynchronous on `stream`. */
@@ -206,10 +214,80 @@ int tfs_select_top_noalloc(const double* stat, int64_t n, int64_t k, int64_t* ou
 int tfs_ascent_step(tfs_ctx* ctx, double* theta, const double* grad, int64_t n,
                     const double* step, const double* lo, const double* hi, void* stream);
 
+/* Particle-swarm maximisation of Upsilon over parameter tiles: the paper searches
+ * each tile of its (M_c, f_in) grid with a particle swarm (Sec. "Implementation
+ * details"). S swarms of P particles run together; the caller evaluates Upsilon for
+ * all S*P positions (one tfs_eval_statistic call on x) between steps. Global-best swarm
+ * with an inertia weight: per particle and coordinate
+ *   v <- inertia v + c1 r1 (pbest - x) + c2 r2 (gbest - x),   x <- x + v,
+ * r1, r2 uniform in [0, 1), drawn from Philox4x32-10 keyed by `seed` with counter
+ * (particle, coordinate, step): the run is a deterministic function of the seed.
+ * For an angle whose tile spans its whole period (phi_0, lambda: 2 pi; psi: pi) the
+ * differences take the shorter way round and x wraps into [0, period); every other
+ * coordinate is clipped to the tile, which zeroes its velocity; a coordinate whose
+ * tile has zero width stays fixed.
+ *   n_swarm S >= 1, n_part P >= 1 (S P < 2^31); lo, hi: double [S][8] tile corners,
+ *   host or device, read at each call; x, v, pbest: double [8][S*P] (SoA: particle i
+ *   of swarm s at column s*P + i, the layout tfs_eval_statistic takes); pval double
+ *   [S*P]; gbest double [8][S]; gval double [S]. All state arrays are device memory of
+ *   the context's device, owned by the caller (TFS_ERR_ARG otherwise). */
+typedef struct tfs_swarm {
+  int n_swarm, n_part;
+  const double *lo, *hi;
+  double inertia, c1, c2;
+  uint64_t seed;
+  double *x, *v, *pbest, *pval, *gbest, *gval;
+} tfs_swarm;
+
+/* Initial swarm: x uniform in the tile, v uniform in +-0.1 of the tile width,
+ * pbest = x, pval = gval = -inf, gbest at the tile centre. Asynchronous on `stream`. */
+int tfs_pso_init(tfs_ctx* ctx, const tfs_swarm* sw, void* stream);
+
+/* One swarm step with f = double [S*P] (device) the objective at the current x:
+ * personal bests where f > pval; each swarm's best replaced by its largest pval (the
+ * lowest particle index among equals) where that is larger; then, if `move` is
+ * non-zero, the velocity and position update above with the draws of step `iter`
+ * (>= 0). history: null, or device double [>= iter + 1][S] whose row `iter` receives
+ * gval after the update. Asynchronous on `stream`. */
+int tfs_pso_step(tfs_ctx* ctx, const tfs_swarm* sw, const double* f, int64_t iter, int move,
+                 double* history, void* stream);
+
+/* Batched gradient-ascent refinement of n candidates (the gradient of Eq. Upsilon-seg
+ * from tfs_grad_statistic drives the step). State, all device memory of the context's
+ * device, owned by the caller: theta double [8][n] (the point just evaluated; replaced
+ * by the next point), best_theta, best_grad double [8][n], best_stat double [n] (start
+ * at -inf), eta double [n] (step lengths in units of sigma), sigma double [8][n]
+ * (per-candidate parameter scales, 0 freezes a parameter); lo, hi: bounds of the
+ * clamped parameters (M_c, eta, f_0, beta, iota; phi_0 and lambda wrap to [0, 2 pi),
+ * psi to [0, pi)); eta_up, eta_down > 0. */
+typedef struct tfs_refine {
+  int64_t n;
+  double *theta, *best_theta, *best_grad, *best_stat, *eta;
+  const double* sigma;
+  double lo[8], hi[8];
+  double eta_up, eta_down;
+} tfs_refine;
+
+/* One refinement step from U = stat [n] and dU/dtheta = grad [8][n] (device) at theta:
+ * where U >= best_stat the candidate accepts (best_* take the current values and eta
+ * is multiplied by eta_up), else it rejects (eta *= eta_down); then
+ *   theta = project(best_theta + eta sigma (sigma best_grad) / |sigma best_grad|).
+ * mean_best: null, or a device double that receives the mean of best_stat (summed in a
+ * fixed order). Asynchronous on `stream`. */
+int tfs_refine_step(tfs_ctx* ctx, const tfs_refine* rf, const double* stat, const double* grad,
+                    double* mean_best, void* stream);
+
 /* Per-kernel GPU times [ms] of the last tfs_eval_statistic / tfs_grad_statistic call
  * made with options.profile = 1: ms[0] set-up, ms[1] sort, ms[2] statistic kernel,
  * ms[3] output fold/copy. Returns TFS_ERR_STATE if nothing was profiled. */
 int tfs_last_profile(const tfs_ctx* ctx, double ms[4]);
+
+/* Shape of the statistic kernel launch of the last tfs_eval_statistic call:
+ * out[0] the compiled tile/schedule variant of the mixed kernel that the autotuner
+ * picked (0 on the other paths), out[1] threads per CTA, out[2] CTAs launched, out[3]
+ * CTAs resident per SM, out[4] SMs of the device, out[5] autotuner trials timed so far
+ * by this context. TFS_ERR_STATE before the first evaluation. */
+int tfs_last_launch_shape(const tfs_ctx* ctx, int32_t out[6]);
 
 /* Kernel launches issued by the last call (for launch accounting). */
 int64_t tfs_last_launch_count(const tfs_ctx* ctx);

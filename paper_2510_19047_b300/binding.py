@@ -17,8 +17,9 @@ import numpy as np
 from . import build as _build
 
 PATH_FP64, PATH_PLAIN, PATH_MIXED = 0, 1, 2
-PIX_F32, PIX_F16, PIX_BF16 = 0, 1, 2
-_PIX_NAMES = {"f32": PIX_F32, "f16": PIX_F16, "bf16": PIX_BF16}
+PIX_F32, PIX_F16, PIX_BF16, PIX_F16_ALL, PIX_BF16_ALL = 0, 1, 2, 3, 4
+_PIX_NAMES = {"f32": PIX_F32, "f16": PIX_F16, "bf16": PIX_BF16, "f16all": PIX_F16_ALL,
+              "bf16all": PIX_BF16_ALL}
 _PATH_NAMES = {"fp64": PATH_FP64, "plain": PATH_PLAIN, "mixed": PATH_MIXED}
 
 _ERRORS = {
@@ -38,6 +39,26 @@ class Options(ctypes.Structure):
                 ("response", ctypes.c_int), ("checked", ctypes.c_int), ("sort", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("max_device_bytes", ctypes.c_int64)]
+
+
+class Swarm(ctypes.Structure):
+    """tfs_swarm (include/tfs.h)."""
+    _fields_ = [("n_swarm", ctypes.c_int), ("n_part", ctypes.c_int),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
+                ("inertia", ctypes.c_double), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("seed", ctypes.c_uint64),
+                ("x", ctypes.c_void_p), ("v", ctypes.c_void_p), ("pbest", ctypes.c_void_p),
+                ("pval", ctypes.c_void_p), ("gbest", ctypes.c_void_p), ("gval", ctypes.c_void_p)]
+
+
+class Refine(ctypes.Structure):
+    """tfs_refine (include/tfs.h)."""
+    _fields_ = [("n", ctypes.c_int64),
+                ("theta", ctypes.c_void_p), ("best_theta", ctypes.c_void_p),
+                ("best_grad", ctypes.c_void_p), ("best_stat", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("lo", ctypes.c_double * 8), ("hi", ctypes.c_double * 8),
+                ("eta_up", ctypes.c_double), ("eta_down", ctypes.c_double)]
 
 
 _lib = None
@@ -77,8 +98,12 @@ def load_library(build_if_missing=True):
         "tfs_grad_statistic": (i32, [P, P, i64, ctypes.c_int32, P, P, P]),
         "tfs_select_top": (i32, [P, P, i64, i64, P, P]),
         "tfs_ascent_step": (i32, [P, P, P, i64, P, P, P, P]),
+        "tfs_pso_init": (i32, [P, ctypes.POINTER(Swarm), P]),
+        "tfs_pso_step": (i32, [P, ctypes.POINTER(Swarm), P, i64, i32, P, P]),
+        "tfs_refine_step": (i32, [P, ctypes.POINTER(Refine), P, P, P, P]),
         "tfs_last_profile": (i32, [P, ctypes.POINTER(ctypes.c_double)]),
         "tfs_last_launch_count": (i64, [P]),
+        "tfs_last_launch_shape": (i32, [P, P]),
         "tfs_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -322,6 +347,23 @@ class TFS:
                                              _ptr(hi_)[0], self._stream(theta)))
         return theta
 
+    # -- search steps (device state only) -------------------------------------------------
+    def pso_init(self, sw, stream_of):
+        """tfs_pso_init on a Swarm whose arrays live on this context's device."""
+        self._check(self.lib.tfs_pso_init(self.h, ctypes.byref(sw), self._stream(stream_of)))
+
+    def pso_step(self, sw, f, it, move, history=None):
+        """tfs_pso_step with the objective f [S*P] (device tensor) at the positions."""
+        ph, _ = _ptr(history)
+        self._check(self.lib.tfs_pso_step(self.h, ctypes.byref(sw), _ptr(f)[0], int(it),
+                                          int(bool(move)), ph, self._stream(f)))
+
+    def refine_step(self, rf, stat, grad, mean_out=None):
+        """tfs_refine_step from stat [n] and grad [8, n] (device tensors)."""
+        pm, _ = _ptr(mean_out)
+        self._check(self.lib.tfs_refine_step(self.h, ctypes.byref(rf), _ptr(stat)[0],
+                                             _ptr(grad)[0], pm, self._stream(stat)))
+
     # -- accounting -----------------------------------------------------------------------
     def last_profile(self):
         ms = (ctypes.c_double * 4)()
@@ -330,3 +372,10 @@ class TFS:
 
     def last_launch_count(self):
         return int(self.lib.tfs_last_launch_count(self.h))
+
+    def last_launch_shape(self):
+        """Shape of the last statistic launch (see tfs_last_launch_shape)."""
+        out = np.zeros(6, np.int32)
+        self._check(self.lib.tfs_last_launch_shape(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        keys = ("variant", "threads_per_cta", "ctas", "ctas_per_sm", "sms", "tune_trials")
+        return dict(zip(keys, (int(x) for x in out)))

@@ -29,6 +29,11 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// The shape of a mixed launch: compiled variant, warps per CTA, CTAs, CTAs per SM.
+struct MixedShape {
+  int variant = 0, warps = 8, ctas = 1, per_sm = 1;
+};
+
 }  // namespace
 
 struct tfs_ctx {
@@ -53,6 +58,10 @@ struct tfs_ctx {
   double su = 1.0, sw = 1.0;
   // per-call scratch
   DevBuf theta, tpl, tplm, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
+  // search steps: tile corners of the swarms, partial sums and block counter of the
+  // refinement step's mean
+  DevBuf tile_lo, tile_hi, rpart, rdone;
+  DevBuf tune_perm;  // the autotuner's strided sample of the queue
   // harmonic content of the templates (n = 0: the dominant mode) and its per-template
   // constant phases (mixed path)
   HarmSet harm{};
@@ -63,8 +72,11 @@ struct tfs_ctx {
   bool prof_valid = false;
   int mixed_warps = 0;
   // autotuned mixed launch shapes: (n_chan, pixel, fine_cap, per_template, response) ->
-  // (warps, ctas)
-  std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> tuned;
+  // (variant, warps, CTAs per SM); trials timed so far
+  std::map<std::tuple<int, int, int, int, int>, MixedShape> tuned;
+  int64_t tune_trials = 0;
+  // shape of the last statistic launch: variant, threads per CTA, CTAs, CTAs per SM, SMs
+  int shape[5] = {0, 0, 0, 0, 0};
   // CUDA graph of the mixed evaluation, replayed while its key is unchanged
   cudaStream_t cstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -197,13 +209,34 @@ int make_levels(tfs_ctx* c, const int32_t* n_seg, int n_levels, Levels* lv) {
 }
 
 void prof_record(tfs_ctx* c, int i, cudaStream_t s) {
-  if (c->opt.profile) cudaEventRecord(c->ev[i], s);
+  if (!c->opt.profile) return;
+  // inside a stream capture the record becomes an external event node, which records
+  // the event each time the graph runs (so that the kernel times stay measurable)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+  const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                             : cudaEventRecordDefault;
+  if (cudaEventRecordWithFlags(c->ev[i], s, flags) != cudaSuccess) cudaGetLastError();
+}
+
+// Per-kernel times of the call just synchronised; a failed query leaves the profile
+// invalid and clears its error, so that no later launch check reports it.
+void read_profile(tfs_ctx* c) {
+  c->prof_valid = true;
+  for (int i = 0; i < 4; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      c->prof_valid = false;
+    }
+    c->prof[i] = ms;
+  }
 }
 
 
 // The launches of one mixed evaluation after the per-template set-up: optional
 // length/frequency sort, counter reset, persistent statistic kernel.
-int issue_mixed(tfs_ctx* c, EvalArgs& a, int64_t n_tpl, int warps, int ctas, cudaStream_t s) {
+int issue_mixed(tfs_ctx* c, EvalArgs& a, int64_t n_tpl, const MixedShape& sh, cudaStream_t s) {
   if (c->opt.sort) {
     int nl = 0;
     CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
@@ -215,66 +248,90 @@ int issue_mixed(tfs_ctx* c, EvalArgs& a, int64_t n_tpl, int warps, int ctas, cud
   }
   prof_record(c, 2, s);
   CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
-  CUDA_TRY(c, launch_eval_mixed(a, c->g.n_chan, c->opt.pixel, warps, ctas, s));
+  CUDA_TRY(c, launch_eval_mixed(a, c->g.n_chan, c->opt.pixel, sh.variant, sh.warps, sh.ctas, s));
   c->launches += 1;
   return TFS_OK;
 }
 
-// Launch shape of the mixed kernel: the options' warps per CTA if set, otherwise the
-// fastest of {4, 8} warps x {full, full - 1} CTAs per SM, timed once per
-// (channels, pixel type, segment slots, per-template mode) on up to 24576 templates of
-// the current (already sorted) queue.
+// Launch shape of the mixed kernel. With options.warps_per_cta set: that CTA size,
+// variant 0, as many CTAs as fit. Otherwise the autotuner's pick, timed once per
+// (channels, pixel type, segment slots, per-template mode, response) on 24576 templates
+// taken at a fixed stride from the current (already sorted) queue: every compiled tile/schedule
+// variant (bin unroll, pixel-load lead, register target) x {4, 8} warps per CTA x
+// {full, full - 1} CTAs per SM, the fastest of two runs each.
 int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_template,
-                cudaStream_t s, int* warps_out, int* ctas_out) {
+                cudaStream_t s, MixedShape* out) {
   const int n_chan = c->g.n_chan, pix = c->opt.pixel;
-  auto shape_for = [&](int warps, int per_sm, int* ctas) {
+  auto ctas_for = [&](int warps, int per_sm) {
     const int64_t need = (n_tpl + warps - 1) / warps;
-    *ctas = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->n_sm * per_sm, need));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->n_sm * per_sm, need));
   };
   if (c->opt.warps_per_cta) {
     int per_sm = 0;
-    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, c->opt.warps_per_cta, fine_cap, &per_sm));
+    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, 0, c->opt.warps_per_cta,
+                                fine_cap, &per_sm));
     if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
-    *warps_out = c->opt.warps_per_cta;
-    shape_for(*warps_out, per_sm, ctas_out);
+    out->variant = 0;
+    out->warps = c->opt.warps_per_cta;
+    out->per_sm = per_sm;
+    out->ctas = ctas_for(out->warps, per_sm);
     return TFS_OK;
   }
   const auto key = std::make_tuple(n_chan, pix, fine_cap, per_template, c->opt.response);
   auto it = c->tuned.find(key);
   if (it == c->tuned.end()) {
-    a.n_work = std::min<int64_t>(n_tpl, 24576);
+    // trial batch: every stride-th entry of the (longest-first) queue, so that it spans
+    // the batch's whole range of track lengths
+    const int64_t cnt = std::min<int64_t>(n_tpl, 24576);
+    a.n_work = cnt;
+    if (a.perm && cnt < n_tpl) {
+      const int64_t stride = n_tpl / cnt;
+      int r;
+      if ((r = buf_ensure(c, c->tune_perm, (size_t)cnt * 4))) return r;
+      CUDA_TRY(c, cudaMemcpy2DAsync(c->tune_perm.p, 4, a.perm, (size_t)stride * 4, 4, (size_t)cnt,
+                                    cudaMemcpyDeviceToDevice, s));
+      a.perm = (const int32_t*)c->tune_perm.p;
+    }
     float best = 1e30f;
-    std::pair<int, int> pick{8, 1};
+    MixedShape pick;
     cudaEvent_t e0 = c->ev[0], e1 = c->ev[1];
-    for (int warps : {4, 8}) {
-      int occ = 0;
-      CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, warps, fine_cap, &occ));
-      for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
-        int ctas;
-        shape_for(warps, per_sm, &ctas);
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-          CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
-          CUDA_TRY(c, cudaEventRecord(e0, s));
-          CUDA_TRY(c, launch_eval_mixed(a, n_chan, pix, warps, ctas, s));
-          CUDA_TRY(c, cudaEventRecord(e1, s));
-          CUDA_TRY(c, cudaEventSynchronize(e1));
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          ms = std::min(ms, t);
-        }
-        if (ms < best) {
-          best = ms;
-          pick = {warps, per_sm};
+    const int nv = mixed_variants(n_chan, c->pitch);
+    for (int v = 0; v < nv; ++v) {
+      for (int warps : {4, 8}) {
+        int occ = 0;
+        CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, v, warps, fine_cap, &occ));
+        for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
+          const int ctas = ctas_for(warps, per_sm);
+          float ms = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
+            CUDA_TRY(c, cudaEventRecord(e0, s));
+            CUDA_TRY(c, launch_eval_mixed(a, n_chan, pix, v, warps, ctas, s));
+            CUDA_TRY(c, cudaEventRecord(e1, s));
+            CUDA_TRY(c, cudaEventSynchronize(e1));
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+          }
+          c->tune_trials++;
+          if (ms < best) {
+            best = ms;
+            pick.variant = v;
+            pick.warps = warps;
+            pick.per_sm = per_sm;
+          }
         }
       }
     }
     it = c->tuned.emplace(key, pick).first;
   }
   int occ = 0;
-  CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, it->second.first, fine_cap, &occ));
-  *warps_out = it->second.first;
-  shape_for(*warps_out, std::min(occ, it->second.second), ctas_out);
+  const MixedShape& t = it->second;
+  CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, t.variant, t.warps, fine_cap, &occ));
+  out->variant = t.variant;
+  out->warps = t.warps;
+  out->per_sm = std::min(occ, t.per_sm);
+  out->ctas = ctas_for(t.warps, out->per_sm);
   return TFS_OK;
 }
 
@@ -301,7 +358,7 @@ void tfs_default_options(tfs_options* o) {
 
 static int check_options(tfs_ctx* c, const tfs_options* o) {
   if (o->path < 0 || o->path > 2) return fail(c, TFS_ERR_ARG, "options.path must be 0, 1 or 2");
-  if (o->pixel < 0 || o->pixel > 2) return fail(c, TFS_ERR_ARG, "options.pixel must be 0, 1 or 2");
+  if (o->pixel < 0 || o->pixel > 4) return fail(c, TFS_ERR_ARG, "options.pixel must be 0 .. 4");
   if (o->pn_order < 0 || o->pn_order > 1) return fail(c, TFS_ERR_ARG, "options.pn_order must be 0 or 1");
   if (o->response < 0 || o->response > 2)
     return fail(c, TFS_ERR_ARG, "options.response must be 0, 1 or 2");
@@ -352,7 +409,7 @@ int tfs_destroy(tfs_ctx* c) {
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
                    &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart,
-                   &c->harmK};
+                   &c->harmK, &c->tile_lo, &c->tile_hi, &c->rpart, &c->rdone, &c->tune_perm};
   for (DevBuf* b : all) buf_free(c, *b);
   for (int i = 0; i < 5; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -677,6 +734,8 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     if (herr) return fail(c, TFS_ERR_DEVICE_CHECK, "a template's tranche range lies outside the grid");
   }
 
+  if (path == TFS_PATH_MIXED && harm && c->opt.pixel > TFS_PIX_BF16)
+    return fail(c, TFS_ERR_ARG, "the precision-study pixel types (3, 4) are not available with harmonics");
   if (path == TFS_PATH_MIXED && harm) {
     // multi-harmonic mixed launch: set-up, constant phases per harmonic, sort, kernel
     if ((r = buf_ensure(c, c->harmK, (size_t)n_tpl * c->harm.n * sizeof(float2)))) return r;
@@ -693,14 +752,21 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     }
     prof_record(c, 2, s);
     CUDA_TRY(c, cudaMemsetAsync(c->counter.p, 0, 16, s));
-    CUDA_TRY(c, launch_eval_harm(a, g.n_chan, c->opt.pixel, c->n_sm, s));
+    int hs[3] = {0, 0, 0};
+    CUDA_TRY(c, launch_eval_harm(a, g.n_chan, c->opt.pixel, c->n_sm, s, hs));
     c->launches += 1;
+    c->shape[0] = 0;
+    c->shape[1] = hs[0];
+    c->shape[2] = hs[1];
+    c->shape[3] = hs[2];
   } else if (path == TFS_PATH_MIXED) {
-    if (!c->opt.checked && (r = setup(s))) return r;
-    int warps = 8, ctas = 1;
+    MixedShape sh;
     const bool must_time = !c->opt.warps_per_cta &&
                            !c->tuned.count(std::make_tuple(g.n_chan, c->opt.pixel, fine_cap, per_template,
                                                            c->opt.response));
+    // the direct launch needs the set-up first; a graph replays its own set-up, so it
+    // runs eagerly only when the autotuner times the kernel on this batch
+    if (!c->opt.checked && (!graph || must_time) && (r = setup(s))) return r;
     if (c->opt.sort && must_time) {
       // the autotuner times the sorted queue, so sort once before choosing
       EvalArgs t = a;
@@ -708,16 +774,20 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
       CUDA_TRY(c, sort_templates((const TplConst*)c->tpl.p, n_tpl, (int32_t*)c->perm.p, c->sortbuf.p,
                                  c->n_sm, s, &nl));
       t.perm = (const int32_t*)c->perm.p;
-      if ((r = mixed_shape(c, t, n_tpl, fine_cap, per_template, s, &warps, &ctas))) return r;
-    } else if ((r = mixed_shape(c, a, n_tpl, fine_cap, per_template, s, &warps, &ctas))) {
+      if ((r = mixed_shape(c, t, n_tpl, fine_cap, per_template, s, &sh))) return r;
+    } else if ((r = mixed_shape(c, a, n_tpl, fine_cap, per_template, s, &sh))) {
       return r;
     }
+    c->shape[0] = sh.variant;
+    c->shape[1] = sh.warps * 32;
+    c->shape[2] = sh.ctas;
+    c->shape[3] = sh.per_sm;
     c->launches = 0;
     if (!graph) {
       c->launches = 1;  // set-up
-      if ((r = issue_mixed(c, a, n_tpl, warps, ctas, s))) return r;
+      if ((r = issue_mixed(c, a, n_tpl, sh, s))) return r;
     } else {
-      std::vector<long long> key = {n_tpl, n_levels, per_template, fine_cap, warps, ctas,
+      std::vector<long long> key = {n_tpl, n_levels, per_template, fine_cap, sh.variant, sh.warps, sh.ctas,
                                     c->opt.pixel, c->opt.sort, c->opt.profile, c->opt.pn_order,
                                     c->opt.response, (long long)th, (long long)o_stat,
                                     (long long)o_neff, (long long)o_diag, (long long)c->tpl.p,
@@ -733,7 +803,7 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
         cudaGraph_t gr = nullptr;
         CUDA_TRY(c, cudaStreamBeginCapture(c->cstream, cudaStreamCaptureModeThreadLocal));
         int rr = setup(c->cstream);
-        if (!rr) rr = issue_mixed(c, a, n_tpl, warps, ctas, c->cstream);
+        if (!rr) rr = issue_mixed(c, a, n_tpl, sh, c->cstream);
         prof_record(c, 3, c->cstream);
         const cudaError_t ce = cudaStreamEndCapture(c->cstream, &gr);
         if (rr) {
@@ -755,6 +825,12 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
     prof_record(c, 2, s);
     CUDA_TRY(c, path == TFS_PATH_PLAIN ? launch_eval_plain(a, s) : launch_eval_fp64(a, s));
     c->launches += 1;
+    int per_sm = 0;
+    CUDA_TRY(c, ref_occupancy(a, path, &per_sm));
+    c->shape[0] = 0;
+    c->shape[1] = 128;
+    c->shape[2] = (int)((n_tpl + 127) / 128);
+    c->shape[3] = per_sm;
   }
   if (!graph) prof_record(c, 3, s);
   if (!dev_stat)
@@ -770,14 +846,7 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   const bool host_out = !is_device_ptr(out_stat) || (out_neff && !is_device_ptr(out_neff)) ||
                         (out_diag && !is_device_ptr(out_diag));
   if (host_out || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (c->opt.profile) {
-    float ms;
-    for (int i = 0; i < 4; ++i) {
-      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
-      c->prof[i] = ms;
-    }
-    c->prof_valid = true;
-  }
+  if (c->opt.profile) read_profile(c);
   return TFS_OK;
 }
 
@@ -792,6 +861,7 @@ int tfs_eval_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, const int
   if (n_tpl > 0 && (!theta || !out_stat))
     return fail(c, TFS_ERR_ARG, "theta and out_stat must not be null");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaGetLastError();  // a launch check below must not report an earlier, unrelated error
   return eval_impl(c, theta, n_tpl, n_seg, n_levels, per_template, out_stat, out_neff, out_diag,
                    (cudaStream_t)stream);
 }
@@ -802,6 +872,15 @@ int tfs_eval_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, const int
 // Ladder selection and gradient-ascent step
 // ---------------------------------------------------------------------------------
 extern "C" {
+
+int tfs_last_launch_shape(const tfs_ctx* c, int32_t out[6]) {
+  if (!c || !out) return TFS_ERR_ARG;
+  if (!c->shape[1]) return TFS_ERR_STATE;
+  for (int i = 0; i < 4; ++i) out[i] = c->shape[i];
+  out[4] = c->n_sm;
+  out[5] = (int32_t)std::min<int64_t>(c->tune_trials, INT32_MAX);
+  return TFS_OK;
+}
 
 int tfs_select_top(tfs_ctx* c, const double* stat, int64_t n, int64_t k, int64_t* out_index,
                    void* stream) {
@@ -885,6 +964,7 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   if (n_tpl == 0) return TFS_OK;
   if (!theta || !out_stat || !out_grad) return fail(c, TFS_ERR_ARG, "null argument");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaGetLastError();  // a launch check below must not report an earlier, unrelated error
   cudaStream_t s = (cudaStream_t)stream;
   int r;
   const void* th = nullptr;
@@ -951,14 +1031,153 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));
   prof_record(c, 4, s);
   if (!dev_stat || !dev_grad || c->opt.profile) CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (c->opt.profile) {
-    float ms;
-    for (int i = 0; i < 4; ++i) {
-      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
-      c->prof[i] = ms;
-    }
-    c->prof_valid = true;
+  if (c->opt.profile) read_profile(c);
+  return TFS_OK;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Search steps: particle swarm and refinement bookkeeping
+// ---------------------------------------------------------------------------------
+namespace {
+
+// Device pointer of the context's device (the search-step calls take device state only).
+bool on_ctx_device(const tfs_ctx* c, const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+         at.device == c->device;
+}
+
+int pso_args(tfs_ctx* c, const tfs_swarm* sw, cudaStream_t s, PsoArgs* a) {
+  if (!sw) return fail(c, TFS_ERR_ARG, "null swarm");
+  if (sw->n_swarm < 1 || sw->n_part < 1 || (int64_t)sw->n_swarm * sw->n_part > INT32_MAX)
+    return fail(c, TFS_ERR_ARG, "need n_swarm >= 1, n_part >= 1, n_swarm * n_part < 2^31");
+  if (!sw->lo || !sw->hi) return fail(c, TFS_ERR_ARG, "null tile corners");
+  double* st[6] = {sw->x, sw->v, sw->pbest, sw->pval, sw->gbest, sw->gval};
+  for (double* p : st)
+    if (!on_ctx_device(c, p))
+      return fail(c, TFS_ERR_ARG, "swarm state must be device memory of the context's device");
+  if (!(std::isfinite(sw->inertia) && std::isfinite(sw->c1) && std::isfinite(sw->c2)))
+    return fail(c, TFS_ERR_ARG, "inertia, c1, c2 must be finite");
+  const size_t nb = (size_t)sw->n_swarm * 8 * sizeof(double);
+  int r;
+  const void *lo = nullptr, *hi = nullptr;
+  if ((r = device_view(c, sw->lo, nb, c->tile_lo, s, &lo))) return r;
+  if ((r = device_view(c, sw->hi, nb, c->tile_hi, s, &hi))) return r;
+  a->n_swarm = sw->n_swarm;
+  a->n_part = sw->n_part;
+  a->x = sw->x;
+  a->v = sw->v;
+  a->pbest = sw->pbest;
+  a->pval = sw->pval;
+  a->gbest = sw->gbest;
+  a->gval = sw->gval;
+  a->lo = (const double*)lo;
+  a->hi = (const double*)hi;
+  a->inertia = sw->inertia;
+  a->c1 = sw->c1;
+  a->c2 = sw->c2;
+  a->key = make_uint2((uint32_t)sw->seed, (uint32_t)(sw->seed >> 32));
+  a->history = nullptr;
+  return TFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tfs_pso_init(tfs_ctx* c, const tfs_swarm* sw, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  PsoArgs a;
+  int r = pso_args(c, sw, s, &a);
+  if (r) return r;
+  c->launches = 0;
+  CUDA_TRY(c, launch_pso_init(a, c->n_sm, s));
+  c->launches = 1;
+  return TFS_OK;
+}
+
+int tfs_pso_step(tfs_ctx* c, const tfs_swarm* sw, const double* f, int64_t iter, int move,
+                 double* history, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (iter < 0) return fail(c, TFS_ERR_ARG, "iter must be >= 0");
+  if (!on_ctx_device(c, f)) return fail(c, TFS_ERR_ARG, "f must be device memory of the context's device");
+  if (history && !on_ctx_device(c, history))
+    return fail(c, TFS_ERR_ARG, "history must be null or device memory of the context's device");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  PsoArgs a;
+  int r = pso_args(c, sw, s, &a);
+  if (r) return r;
+  a.history = history;
+  c->launches = 0;
+  CUDA_TRY(c, launch_pso_step(a, f, iter, move ? 1 : 0, s));
+  c->launches = 1;
+  return TFS_OK;
+}
+
+int tfs_refine_step(tfs_ctx* c, const tfs_refine* rf, const double* stat, const double* grad,
+                    double* mean_best, void* stream) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (!rf) return fail(c, TFS_ERR_ARG, "null refinement state");
+  if (rf->n < 0) return fail(c, TFS_ERR_ARG, "n must be >= 0");
+  if (rf->n == 0) return TFS_OK;
+  const void* ptrs[9] = {stat, grad, rf->theta, rf->best_theta, rf->best_grad, rf->best_stat,
+                         rf->eta, rf->sigma, nullptr};
+  for (int i = 0; i < 8; ++i)
+    if (!on_ctx_device(c, ptrs[i]))
+      return fail(c, TFS_ERR_ARG, "refinement arrays must be device memory of the context's device");
+  if (mean_best && !on_ctx_device(c, mean_best))
+    return fail(c, TFS_ERR_ARG, "mean_best must be null or device memory of the context's device");
+  if (!(rf->eta_up > 0.0) || !(rf->eta_down > 0.0))
+    return fail(c, TFS_ERR_ARG, "eta_up and eta_down must be > 0");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, TFS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  RefineArgs a;
+  a.n = rf->n;
+  a.stat = stat;
+  a.grad = grad;
+  a.theta = rf->theta;
+  a.best_theta = rf->best_theta;
+  a.best_grad = rf->best_grad;
+  a.best_stat = rf->best_stat;
+  a.eta = rf->eta;
+  a.sigma = rf->sigma;
+  for (int q = 0; q < 8; ++q) {
+    a.lo[q] = rf->lo[q];
+    a.hi[q] = rf->hi[q];
+  }
+  a.eta_up = rf->eta_up;
+  a.eta_down = rf->eta_down;
+  a.mean_out = mean_best;
+  a.part = nullptr;
+  a.done = nullptr;
+  int r;
+  if (mean_best) {
+    const int64_t blocks = (rf->n + 255) / 256;
+    if ((r = buf_ensure(c, c->rpart, (size_t)blocks * 8))) return r;
+    if (!c->rdone.p) {
+      if ((r = buf_ensure(c, c->rdone, 16))) return r;
+      CUDA_TRY(c, cudaMemsetAsync(c->rdone.p, 0, 16, s));
+    }
+    a.part = (double*)c->rpart.p;
+    a.done = (unsigned*)c->rdone.p;
+  }
+  c->launches = 0;
+  CUDA_TRY(c, launch_refine_update(a, s));
+  c->launches = 1;
   return TFS_OK;
 }
 

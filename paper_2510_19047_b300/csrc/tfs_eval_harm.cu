@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
 namespace {
 
 template <int NCH, int PIX, int PITCH>
-cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
+cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s, int* shape) {
   constexpr int kWarps = 8;
   const size_t smem = (size_t)kWarps * (a.fine_cap * sizeof(float4) + kTrkF * 32 * sizeof(float));
   auto kern = a.response == 2 ? k_eval_harm<NCH, PIX, PITCH, true> : k_eval_harm<NCH, PIX, PITCH, false>;
@@ -486,32 +486,38 @@ cudaError_t launch_harm_one(const EvalArgs& a, int n_sm, cudaStream_t s) {
   const int64_t need = (a.n_work + kWarps - 1) / kWarps;
   const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
   kern<<<(unsigned)ctas, kWarps * 32, smem, s>>>(a);
+  if (shape) {
+    shape[0] = kWarps * 32;
+    shape[1] = (int)ctas;
+    shape[2] = per_sm;
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s) {
+cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s,
+                             int* shape) {
   if (a.n_work <= 0) return cudaSuccess;
   const bool fixed = a.pitch == kMixedPitch;
   if (n_chan == 1) {
     if (pix == TFS_PIX_F32)
-      return fixed ? launch_harm_one<1, TFS_PIX_F32, kMixedPitch>(a, n_sm, s)
-                   : launch_harm_one<1, TFS_PIX_F32, 0>(a, n_sm, s);
+      return fixed ? launch_harm_one<1, TFS_PIX_F32, kMixedPitch>(a, n_sm, s, shape)
+                   : launch_harm_one<1, TFS_PIX_F32, 0>(a, n_sm, s, shape);
     if (pix == TFS_PIX_F16)
-      return fixed ? launch_harm_one<1, TFS_PIX_F16, kMixedPitch>(a, n_sm, s)
-                   : launch_harm_one<1, TFS_PIX_F16, 0>(a, n_sm, s);
-    return fixed ? launch_harm_one<1, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s)
-                 : launch_harm_one<1, TFS_PIX_BF16, 0>(a, n_sm, s);
+      return fixed ? launch_harm_one<1, TFS_PIX_F16, kMixedPitch>(a, n_sm, s, shape)
+                   : launch_harm_one<1, TFS_PIX_F16, 0>(a, n_sm, s, shape);
+    return fixed ? launch_harm_one<1, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s, shape)
+                 : launch_harm_one<1, TFS_PIX_BF16, 0>(a, n_sm, s, shape);
   }
   if (pix == TFS_PIX_F32)
-    return fixed ? launch_harm_one<2, TFS_PIX_F32, kMixedPitch>(a, n_sm, s)
-                 : launch_harm_one<2, TFS_PIX_F32, 0>(a, n_sm, s);
+    return fixed ? launch_harm_one<2, TFS_PIX_F32, kMixedPitch>(a, n_sm, s, shape)
+                 : launch_harm_one<2, TFS_PIX_F32, 0>(a, n_sm, s, shape);
   if (pix == TFS_PIX_F16)
-    return fixed ? launch_harm_one<2, TFS_PIX_F16, kMixedPitch>(a, n_sm, s)
-                 : launch_harm_one<2, TFS_PIX_F16, 0>(a, n_sm, s);
-  return fixed ? launch_harm_one<2, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s)
-               : launch_harm_one<2, TFS_PIX_BF16, 0>(a, n_sm, s);
+    return fixed ? launch_harm_one<2, TFS_PIX_F16, kMixedPitch>(a, n_sm, s, shape)
+                 : launch_harm_one<2, TFS_PIX_F16, 0>(a, n_sm, s, shape);
+  return fixed ? launch_harm_one<2, TFS_PIX_BF16, kMixedPitch>(a, n_sm, s, shape)
+               : launch_harm_one<2, TFS_PIX_BF16, 0>(a, n_sm, s, shape);
 }
 
 }  // namespace tfs

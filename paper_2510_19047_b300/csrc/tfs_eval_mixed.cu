@@ -42,25 +42,34 @@ static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &
 
 }  // namespace
 
-#ifndef TFS_MIXED_UNROLL
-#define TFS_MIXED_UNROLL 3
-#endif
-#ifndef TFS_MIXED_MINB
-#define TFS_MIXED_MINB 4
-#endif
-
-constexpr int kBinUnroll = TFS_MIXED_UNROLL;
-#ifndef TFS_MIXED_DEPTH
-#define TFS_MIXED_DEPTH 3
-#endif
-constexpr int kDepth = TFS_MIXED_DEPTH;  // pixel-load lead of the unrolled path, in bins
+// Tile and schedule variants the launch autotuner chooses among (mixed_shape in
+// tfs_api.cu): the bin unroll of the general-bin loop path, the pixel-load lead of the
+// unrolled path (a ring of packed elements in registers, in bins), and the CTAs of 256
+// threads per SM the register allocation targets (4: 64 registers, 3: 85).
+template <int V>
+struct MixedVariant;
+template <>
+struct MixedVariant<0> {
+  static constexpr int unroll = 3, depth = 3, minb = 4;
+};
+template <>
+struct MixedVariant<1> {
+  static constexpr int unroll = 2, depth = 2, minb = 4;
+};
+template <>
+struct MixedVariant<2> {
+  static constexpr int unroll = 3, depth = 5, minb = 3;
+};
 
 // PITCH: the m-pitch of the pixel plane as a compile-time constant (kMixedPitch) so that
 // the 21 window rows are immediate offsets from one address, or 0 for a runtime pitch.
 // TDI: the TDI-1.5 response (response code 2) instead of the long-wavelength one, as
 // its own instantiation so the long-wavelength kernel carries none of its code.
-template <int NCH, int PIX, int PITCH, bool TDI>
-__global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) {
+// V: the tile/schedule variant (MixedVariant).
+template <int NCH, int PIX, int PITCH, bool TDI, int V>
+__global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalArgs a) {
+  constexpr int kBinUnroll = MixedVariant<V>::unroll;
+  constexpr int kDepth = MixedVariant<V>::depth;  // pixel-load lead of the unrolled path
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
   const int lane = threadIdx.x & 31;
@@ -83,6 +92,8 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   // in a long segment's. The FP16/BF16 pixels' own rounding is larger, and those
   // instantiations skip it (it costs registers in the hot loop).
   constexpr bool kNear = PIX == TFS_PIX_F32;
+  // precision-study pixel types: the template's values held at FP16 precision
+  constexpr bool kR16 = PIX == TFS_PIX_F16_ALL || PIX == TFS_PIX_BF16_ALL;
 
   for (;;) {
     int t = 0;
@@ -239,6 +250,12 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
               Tr1 = fmaf(fpE, amp_c, fxE * amp_s);
               Ti1 = fmaf(fpE, amp_s, -fxE * amp_c);
             }
+            if (kR16) {
+              Tr0 = round_f16(Tr0);
+              Ti0 = round_f16(Ti0);
+              Tr1 = round_f16(Tr1);
+              Ti1 = round_f16(Ti1);
+            }
           }
         }
       }
@@ -291,9 +308,13 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
               const float x1 = kNear && j == kNFHalf - 1 ? a1 : aa - c;
               const float x2 = kNear && j == kNFHalf - 1 ? a1 + eps : ae - c;
               w_general(x1, x2, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
+              if (kR16) {
+                wr = round_f16(wr);
+                wi = round_f16(wi);
+              }
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
+              acc_asym<kR16>(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
             }
           }
         } else {
@@ -313,9 +334,13 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
               float wr, wi;
               const bool near = kNear && jp == -1;
               w_general(near ? a1 : x1, near ? a1 + eps : x2, sig, spi, cpsi, spsi, true, wr, wi);
+              if (kR16) {
+                wr = round_f16(wr);
+                wi = round_f16(wi);
+              }
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
             } else {
-              acc_asym(s, cur_r, cur_i, cur_w, xx, m2c);
+              acc_asym<kR16>(s, cur_r, cur_i, cur_w, xx, m2c);
             }
             if (j + 1 < kNF) cur = nxt;
           }
@@ -396,60 +421,78 @@ __global__ void __launch_bounds__(256, TFS_MIXED_MINB) k_eval_mixed(EvalArgs a) 
   }
 }
 
+// The instantiation of (channels, pixel type, pitch, response, variant). Variants other
+// than 0 are compiled for the two-channel, fixed-pitch planes only (the configuration of
+// long A/E grids); other configurations map every variant to variant 0.
 template <int NCH, int PIX, int PITCH>
-static cudaError_t launch_one(const EvalArgs& a, int warps, int ctas, cudaStream_t s) {
+static void (*kernel_of(int resp, int variant))(EvalArgs) {
+  constexpr bool kTuned = NCH == 2 && PITCH == kMixedPitch && PIX <= TFS_PIX_BF16;
+  const int v = kTuned ? variant : 0;
+  if (resp == 2) {
+    if (v == 1) return k_eval_mixed<NCH, PIX, PITCH, true, kTuned ? 1 : 0>;
+    if (v == 2) return k_eval_mixed<NCH, PIX, PITCH, true, kTuned ? 2 : 0>;
+    return k_eval_mixed<NCH, PIX, PITCH, true, 0>;
+  }
+  if (v == 1) return k_eval_mixed<NCH, PIX, PITCH, false, kTuned ? 1 : 0>;
+  if (v == 2) return k_eval_mixed<NCH, PIX, PITCH, false, kTuned ? 2 : 0>;
+  return k_eval_mixed<NCH, PIX, PITCH, false, 0>;
+}
+
+template <int NCH, int PIX, int PITCH>
+static cudaError_t launch_one(const EvalArgs& a, int variant, int warps, int ctas, cudaStream_t s) {
   const size_t smem = (size_t)warps * a.fine_cap * sizeof(float4);
-  if (a.response == 2)
-    k_eval_mixed<NCH, PIX, PITCH, true><<<ctas, warps * 32, smem, s>>>(a);
-  else
-    k_eval_mixed<NCH, PIX, PITCH, false><<<ctas, warps * 32, smem, s>>>(a);
+  kernel_of<NCH, PIX, PITCH>(a.response, variant)<<<ctas, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Sets the dynamic shared-memory limit of the instantiation and returns how many CTAs
 // of this shape fit on one SM.
 template <int NCH, int PIX, int PITCH>
-static cudaError_t occ_one(int warps, int fine_cap, int resp, int* n) {
+static cudaError_t occ_one(int variant, int warps, int fine_cap, int resp, int* n) {
   const size_t smem = (size_t)warps * fine_cap * sizeof(float4);
-  auto kern = resp == 2 ? k_eval_mixed<NCH, PIX, PITCH, true> : k_eval_mixed<NCH, PIX, PITCH, false>;
+  auto kern = kernel_of<NCH, PIX, PITCH>(resp, variant);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, warps * 32, smem);
 }
 
 // Instantiation for (channels, pixel type, pitch); CALL(NCH, PIX, PITCH) is an expression.
+#define TFS_MIXED_DISPATCH_PIX(CALL, N, pix, fixed)                                         \
+  do {                                                                                      \
+    if ((pix) == TFS_PIX_F32)                                                               \
+      return (fixed) ? CALL(N, TFS_PIX_F32, kMixedPitch) : CALL(N, TFS_PIX_F32, 0);         \
+    if ((pix) == TFS_PIX_F16)                                                               \
+      return (fixed) ? CALL(N, TFS_PIX_F16, kMixedPitch) : CALL(N, TFS_PIX_F16, 0);         \
+    if ((pix) == TFS_PIX_BF16)                                                              \
+      return (fixed) ? CALL(N, TFS_PIX_BF16, kMixedPitch) : CALL(N, TFS_PIX_BF16, 0);       \
+    if ((pix) == TFS_PIX_F16_ALL)                                                           \
+      return (fixed) ? CALL(N, TFS_PIX_F16_ALL, kMixedPitch) : CALL(N, TFS_PIX_F16_ALL, 0); \
+    return (fixed) ? CALL(N, TFS_PIX_BF16_ALL, kMixedPitch) : CALL(N, TFS_PIX_BF16_ALL, 0);  \
+  } while (0)
 #define TFS_MIXED_DISPATCH(CALL, n_chan, pix, pitch)                                        \
   do {                                                                                      \
-    const bool fixed = (pitch) == kMixedPitch;                                              \
-    if ((n_chan) == 1) {                                                                    \
-      if ((pix) == TFS_PIX_F32)                                                             \
-        return fixed ? CALL(1, TFS_PIX_F32, kMixedPitch) : CALL(1, TFS_PIX_F32, 0);         \
-      if ((pix) == TFS_PIX_F16)                                                             \
-        return fixed ? CALL(1, TFS_PIX_F16, kMixedPitch) : CALL(1, TFS_PIX_F16, 0);         \
-      return fixed ? CALL(1, TFS_PIX_BF16, kMixedPitch) : CALL(1, TFS_PIX_BF16, 0);         \
-    }                                                                                       \
-    if ((pix) == TFS_PIX_F32)                                                               \
-      return fixed ? CALL(2, TFS_PIX_F32, kMixedPitch) : CALL(2, TFS_PIX_F32, 0);           \
-    if ((pix) == TFS_PIX_F16)                                                               \
-      return fixed ? CALL(2, TFS_PIX_F16, kMixedPitch) : CALL(2, TFS_PIX_F16, 0);           \
-    return fixed ? CALL(2, TFS_PIX_BF16, kMixedPitch) : CALL(2, TFS_PIX_BF16, 0);           \
+    const bool fixed_ = (pitch) == kMixedPitch;                                             \
+    if ((n_chan) == 1) TFS_MIXED_DISPATCH_PIX(CALL, 1, pix, fixed_);                        \
+    TFS_MIXED_DISPATCH_PIX(CALL, 2, pix, fixed_);                                           \
   } while (0)
 
 // Launch only (no attribute calls, so it can be captured into a CUDA graph);
 // mixed_occupancy() must have been called for the same shape first.
-cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
-                              cudaStream_t s) {
+cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int variant, int warps,
+                              int ctas, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
-#define TFS_CALL(N, P, Q) launch_one<N, P, Q>(a, warps, ctas, s)
+#define TFS_CALL(N, P, Q) launch_one<N, P, Q>(a, variant, warps, ctas, s)
   TFS_MIXED_DISPATCH(TFS_CALL, n_chan, pix, a.pitch);
 #undef TFS_CALL
 }
 
-cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int warps, int fine_cap,
-                            int* ctas_per_sm) {
-#define TFS_CALL(N, P, Q) occ_one<N, P, Q>(warps, fine_cap, resp, ctas_per_sm)
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int variant, int warps,
+                            int fine_cap, int* ctas_per_sm) {
+#define TFS_CALL(N, P, Q) occ_one<N, P, Q>(variant, warps, fine_cap, resp, ctas_per_sm)
   TFS_MIXED_DISPATCH(TFS_CALL, n_chan, pix, pitch);
 #undef TFS_CALL
 }
+
+int mixed_variants(int n_chan, int pitch) { return n_chan == 2 && pitch == kMixedPitch ? 3 : 1; }
 
 }  // namespace tfs

@@ -764,6 +764,18 @@ __global__ void __launch_bounds__(128) k_eval_plain_harm(EvalArgs a) {
   }
 }
 
+cudaError_t ref_occupancy(const EvalArgs& a, int path, int* per_sm) {
+  const bool tdi = a.response == 2, harm = a.harm.n > 0;
+  const void* k;
+  if (path == TFS_PATH_FP64)
+    k = harm ? (tdi ? (const void*)k_eval_fp64_harm<true> : (const void*)k_eval_fp64_harm<false>)
+             : (tdi ? (const void*)k_eval_fp64<true> : (const void*)k_eval_fp64<false>);
+  else
+    k = harm ? (tdi ? (const void*)k_eval_plain_harm<true> : (const void*)k_eval_plain_harm<false>)
+             : (tdi ? (const void*)k_eval_plain<true> : (const void*)k_eval_plain<false>);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, 128, 0);
+}
+
 cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s) {
   if (a.n_tpl <= 0) return cudaSuccess;
   if (a.harm.n > 0) {

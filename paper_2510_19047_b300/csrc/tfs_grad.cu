@@ -137,7 +137,9 @@ __device__ __forceinline__ BinW bin_w(float v1, float v2, float cps, float sps) 
   float cp = 1.f, sp = 0.f;
   const bool sweep = s1 != s2;
   if (sweep) {
-    sincospif(0.5f * v1 * v1, &sp, &cp);
+    // argument in units of pi reduced to [-1, 1], then the hardware sine/cosine
+    const float h = 0.5f * v1 * v1;
+    __sincosf(3.141592654f * (h - 2.0f * rint_small(0.5f * h)), &sp, &cp);
     b.wr += cp + sp;  // (1+i) e^{-i pi v1^2/2}
     b.wi += cp - sp;
   }

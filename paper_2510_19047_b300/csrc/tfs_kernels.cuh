@@ -80,17 +80,52 @@ cudaError_t launch_setup(const double* theta, int64_t n, int pn_order, const Gri
 cudaError_t launch_check_tpl(const TplConst* tpl, int64_t n, int n_tranche, int* err, cudaStream_t s);
 cudaError_t launch_eval_fp64(const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_eval_plain(const EvalArgs& a, cudaStream_t s);
-// Persistent mixed-precision launch; grid = ctas, block = 32 * warps.
-cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int warps, int ctas,
-                              cudaStream_t s);
-cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int warps, int fine_cap,
-                            int* ctas_per_sm);
+// CTAs of 128 threads resident per SM for the FP64 (path 0) or plain (path 1) kernel.
+cudaError_t ref_occupancy(const EvalArgs& a, int path, int* per_sm);
+// Persistent mixed-precision launch; grid = ctas, block = 32 * warps; variant selects
+// the compiled tile/schedule variant (0 .. mixed_variants() - 1).
+cudaError_t launch_eval_mixed(const EvalArgs& a, int n_chan, int pix, int variant, int warps,
+                              int ctas, cudaStream_t s);
+cudaError_t mixed_occupancy(int n_chan, int pix, int pitch, int resp, int variant, int warps,
+                            int fine_cap, int* ctas_per_sm);
+// Number of compiled variants for this configuration.
+int mixed_variants(int n_chan, int pitch);
 // Multi-harmonic mixed launch (persistent, a.counter zeroed by the caller); a.harm_K
 // from launch_harm_phase. Chooses its own grid (n_sm x resident CTAs of 8 warps).
-cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s);
+cudaError_t launch_eval_harm(const EvalArgs& a, int n_chan, int pix, int n_sm, cudaStream_t s,
+                             int* shape = nullptr);  // shape: threads per CTA, CTAs, CTAs per SM
 // K[i][h] = frac(nu_h (phi0 + P5 + P3) / 2 pi) of template i as double-float.
 cudaError_t launch_harm_phase(const TplConst* tpl, int64_t n, const HarmSet& h, float2* K,
                               cudaStream_t s);
+
+// Particle-swarm state of S swarms x P particles (all device pointers): positions,
+// velocities and personal bests SoA [8][S*P] (particle i of swarm s at s*P + i), personal
+// best values [S*P], swarm bests [8][S] and values [S]; tile corners [S][8].
+struct PsoArgs {
+  int n_swarm, n_part;
+  double *x, *v, *pbest, *pval, *gbest, *gval;
+  const double *lo, *hi;
+  double inertia, c1, c2;
+  uint2 key;        // Philox key (the seed)
+  double* history;  // [iterations][S] swarm best after each step, or null
+};
+cudaError_t launch_pso_init(const PsoArgs& a, int n_sm, cudaStream_t s);
+cudaError_t launch_pso_step(const PsoArgs& a, const double* f, int64_t iter, int move,
+                            cudaStream_t s);
+
+// One refinement step of n candidates (device pointers; see k_refine_update).
+struct RefineArgs {
+  int64_t n;
+  const double *stat, *grad;            // U [n] and dU/dtheta [8][n] at theta
+  double *theta, *best_theta, *best_grad, *best_stat, *eta;
+  const double* sigma;                  // [8][n]
+  double lo[8], hi[8];
+  double eta_up, eta_down;
+  double* mean_out;                     // mean of U_best, or null
+  double* part;                         // [blocks] partial sums (when mean_out is set)
+  unsigned* done;                       // block counter, zero between calls
+};
+cudaError_t launch_refine_update(const RefineArgs& a, cudaStream_t s);
 
 struct AscentParams {
   double step[8], lo[8], hi[8];

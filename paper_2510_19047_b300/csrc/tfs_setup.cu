@@ -179,6 +179,12 @@ __global__ void k_pack_mixed(GridDesc g, int pitch, const double* d_re, const do
     } else if (PIX == TFS_PIX_F16) {
       ((uint4*)out)[i] = make_uint4(pack_h2(v[0][0], v[1][0]), pack_h2(v[0][1], v[1][1]),
                                     __float_as_uint(v[0][2]), __float_as_uint(v[1][2]));
+    } else if (PIX == TFS_PIX_F16_ALL) {
+      ((uint4*)out)[i] = make_uint4(pack_h2(v[0][0], v[1][0]), pack_h2(v[0][1], v[1][1]),
+                                    pack_h2(v[0][2], v[1][2]), 0u);
+    } else if (PIX == TFS_PIX_BF16_ALL) {
+      ((uint4*)out)[i] = make_uint4(pack_b2(v[0][0], v[1][0]), pack_b2(v[0][1], v[1][1]),
+                                    pack_b2(v[0][2], v[1][2]), 0u);
     } else {
       ((uint4*)out)[i] = make_uint4(pack_b2(v[0][0], v[1][0]), pack_b2(v[0][1], v[1][1]),
                                     __float_as_uint(v[0][2]), __float_as_uint(v[1][2]));
@@ -362,6 +368,12 @@ cudaError_t launch_pack_mixed(int pix, const GridDesc& g, int pitch, const doubl
       break;
     case TFS_PIX_F16:
       k_pack_mixed<TFS_PIX_F16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
+      break;
+    case TFS_PIX_F16_ALL:
+      k_pack_mixed<TFS_PIX_F16_ALL><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
+      break;
+    case TFS_PIX_BF16_ALL:
+      k_pack_mixed<TFS_PIX_BF16_ALL><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);
       break;
     default:
       k_pack_mixed<TFS_PIX_BF16><<<blocks, 256, 0, s>>>(g, pitch, d_re, d_im, w, su, sw, P);

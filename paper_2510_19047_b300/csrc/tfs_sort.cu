@@ -135,12 +135,13 @@ __global__ void k_template_keys(const TplConst* __restrict__ tpl, int64_t n, uin
   }
 }
 
-// Ascending order of the key = decreasing order of the statistic; NaN sorts last.
+// Ascending order of the key = decreasing order of the statistic; NaN sorts last; -0.0
+// and +0.0 are one key, so that they tie like other equal values (by the lower index).
 __global__ void k_stat_keys(const double* __restrict__ stat, int64_t n, uint64_t* keys,
                             int32_t* vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
-    const double x = stat[i];
+    const double x = stat[i] == 0.0 ? 0.0 : stat[i];
     uint64_t b = (uint64_t)__double_as_longlong(x);
     b = (b >> 63) ? ~b : (b | 0x8000000000000000ull);  // monotone in x
     keys[i] = isnan(x) ? ~0ull : ~b;
@@ -247,13 +248,19 @@ cudaError_t static_scratch(void** out) {
   return cudaSuccess;
 }
 
+// Device (or managed) memory of the current device.
 bool on_device(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace

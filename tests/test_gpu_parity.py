@@ -8,6 +8,10 @@ Tolerances (relative error of Upsilon per template and level):
   mixed, FP32 pixels 1e-4
   mixed, FP16 pixels max 1.5e-3, p99 1e-3   (3x and 2x the FP16 unit roundoff 2^-11)
   mixed, BF16 pixels max 1.2e-2, p99 8e-3   (3x and 2x the BF16 unit roundoff 2^-8)
+  mixed, u and w FP16, template values FP16   max 2e-3, p99 1.5e-3 (two independent
+                     roundings of 2^-11 per bin: the pixel's and the template value's)
+  mixed, u and w BF16, template values FP16   max 1.2e-2, p99 8e-3 (the BF16 pixel rounding
+                     dominates)
 The reduced-precision bounds follow from rounding u = d~/S once to the storage type
 (w = 1/S is stored in FP32): each pixel carries an independent relative error below the
 unit roundoff, so |Z_n| moves by a random fraction of it and Upsilon by about twice
@@ -23,7 +27,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = {("fp64", "f16"): (1e-10, 1e-10), ("plain", "f16"): (1e-4, 1e-4),
        ("mixed", "f32"): (1e-4, 1e-4), ("mixed", "f16"): (1.5e-3, 1e-3),
-       ("mixed", "bf16"): (1.2e-2, 8e-3)}
+       ("mixed", "bf16"): (1.2e-2, 8e-3),
+       ("mixed", "f16all"): (2e-3, 1.5e-3), ("mixed", "bf16all"): (1.2e-2, 8e-3)}
 CASES = list(TOL)
 FP64_TOL = 1e-10
 
@@ -375,6 +380,25 @@ def test_two_year_full_bank_sampled(two_year):
             tol = FP64_TOL if path == "fp64" else 1e-4
             ref = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT, pn_order=1, response=1)[0]
             assert rel_err(got[i], ref)[0] < tol, (path, L)
+
+
+def test_graph_replay_with_profiling(ae45, ae45_bank):
+    """The bench's call pattern: a profiled context replaying a CUDA graph, first with
+    the diagnostic outputs and then without, repeatedly; the kernel times are reported
+    and the results match the direct launch bit for bit."""
+    lev = [64, 16, 4]
+    ref, _, rdiag = ctx_for(ae45, "mixed", "f16").eval_statistic(ae45_bank, lev, diag=True)
+    c = ctx_for(ae45, "mixed", "f16", use_graph=1, profile=1)
+    got, _, diag = c.eval_statistic(ae45_bank, lev, diag=True)
+    assert np.array_equal(got, ref) and np.array_equal(diag, rdiag)
+    for _ in range(3):
+        got, _, _ = c.eval_statistic(ae45_bank, lev)
+        assert np.array_equal(got, ref)
+        prof = c.last_profile()
+        assert prof["statistic"] > 0 and prof["setup"] > 0
+    shape = c.last_launch_shape()
+    assert shape["threads_per_cta"] in (128, 256) and shape["ctas"] >= 1
+    assert shape["tune_trials"] >= 8
 
 
 def test_graph_replay_checked_mode_and_launch_shapes(ae45, ae45_bank):
