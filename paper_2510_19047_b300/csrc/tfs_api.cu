@@ -62,6 +62,7 @@ struct tfs_ctx {
   // refinement step's mean
   DevBuf tile_lo, tile_hi, rpart, rdone;
   DevBuf tune_perm;  // the autotuner's strided sample of the queue
+  DevBuf live, rank;  // unmasked tranches in order; unmasked tranches before each tranche
   // harmonic content of the templates (n = 0: the dominant mode) and its per-template
   // constant phases (mixed path)
   HarmSet harm{};
@@ -409,7 +410,8 @@ int tfs_destroy(tfs_ctx* c) {
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
                    &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart,
-                   &c->harmK, &c->tile_lo, &c->tile_hi, &c->rpart, &c->rdone, &c->tune_perm};
+                   &c->harmK, &c->tile_lo, &c->tile_hi, &c->rpart, &c->rdone, &c->tune_perm,
+                   &c->live, &c->rank};
   for (DevBuf* b : all) buf_free(c, *b);
   for (int i = 0; i < 5; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -546,6 +548,26 @@ int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tran
                                                        : cudaMemcpyHostToDevice));
   } else {
     CUDA_TRY(c, cudaMemset(c->mask.p, 1, c->g.n_tranche));
+  }
+  // the unmasked tranches in order, and for each tranche the count of unmasked ones
+  // before it: the mixed kernel walks a template's range over these only, so that no
+  // lane of a warp idles on a gap
+  {
+    const int nt = c->g.n_tranche;
+    std::vector<uint8_t> hmask(nt);
+    CUDA_TRY(c, cudaMemcpy(hmask.data(), c->mask.p, nt, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> live, rank(nt + 1);
+    for (int m = 0; m < nt; ++m) {
+      rank[m] = (int32_t)live.size();
+      if (hmask[m]) live.push_back(m);
+    }
+    rank[nt] = (int32_t)live.size();
+    if ((r = buf_ensure(c, c->live, std::max<size_t>(live.size(), 1) * 4)) ||
+        (r = buf_ensure(c, c->rank, (size_t)(nt + 1) * 4)))
+      return r;
+    if (!live.empty())
+      CUDA_TRY(c, cudaMemcpy(c->live.p, live.data(), live.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->rank.p, rank.data(), (size_t)(nt + 1) * 4, cudaMemcpyHostToDevice));
   }
   // validate and find the ranges of u = d w and w
   unsigned long long* mx = (unsigned long long*)c->counter.p;
@@ -688,6 +710,8 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.w32 = (const float*)c->w32.p;
   a.Umix = c->Umix.p;
   a.mask = (const uint8_t*)c->mask.p;
+  a.live = (const int32_t*)c->live.p;
+  a.rank = (const int32_t*)c->rank.p;
   a.tpl = (const TplConst*)c->tpl.p;
   a.tplm = mix;
   a.perm = nullptr;

@@ -41,6 +41,8 @@ struct EvalArgs {
   const float* w32;             // [c][m][k] scaled FP32 w
   const void* Umix;             // [k][pitch] mixed plane (u and w of both channels)
   const uint8_t* mask;          // [N_t]
+  const int32_t* live;          // [n_live] unmasked tranches in increasing order
+  const int32_t* rank;          // [N_t + 1] unmasked tranches before tranche m
   const TplConst* tpl;          // [n_tpl]
   const TplMix* tplm;           // [n_tpl] (mixed path)
   const int32_t* perm;          // processing order (mixed path), may be null
