@@ -26,6 +26,15 @@ import time
 import numpy as np
 
 
+# FP32 peak (148 SMs x 128 lanes x 2 flop x 2.032 GHz) and the gradient kernel's
+# algorithmic flops per active (template, tranche) unit: pass A recomputes Z_n, N_n
+# (1250, the statistic's own figure); pass B forms per bin the five complex and eight
+# real weighted sums of both channels (~83 flops) and per tranche the sensitivities and
+# the reverse-mode step through track and response (~500): 1250 + 21 x 83 + 500 ~ 3500.
+PEAK_FP32_TFLOPS = 148 * 128 * 2 * 2.032 / 1000.0
+GRAD_FLOP_PER_UNIT = 3500
+
+
 def _ctx(D, **kw):
     from paper_2510_19047_b300.binding import TFS
     c = TFS(0, pn_order=D.pn_order, response=D.response, **kw)
@@ -129,13 +138,30 @@ def refine(args):
         ts.append(e0.elapsed_time(e1))
     idx = np.linspace(0, cand.shape[1] - 1, 6).astype(int)
     ru, rg = oracle.gradient(D.d, D.w, D.mask, cand[:, idx], 16, D.dT, pn_order=1, response=1)
+    S = oracle.gradient_scale(D.d, D.w, D.mask, cand[:, idx], 16, D.dT, pn_order=1, response=1,
+                              tranche_level=True)
     gg = g.cpu().numpy()[:, idx]
     comp = {}
     for p, name in enumerate(("Mc", "eta", "f0", "phi0", "lam", "beta", "psi", "iota")):
         if p == 3:
             continue
-        scale = np.maximum(np.abs(rg[p]), 1e-3 * np.abs(rg[p]).max())
-        comp[name] = float(np.max(np.abs(gg[p] - rg[p]) / scale))
+        # error in units of the component's tranche-level term scale
+        comp[name] = float(np.max(np.abs(gg[p] - rg[p]) / S[p]))
+    # roofline of the gradient kernel: active (template, tranche) units of the batch x
+    # GRAD_FLOP_PER_UNIT, over the kernel's time
+    _, _, dg = c.eval_statistic(th, 16, diag=True)
+    units = int(dg[0].sum().item())
+    c.set_options(profile=1)
+    kms = []
+    for _ in range(3):
+        c.grad_statistic(th, 16)
+        kms.append(c.last_profile()["statistic"])
+    c.set_options(profile=0)
+    k_ms = statistics.median(kms)
+    achieved = units * GRAD_FLOP_PER_UNIT / (k_ms / 1000.0) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / PEAK_FP32_TFLOPS, "kernel": "k_grad", "kernel_ms": k_ms,
+            "units_per_launch": units, "flop_per_unit": GRAD_FLOP_PER_UNIT}
     run_refine(c, th, 16, steps=2)  # untimed: first use of the ascent's device kernels
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -145,7 +171,8 @@ def refine(args):
     u0, u1 = u0.cpu().numpy(), u1.cpu().numpy()
     return {"study": "refine", "workload": "AE-2yr-2048x6144, 4096 candidates near 20 injections, N_seg 16",
             "grad_ms_per_call": statistics.median(ts),
-            "grad_rel_err_vs_oracle": comp,
+            "roofline": roof,
+            "grad_err_vs_oracle_in_term_scale": comp,
             "stat_rel_err_vs_oracle": _rel(u.cpu().numpy()[idx], ru)[0],
             "ascent_steps": 200, "ascent_seconds": dt,
             "mean_upsilon_start": float(u0.mean()), "mean_upsilon_end": float(u1.mean()),

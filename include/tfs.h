@@ -128,6 +128,20 @@ int tfs_load_tf_data(tfs_ctx* ctx, int n_chan, int n_tranche, int n_bins, double
  * Forms the weighted data u = d~ w once, in every storage the paths use. */
 int tfs_set_noise_weights(tfs_ctx* ctx, const double* inv_psd, const uint8_t* tranche_mask);
 
+/* Replace the loaded data by a noise-only realisation drawn from the current noise
+ * weights, for false-alarm backgrounds (Sec. "False alarm probabilities": the paper
+ * estimates the background of the search maximum from independent noise-only
+ * realisations). Per pixel d~ = sqrt(S / (4 delta f)) (g1 + i g2) with S = 1/w (d~ = 0
+ * where w = 0), so E|d~|^2 = S / (2 delta f), the data's convention; g1, g2 are
+ * independent standard normals from the Box-Muller transform
+ *   g1 + i g2 = sqrt(-2 ln(1 - a)) e^{2 pi i b}
+ * of the two uniforms a, b in [0, 1) (top 53 bits of each half) of one Philox4x32-10
+ * block keyed by `seed` (low, high 32 bits) with counter (pixel index low 32 bits, high
+ * 32 bits, 0, 0x4E4F4953); pixel index = (chan * N_t + tranche) * n_bins + bin. The
+ * weights and mask stay; u = d~ w is re-formed in every storage. Synchronous.
+ * TFS_ERR_STATE before load_tf_data and set_noise_weights. */
+int tfs_noise_realisation(tfs_ctx* ctx, uint64_t seed);
+
 /* Upsilon_{N_seg} (Eq. Upsilon-seg) for n_tpl templates.
  *   theta: double [8][n_tpl] (SoA, order above).
  *   per_template == 0: n_seg[0..n_levels-1] are 1..4 segment counts applied to every

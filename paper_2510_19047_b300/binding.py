@@ -94,6 +94,7 @@ def load_library(build_if_missing=True):
         "tfs_load_tf_data": (i32, [P, i32, i32, i32, dbl, dbl, dbl, P, P]),
         "tfs_set_noise_weights": (i32, [P, P, P]),
         "tfs_set_harmonics": (i32, [P, i32, P, P, P]),
+        "tfs_noise_realisation": (i32, [P, ctypes.c_uint64]),
         "tfs_eval_statistic": (i32, [P, P, i64, P, i32, i32, P, P, P, P]),
         "tfs_grad_statistic": (i32, [P, P, i64, ctypes.c_int32, P, P, P]),
         "tfs_select_top": (i32, [P, P, i64, i64, P, P]),
@@ -232,6 +233,11 @@ class TFS:
         pw, kw = _ptr(inv_psd)
         pm, km = _ptr(mask)
         self._check(self.lib.tfs_set_noise_weights(self.h, pw, pm))
+
+    def noise_realisation(self, seed):
+        """Replace the data by a noise-only realisation drawn from the current weights
+        (tfs_noise_realisation)."""
+        self._check(self.lib.tfs_noise_realisation(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF))
 
     # -- statistic ----------------------------------------------------------------------
     def eval_statistic(self, theta, n_seg, per_template=False, diag=False, out=None):

@@ -527,6 +527,8 @@ int tfs_load_tf_data(tfs_ctx* c, int n_chan, int n_tranche, int n_bins, double d
   return TFS_OK;
 }
 
+static int pack_all(tfs_ctx* c);
+
 int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tranche_mask) {
   if (!c) return TFS_ERR_ARG;
   c->err.clear();
@@ -569,6 +571,17 @@ int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tran
       CUDA_TRY(c, cudaMemcpy(c->live.p, live.data(), live.size() * 4, cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->rank.p, rank.data(), (size_t)(nt + 1) * 4, cudaMemcpyHostToDevice));
   }
+  c->has_weights = false;
+  if ((r = pack_all(c))) return r;
+  c->has_weights = true;
+  return TFS_OK;
+}
+
+// Validates the data under the weights, finds the storage scales and forms u = d~ w and
+// w in every storage the paths use (synchronous).
+static int pack_all(tfs_ctx* c) {
+  const size_t n = (size_t)c->g.n_chan * c->g.n_tranche * c->g.n_bins;
+  int r;
   // validate and find the ranges of u = d w and w
   unsigned long long* mx = (unsigned long long*)c->counter.p;
   int* bad = (int*)((char*)c->counter.p + 16);
@@ -597,6 +610,23 @@ int tfs_set_noise_weights(tfs_ctx* c, const double* inv_psd, const uint8_t* tran
   if (r) return r;
   c->ugrad_ok = false;
   CUDA_TRY(c, cudaDeviceSynchronize());
+  return TFS_OK;
+}
+
+int tfs_noise_realisation(tfs_ctx* c, uint64_t seed) {
+  if (!c) return TFS_ERR_ARG;
+  c->err.clear();
+  if (!c->has_data || !c->has_weights)
+    return fail(c, TFS_ERR_STATE, "load_tf_data and set_noise_weights must be called first");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  cudaGetLastError();
+  const int64_t n = (int64_t)c->g.n_chan * c->g.n_tranche * c->g.n_bins;
+  CUDA_TRY(c, launch_noise(n, (const double*)c->w_in.p, c->g.df, seed, (double*)c->d_re.p,
+                           (double*)c->d_im.p, c->n_sm, 0));
+  c->has_weights = false;
+  int r = pack_all(c);
+  if (r) return r;
+  c->launches += 1;
   c->has_weights = true;
   return TFS_OK;
 }

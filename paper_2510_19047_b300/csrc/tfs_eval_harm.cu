@@ -264,44 +264,47 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
                      c3 = ldg_nc4(cq + 3);
         const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
         const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
-        const df dopc = {c2.z, c2.w}, dops = {c3.x, c3.y};
-        const float C2 = c3.z, fd_k = c3.w;
+        const float dopc = c2.z, dops = c2.w;
+        const df C2 = {c3.x, c3.y};
+        const float fd_k = c3.z;
         const TrancheF tr = a.tabF[m];
         tk.ca = tr.ca_hi;
         tk.sa = tr.sa_hi;
         const df tt = {tr.t_hi, tr.t_lo};
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (a.response) {
-          d0 = fmaf(dopc.hi, tr.ca_hi, dops.hi * tr.sa_hi);
-          d1 = (float)kOmega * (dops.hi * tr.ca_hi - dopc.hi * tr.sa_hi);
+          d0 = fmaf(dopc, tr.ca_hi, dops * tr.sa_hi);
+          d1 = (float)kOmega * (dops * tr.ca_hi - dopc * tr.sa_hi);
           d2 = -(float)(kOmega * kOmega) * d0;
         }
         const df tp = quick_add_f(tt, d0);
-        const df u = one_minus(df_mul(tp, tc_inv));  // 1 - t'/t_c
+        const df u = one_minus(df_mul_u(tp, tc_inv));  // 1 - t'/t_c
         if (!(u.hi > 0.f)) {
           act = false;
         } else {
           // y = u^(-1/8): FP32 seed, one Newton step with a double-float residual
           const float y0 = pow_m18(u.hi);
           const df y02 = two_prod(y0, y0);
-          const df y08 = df_sqr(df_sqr(y02));
-          const df p = df_mul(u, y08);
+          const df y08 = df_sqr_u(df_sqr_u(y02));
+          const df p = df_mul_u(u, y08);
           const float r = __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo);
           const df y = quick_two_sum(y0, y0 * r * 0.125f);
-          const df y2 = df_sqr(y);
-          const df y3 = df_mul(y2, y);
-          const float c2y2 = C2 * y2.hi;
-          const df fs = df_mul(df_mul(F0, y3), two_sum(1.0f, c2y2));
+          // products that only feed further df arithmetic stay unnormalised (~46 bits)
+          const df y2 = df_sqr_u(y);
+          const df y3 = df_mul_u(y2, y);
+          const df c2y2d = df_mul_u(C2, y2);
+          const float c2y2 = c2y2d.hi;
+          const df fs = df_mul_u(df_mul_u(F0, y3), one_plus_u(c2y2d));
           const df f = quick_add_f(fs, fs.hi * d1);
           const float y2f = y2.hi, y3f = y3.hi;
-          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
+          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
           tk.fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
           tk.x = df_mul(f, dTd);
           tk.f = f.hi;
           if (!(tk.fdot > 0.f)) {
             act = false;
           } else {
-            tk.S = df_mul(df_mul(u, y3), df_add(P5, df_mul(P3, y2)));
+            tk.S = df_mul(df_mul_u(u, y3), df_add(P5, df_mul_u(P3, y2)));
             tk.amp = y2f * fmaf(c2y2, fmaf(c2y2, fmaf(c2y2, 4.0f / 81.0f, -1.0f / 9.0f), 2.0f / 3.0f),
                                 1.0f);
             if (a.response && !TDI) {

@@ -36,8 +36,8 @@ namespace tfs {
 namespace {
 
 static_assert(offsetof(TplMix, tcinv_hi) == 0 && offsetof(TplMix, P5_hi) == 16 &&
-                  offsetof(TplMix, K_hi) == 32 && offsetof(TplMix, dops_hi) == 48 &&
-                  offsetof(TplMix, C2) == 56 && offsetof(TplMix, fd_k) == 60 &&
+                  offsetof(TplMix, K_hi) == 32 && offsetof(TplMix, dopc) == 40 &&
+                  offsetof(TplMix, C2_hi) == 48 && offsetof(TplMix, fd_k) == 56 &&
                   offsetof(TplMix, pp) == 64 && offsetof(TplMix, px) == 88 &&
                   offsetof(TplMix, nx) == 112,
               "TplMix layout assumed by the 16-byte loads of the mixed kernel");
@@ -148,40 +148,44 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
                      c3 = ldg_nc4(cq + 3);
         const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
         const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};  // phase coefficients in cycles
-        const df Kc = {c2.x, c2.y}, dopc = {c2.z, c2.w};
-        const df dops = {c3.x, c3.y};
-        const float C2 = c3.z, fd_k = c3.w;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
+        const df Kc = {c2.x, c2.y};
+        const float dopc = c2.z, dops = c2.w;
+        const df C2 = {c3.x, c3.y};
+        const float fd_k = c3.z;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
         const TrancheF tr = a.tabF[m];
         const df tt = {tr.t_hi, tr.t_lo};
         // barycentre delay n.r/c (|d0| <= 500 s) in FP32: its rounding, < 1e-4 s, moves
         // the phase by < 1e-5 cycles
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (a.response) {
-          d0 = fmaf(dopc.hi, tr.ca_hi, dops.hi * tr.sa_hi);
-          d1 = (float)kOmega * (dops.hi * tr.ca_hi - dopc.hi * tr.sa_hi);
+          d0 = fmaf(dopc, tr.ca_hi, dops * tr.sa_hi);
+          d1 = (float)kOmega * (dops * tr.ca_hi - dopc * tr.sa_hi);
           d2 = -(float)(kOmega * kOmega) * d0;
         }
         // |t| >= |d0| except at t = 0, where the quick sum is exact as well
-        const df tp = quick_add_f(tt, d0);
-        const df u = one_minus(df_mul(tp, tc_inv));  // 1 - t'/t_c
+        const df tp = quick_add_f_u(tt, d0);
+        const df u = one_minus_u(df_mul_u(tp, tc_inv));  // 1 - t'/t_c
         if (!(u.hi > 0.f)) {
           act = false;
         } else {
           // y = u^(-1/8): FP32 seed, one Newton step with a double-float residual
           const float y0 = pow_m18(u.hi);
           const df y02 = two_prod(y0, y0);
-          const df y08 = df_sqr(df_sqr(y02));
-          const df p = df_mul(u, y08);
+          const df y08 = df_sqr_u(df_sqr_u(y02));
+          const df p = df_mul_u(u, y08);
           const float r = __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo);
           const df y = quick_two_sum(y0, y0 * r * 0.125f);
-          const df y2 = df_sqr(y);
-          const df y3 = df_mul(y2, y);
-          const float c2y2 = C2 * y2.hi;
-          const df onec = two_sum(1.0f, c2y2);
-          const df fs = df_mul(df_mul(F0, y3), onec);  // source-frame frequency
-          const df f = quick_add_f(fs, fs.hi * d1);     // detector frame: f (1 + dt'/dt - 1)
+          // products that only feed further df arithmetic stay unnormalised (~46 bits);
+          // their hi words enter FP32 terms (fdot, amplitude) only
+          const df y2 = df_sqr_u(y);
+          const df y3 = df_mul_u(y2, y);
+          const df c2y2d = df_mul_u(C2, y2);
+          const float c2y2 = c2y2d.hi;
+          const df onec = one_plus_u(c2y2d);  // |C2 y^2| < 1
+          const df fs = df_mul_u(df_mul_u(F0, y3), onec);  // source-frame frequency
+          const df f = quick_add_f_u(fs, fs.hi * d1);   // detector frame: f (1 + dt'/dt - 1)
           const float y2f = y2.hi, y3f = y3.hi;
-          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
+          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
           const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
           const df x = df_mul(f, dTd);  // f_nm / df
           // the window test first on the float, so that x is small enough for the
@@ -207,8 +211,8 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             // phase in cycles: K - P5 u^(5/8) - P3 u^(3/8) = K - u y^3 (P5 + P3 y^2)
             // (u^(5/8) = u y^3, u^(3/8) = u y^5); the fractional part is taken in two
             // steps because the hi word can be an integer-valued float (|Phi| > 2^23)
-            const df u58 = df_mul(u, y3);
-            const df ph = df_sub(Kc, df_mul(u58, df_add(P5, df_mul(P3, y2))));
+            const df u58 = df_mul_u(u, y3);
+            const df ph = df_sub_u(Kc, df_mul_u(u58, df_add_u(P5, df_mul_u(P3, y2))));
             float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
             cyc = __fsub_rn(cyc, rint_small(cyc));
             // cyc is in [-1/2, 1/2]: the hardware sine/cosine are accurate to ~4e-7 there

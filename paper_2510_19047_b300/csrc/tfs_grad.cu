@@ -310,8 +310,9 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   const df tc_inv = {c0.x, c0.y}, F0 = {c0.z, c0.w};
   const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
   const df Kc = {c2.x, c2.y};
-  const float dopc = c2.z, dops = c3.x;
-  const float C2 = c3.z, fd_k = c3.w;
+  const float dopc = c2.z, dops = c2.w;
+  const df C2 = {c3.x, c3.y};
+  const float fd_k = c3.z;
   const TrancheF tr = a.tabF[m];
   float d0 = 0.f, d1 = 0.f, d2 = 0.f;
   if (a.response) {
@@ -330,12 +331,13 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   const df y = quick_two_sum(y0, y0 * r * 0.125f);
   const df y2 = df_sqr(y);
   const df y3 = df_mul(y2, y);
-  const float c2y2 = C2 * y2.hi;
-  const df onec = two_sum(1.0f, c2y2);
+  const df c2y2d = df_mul(C2, y2);
+  const float c2y2 = c2y2d.hi;
+  const df onec = df_add(df{1.0f, 0.0f}, c2y2d);
   const df fs = df_mul(df_mul(F0, y3), onec);
   const df f = df_add_f(fs, fs.hi * d1);
   const float y2f = y2.hi, y3f = y3.hi;
-  const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2, y2f, 3.0f);
+  const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
   const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
   const df x = df_mul(f, df{a.mc.dT_hi, a.mc.dT_lo});
   const bool inband = x.hi > (float)kNFHalf && x.hi < a.mc.x_hi;

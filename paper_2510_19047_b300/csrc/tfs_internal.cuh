@@ -77,8 +77,10 @@ struct __align__(16) TplMix {
   float P5_hi, P5_lo;        // P5 / 2 pi (cycles)
   float P3_hi, P3_lo;        // P3 / 2 pi
   float K_hi, K_lo;          // frac(phi0 / 2 pi + P5 / 2 pi + P3 / 2 pi): Phi = K - P5 u^5/8 - P3 u^3/8
-  float dopc_hi, dopc_lo, dops_hi, dops_lo;
-  float C2, fd_k;            // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
+  float dopc, dops;          // barycentre delay coefficients (FP32: |delay| <= 500 s)
+  float C2_hi, C2_lo;        // f_src = F0 y^3 (1 + C2 y^2); C2 y^2 moves f_nm / df by
+                             // up to ~1e4 bins, so C2 is kept to double-float precision
+  float fd_k, pad0;          // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
   float pp[6], px[6];
   float nx, ny, nz, pad;     // direction to the source (TDI response)
   int m_lo, m_hi;
@@ -151,6 +153,42 @@ __device__ __forceinline__ df df_mul_f(df x, float b) {
   float e = __fmaf_rn(x.hi, b, -p);
   e = __fmaf_rn(x.lo, b, e);
   return quick_two_sum(p, e);
+}
+// Products without the final renormalisation: (p, e) with p = fl(x.hi y.hi) and e the
+// rest, |e| <~ 2^-22 |p|. Such a pair keeps ~46 bits and is a valid operand of the df
+// operations above; it is used where the result only feeds further df arithmetic
+// (a comparison or rounding of the value needs the normalised form).
+__device__ __forceinline__ df df_mul_u(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df{p, e};
+}
+__device__ __forceinline__ df df_sqr_u(df x) {
+  const float p = __fmul_rn(x.hi, x.hi);
+  float e = __fmaf_rn(x.hi, x.hi, -p);
+  e = __fmaf_rn(2.0f * x.hi, x.lo, e);
+  return df{p, e};
+}
+// Sums without the final renormalisation (operands as in df_add / quick_add_f / one_minus).
+__device__ __forceinline__ df df_add_u(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+__device__ __forceinline__ df df_sub_u(df x, df y) { return df_add_u(x, df{-y.hi, -y.lo}); }
+__device__ __forceinline__ df quick_add_f_u(df x, float b) {
+  const df s = quick_two_sum(x.hi, b);
+  return df{s.hi, __fadd_rn(s.lo, x.lo)};
+}
+// 1 + x for |x.hi| <= 1
+__device__ __forceinline__ df one_plus_u(df x) {
+  const df s = quick_two_sum(1.0f, x.hi);
+  return df{s.hi, __fadd_rn(s.lo, x.lo)};
+}
+__device__ __forceinline__ df one_minus_u(df x) {
+  const df s = quick_two_sum(1.0f, -x.hi);
+  return df{s.hi, __fsub_rn(s.lo, x.lo)};
 }
 __device__ __forceinline__ df df_sqr(df x) {
   float p = __fmul_rn(x.hi, x.hi);

@@ -115,6 +115,10 @@ cudaError_t launch_pso_init(const PsoArgs& a, int n_sm, cudaStream_t s);
 cudaError_t launch_pso_step(const PsoArgs& a, const double* f, int64_t iter, int move,
                             cudaStream_t s);
 
+// Noise-only data grid from the weights w (FP64 [c][m][k]) into d_re, d_im.
+cudaError_t launch_noise(int64_t n, const double* w, double df, uint64_t seed, double* d_re,
+                         double* d_im, int n_sm, cudaStream_t s);
+
 // One refinement step of n candidates (device pointers; see k_refine_update).
 struct RefineArgs {
   int64_t n;

@@ -186,6 +186,46 @@ cudaError_t launch_pso_step(const PsoArgs& a, const double* f, int64_t iter, int
 }
 
 // ---------------------------------------------------------------------------------
+// Noise-only data for false-alarm backgrounds (Sec. "False alarm probabilities": the
+// background comes from independent noise-only realisations): per pixel
+//   d~ = sqrt(S / (4 df)) (g1 + i g2),  S = 1/w (d~ = 0 where w = 0),
+// so that E|d~|^2 = S / (2 df), with g1, g2 independent standard normals from the
+// Box-Muller transform of the two uniforms of one Philox4x32-10 block keyed by the seed,
+// counter (pixel index low, high, 0, kNoiseTag).
+// ---------------------------------------------------------------------------------
+constexpr uint32_t kNoiseTag = 0x4E4F4953u;
+
+__global__ void k_noise(int64_t n, const double* __restrict__ w, double df, uint2 key,
+                        double* __restrict__ d_re, double* __restrict__ d_im) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double u1, u2;
+    philox_uniform2(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, kNoiseTag), key,
+                    u1, u2);
+    const double wi = w[i];
+    double re = 0.0, im = 0.0;
+    if (wi > 0.0) {
+      const double r = sqrt(-2.0 * log(1.0 - u1)) * sqrt(1.0 / (4.0 * df * wi));
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      re = r * cs;
+      im = r * sn;
+    }
+    d_re[i] = re;
+    d_im[i] = im;
+  }
+}
+
+cudaError_t launch_noise(int64_t n, const double* w, double df, uint64_t seed, double* d_re,
+                         double* d_im, int n_sm, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 16);
+  k_noise<<<blocks, 256, 0, s>>>(n, w, df, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)),
+                                d_re, d_im);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // Refinement by projected gradient ascent, one thread per candidate. With U and g the
 // statistic and its gradient at the current parameters theta:
 //   accept when U >= U_best (theta_best, g_best, U_best take the current values, the

@@ -233,10 +233,11 @@ __device__ TplMix mix_of(const TplConst& c) {
   // Phi/2pi = phi0/2pi + P5 (1 - u^5/8) + P3 (1 - u^3/8) = K - P5 u^5/8 - P3 u^3/8; the
   // integer part of K is irrelevant
   split(dd_frac(const_cycles(c)), t.K_hi, t.K_lo);
-  split(c.dop_c, t.dopc_hi, t.dopc_lo);
-  split(c.dop_s, t.dops_hi, t.dops_lo);
-  t.C2 = (float)c.C2;
+  t.dopc = (float)c.dop_c;
+  t.dops = (float)c.dop_s;
+  split(c.C2, t.C2_hi, t.C2_lo);
   t.fd_k = (float)(c.F0 / (8.0 * c.tc));
+  t.pad0 = 0.0f;
   for (int k = 0; k < 6; ++k) {
     t.pp[k] = (float)c.pp[k];
     t.px[k] = (float)c.px[k];

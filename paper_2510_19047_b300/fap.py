@@ -10,45 +10,29 @@ distribution p0 of the search maximum of Upsilon, and two fits extrapolate its t
   optimistic estimate.
 
 background_maxima() runs one eval_statistic call per realisation over a template bank
-(a search tile). The noise pixels are drawn on the device with the data's convention,
-E|n|^2 = S / (2 delta f). The fits are plain maximum-likelihood estimates on the host.
+(a search tile). The noise pixels are drawn by the library on the device with the data's
+convention, E|n|^2 = S / (2 delta f). The fits are plain maximum-likelihood estimates on
+the host.
 """
 import math
 
 import numpy as np
 
 
-def noise_realisation(inv_psd, df, seed, device="cuda"):
-    """Complex Gaussian TF noise with E|n|^2 = S/(2 df), S = 1/w (zero where w = 0),
-    drawn on `device` from a seeded generator. Returns a complex128 tensor."""
-    import torch
-    w = inv_psd if isinstance(inv_psd, torch.Tensor) else torch.from_numpy(np.asarray(inv_psd))
-    w = w.to(device=device, dtype=torch.float64)
-    S = torch.where(w > 0, 1.0 / torch.where(w > 0, w, torch.ones_like(w)), torch.zeros_like(w))
-    sd = torch.sqrt(S / (4.0 * df))
-    g = torch.Generator(device=device)
-    g.manual_seed(int(seed))
-    re = torch.randn(w.shape, generator=g, dtype=torch.float64, device=device)
-    im = torch.randn(w.shape, generator=g, dtype=torch.float64, device=device)
-    return torch.complex(re * sd, im * sd)
-
-
 def background_maxima(tfs, D, theta, n_seg, n_real, seed=0):
     """max over the bank `theta` [8, n] of Upsilon_{n_seg} in each of n_real noise-only
-    realisations of the grid D (its weights, mask and timing). Returns float64 [n_real]."""
-    import torch
-    dev = torch.device("cuda", tfs.device)
-    th = theta if isinstance(theta, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(theta))
-    th = th.to(dev, dtype=torch.float64).contiguous()
-    w = torch.from_numpy(np.ascontiguousarray(D.w)).to(dev)
-    mask = torch.from_numpy(np.ascontiguousarray(D.mask, dtype=np.uint8)).to(dev)
+    realisations of the grid D (its weights, mask and timing), drawn by the library
+    (tfs_noise_realisation, seeds seed .. seed + n_real - 1). The context's data are
+    replaced. Returns float64 [n_real]."""
+    th = np.ascontiguousarray(theta.cpu().numpy() if hasattr(theta, "cpu") else theta,
+                              dtype=np.float64)
+    tfs.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    tfs.set_noise_weights(D.w, D.mask)
     out = np.empty(n_real)
     for r in range(n_real):
-        n = noise_realisation(w, 1.0 / D.dT, seed + r, dev)
-        tfs.load_tf_data(n, D.dt, D.dT, D.t0)
-        tfs.set_noise_weights(w, mask)
+        tfs.noise_realisation(seed + r)
         st, _, _ = tfs.eval_statistic(th, n_seg)
-        out[r] = float(st.max())
+        out[r] = float(np.max(st))
     return out
 
 

@@ -129,3 +129,26 @@ def refine_step(stat, grad, theta, best_theta, best_grad, best_stat, eta, sigma,
         else:
             nxt[q] = np.clip(nxt[q], lo[q], hi[q])
     return nxt, best_theta, best_grad, best_stat, eta, best_stat.mean()
+
+
+NOISE_TAG = 0x4E4F4953
+
+
+def noise(w, df, seed):
+    """The noise-only data tfs_noise_realisation draws: d~ = sqrt(S/(4 df)) (g1 + i g2),
+    S = 1/w (0 where w = 0), g1 + i g2 = sqrt(-2 ln(1 - a)) e^{2 pi i b} from the two
+    uniforms of one Philox4x32-10 block with counter (pixel index low, high, 0, tag)."""
+    w = np.asarray(w, dtype=np.float64)
+    n = w.size
+    i = np.arange(n, dtype=np.uint64)
+    c = np.zeros((n, 4), dtype=np.uint64)
+    c[:, 0] = i & MASK
+    c[:, 1] = i >> np.uint64(32)
+    c[:, 3] = NOISE_TAG
+    a, b = uniform2(c, key_of(seed))
+    wf = w.ravel()
+    pos = wf > 0
+    r = np.zeros(n)
+    r[pos] = np.sqrt(-2.0 * np.log(1.0 - a[pos])) * np.sqrt(1.0 / (4.0 * df * wf[pos]))
+    d = r * np.exp(2j * np.pi * b)
+    return d.reshape(w.shape)

@@ -63,20 +63,19 @@ def test_tail_of_a_known_exponential_maximum():
 
 @pytest.mark.gpu
 def test_device_noise_gives_expected_statistic_mean():
-    """One template's Upsilon over noise-only realisations drawn by the device generator
-    has mean 2 N_eff (Upsilon is chi^2 with 2 N_eff degrees of freedom in noise)."""
+    """One template's Upsilon over noise-only realisations drawn by the library
+    (tfs_noise_realisation) has mean 2 N_eff (Upsilon is chi^2 with 2 N_eff degrees of
+    freedom in noise)."""
     from paper_2510_19047_b300 import synth
     from paper_2510_19047_b300.binding import TFS
     D = synth.week_one_channel(seed=0)
     c = TFS(0, pn_order=0, response=0, path="mixed", pixel="f32")
+    c.load_tf_data(D.d, D.dt, D.dT)
+    c.set_noise_weights(D.w)
     th = synth.week_bank(8, 0)
     vals, neff = [], None
-    import torch
-    w = torch.from_numpy(D.w).cuda()
     for r in range(200):
-        n = fap.noise_realisation(w, 1.0 / D.dT, seed=1000 + r)
-        c.load_tf_data(n, D.dt, D.dT)
-        c.set_noise_weights(w)
+        c.noise_realisation(1000 + r)
         s, ne, _ = c.eval_statistic(th, 8)
         vals.append(s)
         neff = ne
@@ -86,3 +85,28 @@ def test_device_noise_gives_expected_statistic_mean():
     assert np.all(np.abs(v.mean(0) - expect) < 4 * sd), (v.mean(0), expect)
     mx = fap.background_maxima(c, D, th, 8, n_real=5, seed=7)
     assert mx.shape == (5,) and np.all(np.isfinite(mx)) and np.all(mx > 0)
+
+
+@pytest.mark.gpu
+def test_device_noise_matches_its_definition():
+    """The realisation tfs_noise_realisation draws is the one its definition gives
+    (restated in NumPy: Philox4x32-10, Box-Muller, S/(4 df) scaling): the FP64 statistic
+    of the library's realisation equals the oracle's statistic of the NumPy one within
+    the FP64 bound, on the 45-day A/E grid with gaps and PSD modulation."""
+    import oracle
+    import search_ref as R
+    from paper_2510_19047_b300 import synth
+    from paper_2510_19047_b300.binding import TFS
+    D = synth.two_year_two_channel(seed=77, n_inj=3, n_tranche=384, L=2048)
+    th = synth.two_year_bank(64, seed=8)
+    c = TFS(0, path="fp64", pn_order=1, response=1)
+    c.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    c.set_noise_weights(D.w, D.mask)
+    for seed in (3, 2**40 + 5):
+        c.noise_realisation(seed)
+        got, ne, _ = c.eval_statistic(th, 8)
+        dn = R.noise(D.w, 1.0 / D.dT, seed)
+        ref, rne, _, _ = oracle.statistic(dn, D.w, D.mask, th, 8, D.dT, pn_order=1, response=1)
+        m = ref > 0
+        assert np.max(np.abs(got[m] - ref[m]) / ref[m]) < 1e-10
+        assert np.array_equal(ne, rne)

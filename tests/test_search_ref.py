@@ -29,3 +29,23 @@ def test_uniform_draws_are_uniform():
         hist = np.histogram(u, bins=20, range=(0, 1))[0]
         assert np.all(np.abs(hist - n / 20) < 5 * np.sqrt(n / 20))
     assert abs(np.corrcoef(a, b)[0, 1]) < 4 / np.sqrt(n)
+
+
+def test_noise_restatement_has_the_data_convention():
+    """E|d~|^2 = S / (2 df) with S = 1/w, real and imaginary parts independent and
+    Gaussian; zero where the weight is zero."""
+    from search_ref import noise
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0.5, 2.0, (2, 50, 2000))
+    w[:, 7, :] = 0.0
+    df = 1e-4
+    d = noise(w, df, seed=11)
+    assert np.all(d[:, 7, :] == 0)
+    m = w > 0
+    z = d[m] * np.sqrt(2.0 * df * w[m])  # unit-variance complex normal
+    n = z.size
+    assert abs(np.mean(np.abs(z) ** 2) - 1.0) < 5 * np.sqrt(1.0 / n)
+    for part in (z.real, z.imag):
+        assert abs(part.mean()) < 5 * np.sqrt(0.5 / n)
+        assert abs(np.mean(part ** 4) / np.mean(part ** 2) ** 2 - 3.0) < 0.05  # Gaussian
+    assert abs(np.corrcoef(z.real, z.imag)[0, 1]) < 5 / np.sqrt(n)
