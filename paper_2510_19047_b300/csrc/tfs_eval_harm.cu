@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         const df P5 = {c1.x, c1.y}, P3 = {c1.z, c1.w};
         const float dopc = c2.z, dops = c2.w;
         const df C2 = {c3.x, c3.y};
-        const float fd_k = c3.z;
+        const float fd_k = c3.z, C2x5 = c3.w;
         const TrancheF tr = a.tabF[m];
         tk.ca = tr.ca_hi;
         tk.sa = tr.sa_hi;
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
           const df fs = df_mul_u(df_mul_u(F0, y3), one_plus_u(c2y2d));
           const df f = quick_add_f(fs, fs.hi * d1);
           const float y2f = y2.hi, y3f = y3.hi;
-          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
+          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(C2x5, y2f, 3.0f);
           tk.fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
           tk.x = df_mul(f, dTd);
           tk.f = f.hi;

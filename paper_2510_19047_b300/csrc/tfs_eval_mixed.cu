@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
   // grid constants as FP32 launch parameters: derived from the FP64 grid here, the
   // compiler re-derives them inside the tranche loop on the narrow FP64 pipe
   const df dTd = {a.mc.dT_hi, a.mc.dT_lo};
-  const float dTf = a.mc.dTf;
+  const float dTf = a.mc.dTf, dTf2 = dTf * dTf;
   const float sig_k = a.mc.sig_k;  // sigma = df sqrt(2/fdot)
   const float ncomp = a.mc.ncomp;  // fdot > 10 df / dT: non-compact
   // FP32 pixels: the bin next to f_nm below it (x1 = f_nm/df - (k_c - 1)) and Psi are
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
         const df Kc = {c2.x, c2.y};
         const float dopc = c2.z, dops = c2.w;
         const df C2 = {c3.x, c3.y};
-        const float fd_k = c3.z;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
+        const float fd_k = c3.z, C2x5 = c3.w;  // fdot_src = fd_k y^11 (3 + 5 C2 y^2)
         const TrancheF tr = a.tabF[m];
         const df tt = {tr.t_hi, tr.t_lo};
         // barycentre delay n.r/c (|d0| <= 500 s) in FP32: its rounding, < 1e-4 s, moves
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
           const df fs = df_mul_u(df_mul_u(F0, y3), onec);  // source-frame frequency
           const df f = quick_add_f_u(fs, fs.hi * d1);   // detector frame: f (1 + dt'/dt - 1)
           const float y2f = y2.hi, y3f = y3.hi;
-          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
+          const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(C2x5, y2f, 3.0f);
           const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
           const df x = df_mul(f, dTd);  // f_nm / df
           // the window test first on the float, so that x is small enough for the
@@ -226,10 +226,10 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             Tr0 = Tr1 = amp_c;
             Ti0 = Ti1 = amp_s;
             sig = sig_k * rsqrt_approx(fdot);
-            eps = fdot * dTf * dTf;  // fdot dT / df: sweep width in bins
-            // Psi / pi = 2 aa + eps = 2 rb + eps (mod 2), reduced to [-1, 1]
-            const float psi = fmaf(2.0f, kNear ? rb : aa, eps);
-            __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &spsi, &cpsi);
+            eps = fdot * dTf2;  // fdot dT / df: sweep width in bins
+            // Psi / 2 pi = aa + eps / 2 = rb + eps / 2 (mod 1), reduced to [-1/2, 1/2]
+            const float hpsi = fmaf(0.5f, eps, kNear ? rb : aa);
+            __sincosf(6.283185307f * (hpsi - rint_small(hpsi)), &spsi, &cpsi);
             if (a.response) {
               float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
               // the polarisation tensors are read here, per tranche, from L1 rather than

@@ -312,7 +312,7 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   const df Kc = {c2.x, c2.y};
   const float dopc = c2.z, dops = c2.w;
   const df C2 = {c3.x, c3.y};
-  const float fd_k = c3.z;
+  const float fd_k = c3.z, C2x5 = c3.w;
   const TrancheF tr = a.tabF[m];
   float d0 = 0.f, d1 = 0.f, d2 = 0.f;
   if (a.response) {
@@ -337,7 +337,7 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   const df fs = df_mul(df_mul(F0, y3), onec);
   const df f = df_add_f(fs, fs.hi * d1);
   const float y2f = y2.hi, y3f = y3.hi;
-  const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(5.0f * C2.hi, y2f, 3.0f);
+  const float fds = fd_k * (y3f * y3f * y3f * y2f) * fmaf(C2x5, y2f, 3.0f);
   const float fdot = fds * (1.0f + d1) * (1.0f + d1) + fs.hi * d2;
   const df x = df_mul(f, df{a.mc.dT_hi, a.mc.dT_lo});
   const bool inband = x.hi > (float)kNFHalf && x.hi < a.mc.x_hi;

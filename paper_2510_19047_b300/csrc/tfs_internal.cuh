@@ -80,7 +80,7 @@ struct __align__(16) TplMix {
   float dopc, dops;          // barycentre delay coefficients (FP32: |delay| <= 500 s)
   float C2_hi, C2_lo;        // f_src = F0 y^3 (1 + C2 y^2); C2 y^2 moves f_nm / df by
                              // up to ~1e4 bins, so C2 is kept to double-float precision
-  float fd_k, pad0;          // fdot_src = fd_k y^11 (3 + 5 C2 y^2), fd_k = F0 / (8 t_c)
+  float fd_k, C2x5;          // fdot_src = fd_k y^11 (3 + C2x5 y^2), fd_k = F0 / (8 t_c), C2x5 = 5 C2
   float pp[6], px[6];
   float nx, ny, nz, pad;     // direction to the source (TDI response)
   int m_lo, m_hi;

@@ -237,7 +237,7 @@ __device__ TplMix mix_of(const TplConst& c) {
   t.dops = (float)c.dop_s;
   split(c.C2, t.C2_hi, t.C2_lo);
   t.fd_k = (float)(c.F0 / (8.0 * c.tc));
-  t.pad0 = 0.0f;
+  t.C2x5 = (float)(5.0 * c.C2);
   for (int k = 0; k < 6; ++k) {
     t.pp[k] = (float)c.pp[k];
     t.px[k] = (float)c.px[k];
