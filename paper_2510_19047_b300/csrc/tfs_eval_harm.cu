@@ -312,13 +312,17 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
               const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
               const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
               const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+              // (F+_A, F+_E) and (Fx_A, Fx_E) as packed pairs
+              float2 fp = make_float2(0.f, 0.f), fx = make_float2(0.f, 0.f);
 #pragma unroll
               for (int q = 0; q < 6; ++q) {
-                tk.fpA = fmaf(tr.DA[q], pp[q], tk.fpA);
-                tk.fxA = fmaf(tr.DA[q], px[q], tk.fxA);
-                tk.fpE = fmaf(tr.DE[q], pp[q], tk.fpE);
-                tk.fxE = fmaf(tr.DE[q], px[q], tk.fxE);
+                fp = __ffma2_rn(tr.D[q], make_float2(pp[q], pp[q]), fp);
+                fx = __ffma2_rn(tr.D[q], make_float2(px[q], px[q]), fx);
               }
+              tk.fpA = fp.x;
+              tk.fpE = fp.y;
+              tk.fxA = fx.x;
+              tk.fxE = fx.y;
             }
           }
         }

@@ -231,34 +231,35 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             const float hpsi = fmaf(0.5f, eps, kNear ? rb : aa);
             __sincosf(6.283185307f * (hpsi - rint_small(hpsi)), &spsi, &cpsi);
             if (a.response) {
-              float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
+              // (F+_A, F+_E) and (Fx_A, Fx_E) as packed pairs
+              float2 fp = make_float2(0.f, 0.f), fx = make_float2(0.f, 0.f);
               // the polarisation tensors are read here, per tranche, from L1 rather than
               // held in registers across the tranche loop
               const float4* pq = reinterpret_cast<const float4*>(a.tplm[idx].pp);
               const float4 q0 = ldg_nc4(pq), q1 = ldg_nc4(pq + 1), q2 = ldg_nc4(pq + 2);
               const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
               const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-#pragma unroll
-              for (int q = 0; q < 6; ++q) {
-                fpA = fmaf(tr.DA[q], pp[q], fpA);
-                fxA = fmaf(tr.DA[q], px[q], fxA);
-                fpE = fmaf(tr.DE[q], pp[q], fpE);
-                fxE = fmaf(tr.DE[q], px[q], fxE);
-              }
               if (TDI) {  // TDI-1.5 transfer at (t_nm, f_nm)
                 const float4 nq = ldg_nc4(pq + 3);  // (nx, ny, nz, pad)
                 Cplx<float> TA, TE;
                 tdi_transfer<float>(f.hi, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
-                fpA = TA.re;
-                fxA = -TA.im;
-                fpE = TE.re;
-                fxE = -TE.im;
+                fp = make_float2(TA.re, TE.re);
+                fx = make_float2(-TA.im, -TE.im);
+              } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                  fp = __ffma2_rn(tr.D[q], make_float2(pp[q], pp[q]), fp);
+                  fx = __ffma2_rn(tr.D[q], make_float2(px[q], px[q]), fx);
+                }
               }
-              // (F+ - i Fx)(amp_c + i amp_s)
-              Tr0 = fmaf(fpA, amp_c, fxA * amp_s);
-              Ti0 = fmaf(fpA, amp_s, -fxA * amp_c);
-              Tr1 = fmaf(fpE, amp_c, fxE * amp_s);
-              Ti1 = fmaf(fpE, amp_s, -fxE * amp_c);
+              // (F+ - i Fx)(amp_c + i amp_s), both channels at once
+              const float2 ac = make_float2(amp_c, amp_c), as = make_float2(amp_s, amp_s);
+              const float2 Tr = __ffma2_rn(fp, ac, __fmul2_rn(fx, as));
+              const float2 Ti = __ffma2_rn(fp, as, __fmul2_rn(fx, make_float2(-amp_c, -amp_c)));
+              Tr0 = Tr.x;
+              Tr1 = Tr.y;
+              Ti0 = Ti.x;
+              Ti1 = Ti.y;
             }
             if (kR16) {
               Tr0 = round_f16(Tr0);

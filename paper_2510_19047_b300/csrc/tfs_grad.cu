@@ -393,10 +393,10 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
       float fpA = 0.f, fxA = 0.f, fpE = 0.f, fxE = 0.f;
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        fpA = fmaf(tr.DA[q], pp[q], fpA);
-        fxA = fmaf(tr.DA[q], px[q], fxA);
-        fpE = fmaf(tr.DE[q], pp[q], fpE);
-        fxE = fmaf(tr.DE[q], px[q], fxE);
+        fpA = fmaf(tr.D[q].x, pp[q], fpA);
+        fxA = fmaf(tr.D[q].x, px[q], fxA);
+        fpE = fmaf(tr.D[q].y, pp[q], fpE);
+        fxE = fmaf(tr.D[q].y, px[q], fxE);
       }
       k.Tr[0] = fpA;
       k.Ti[0] = -fxA;
@@ -467,8 +467,8 @@ __device__ __forceinline__ void track_adjoint(const GradArgs& a, const SrcF& s, 
     if (a.response != 2) {  // T_alpha = D_alpha : (pp - i px); TDI: tdi_adjoint
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
-        g[8 + q] = cTr[0] * tr.DA[q] + cTr[1] * tr.DE[q];
-        g[14 + q] = -(cTi[0] * tr.DA[q] + cTi[1] * tr.DE[q]);
+        g[8 + q] = cTr[0] * tr.D[q].x + cTr[1] * tr.D[q].y;
+        g[14 + q] = -(cTi[0] * tr.D[q].x + cTi[1] * tr.D[q].y);
       }
     }
   }

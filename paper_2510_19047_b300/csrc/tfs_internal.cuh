@@ -46,11 +46,13 @@ struct TrancheD {
   double DA[6], DE[6];
   double pad;
 };
-// Same for the mixed path: double-float time and orbital cos/sin, FP32 tensors.
+// Same for the mixed path: double-float time and orbital cos/sin, FP32 tensors with
+// the two channels' components paired, D[q] = (DA[q], DE[q]), so that both channels'
+// antenna patterns are formed with packed f32x2 FMAs.
 struct __align__(16) TrancheF {
   float t_hi, t_lo, ca_hi, ca_lo;
   float sa_hi, sa_lo, pad0, pad1;
-  float DA[6], DE[6];
+  float2 D[6];
 };
 
 // Per-template constants, computed once in FP64 by the set-up kernel.

@@ -77,8 +77,7 @@ __global__ void k_tranche_table(GridDesc g, TrancheD* td, TrancheF* tf) {
   f.sa_lo = (float)(d.sa - (double)f.sa_hi);
   f.pad0 = f.pad1 = 0.0f;
   for (int p = 0; p < 6; ++p) {
-    f.DA[p] = (float)d.DA[p];
-    f.DE[p] = (float)d.DE[p];
+    f.D[p] = make_float2((float)d.DA[p], (float)d.DE[p]);
   }
   tf[m] = f;
 }
