@@ -84,7 +84,7 @@ __device__ __forceinline__ float bin_x1(const HarmM& q, float j) {
   return NEAR && j == -1.0f ? q.a1 : q.aa - j;
 }
 
-// NEAR (FP32 pixels): the bin below f_nm (x1 = x - (k_c - 1)) and Psi are formed from
+// NEAR (every pixel type): the bin below f_nm (x1 = x - (k_c - 1)) and Psi are formed from
 // rb = x - rint(x), to full relative precision when f_nm is just above a bin, as in the
 // single-mode kernel.
 template <bool TDI, bool NEAR>
@@ -155,7 +155,7 @@ template <int NCH, int PIX, bool TDI>
 __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
                                           const float2* Kp, int m, float sig_k, float dTf) {
   using Ld = PixLoad<PIX>;
-  constexpr bool kNear = PIX == TFS_PIX_F32;
+  constexpr bool kNear = true;  // see harm_of
   const typename Ld::P* PX = (const typename Ld::P*)a.Umix;
   float N = 0.0f;
   for (int ha = 0; ha < a.harm.n; ++ha) {
@@ -200,7 +200,7 @@ template <int NCH, int PIX, int PITCH, bool TDI>
 __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
-  constexpr bool kNear = PIX == TFS_PIX_F32;  // see harm_of
+  constexpr bool kNear = true;  // see harm_of
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   // per warp: the fine-segment sums, then the lanes' TrackH (kTrkF x 32 floats)

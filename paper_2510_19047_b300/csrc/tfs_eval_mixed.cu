@@ -86,14 +86,12 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
   const float dTf = a.mc.dTf, dTf2 = dTf * dTf;
   const float sig_k = a.mc.sig_k;  // sigma = df sqrt(2/fdot)
   const float ncomp = a.mc.ncomp;  // fdot > 10 df / dT: non-compact
-  // FP32 pixels: the bin next to f_nm below it (x1 = f_nm/df - (k_c - 1)) and Psi are
-  // formed from rb = f_nm/df - rint(f_nm/df), which keeps full relative precision when
-  // f_nm is just above a bin. From aa = f_nm/df - k_c ~ -1 they keep ~6e-8 bins absolute
-  // only, against a sweep x2 - x1 = eps = 2/sigma^2 of ~5e-5 bins for slow chirps: a
-  // ~1e-3 relative error of W'' on that bin, invisible in one tranche's |Z|^2/N but not
-  // in a long segment's. The FP16/BF16 pixels' own rounding is larger, and those
-  // instantiations skip it (it costs registers in the hot loop).
-  constexpr bool kNear = PIX == TFS_PIX_F32;
+  // The bin next to f_nm below it (x1 = f_nm/df - (k_c - 1)) and Psi are formed from
+  // rb = f_nm/df - rint(f_nm/df), which keeps full relative precision when f_nm is just
+  // above a bin. From aa = f_nm/df - k_c ~ -1 they would keep ~6e-8 bins absolute only,
+  // against a sweep x2 - x1 = eps = 2/sigma^2 of ~5e-5 bins for slow chirps: a ~1e-3
+  // relative error of W'' on that bin, invisible in one tranche's |Z|^2/N but adding up
+  // over a long segment's coherent tranches.
   // precision-study pixel types: the template's values held at FP16 precision
   constexpr bool kR16 = PIX == TFS_PIX_F16_ALL || PIX == TFS_PIX_BF16_ALL;
 
@@ -194,15 +192,9 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
           float kcf = rint_small(inband ? x.hi : 0.0f);  // ceil(x) = rint(x) (+1 if below x)
           // rb = x - rint(x) in [-1/2, 1/2]; rb > 0 exactly when ceil(x) = rint(x) + 1
           const float rb = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
-          if (kNear) {
-            kc = int_small(rb > 0.f ? kcf + 1.0f : kcf);
-            aa = rb > 0.f ? rb - 1.0f : rb;  // f_nm/df - k_c, in (-1, 0]
-            a1 = rb > 0.f ? rb : rb + 1.0f;  // f_nm/df - (k_c - 1)
-          } else {
-            if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
-            kc = int_small(kcf);
-            aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);  // f_nm/df - k_c, in (-1, 0]
-          }
+          kc = int_small(rb > 0.f ? kcf + 1.0f : kcf);
+          aa = rb > 0.f ? rb - 1.0f : rb;  // f_nm/df - k_c, in (-1, 0]
+          a1 = rb > 0.f ? rb : rb + 1.0f;  // f_nm/df - (k_c - 1)
           if (!inband || !(fdot > 0.f) || kc - kNFHalf < 1 || kc + kNFHalf > g.n_bins - 1) {
             act = false;
           } else {
@@ -228,7 +220,7 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             sig = sig_k * rsqrt_approx(fdot);
             eps = fdot * dTf2;  // fdot dT / df: sweep width in bins
             // Psi / 2 pi = aa + eps / 2 = rb + eps / 2 (mod 1), reduced to [-1/2, 1/2]
-            const float hpsi = fmaf(0.5f, eps, kNear ? rb : aa);
+            const float hpsi = fmaf(0.5f, eps, rb);
             __sincosf(6.283185307f * (hpsi - rint_small(hpsi)), &spsi, &cpsi);
             if (a.response) {
               // (F+_A, F+_E) and (Fx_A, Fx_E) as packed pairs
@@ -301,32 +293,42 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
           // Only the two bins next to f_nm (jp = -1, 0) can need the general form:
           // fully unrolled, no per-bin branch. For jp >= 1, x2 < -r6 < 0; for jp <= -2,
           // x1 > 1 > r6; and only jp = 0 can hold the sweep (x1 = aa <= 0 < x2).
-          // pixel loads run kDepth bins ahead (a ring of packed elements in registers)
+          // The two general bins first, so that a1 and the general form's temporaries are
+          // dead before the asymptotic bins run; pixel loads of those run kDepth bins
+          // ahead (a ring of packed elements in registers, started before the general
+          // bins so that their latency is covered)
+          constexpr int kAsym = kNF - 2;
+          // the k-th asymptotic bin: 0..kNFHalf-2, then kNFHalf+1..kNF-1
+          auto asym_bin = [](int k) { return k < kNFHalf - 1 ? k : k + 2; };
           typename Ld::P ring[kDepth];
           ring[0] = cur;
 #pragma unroll
-          for (int q = 1; q < kDepth; ++q) ring[q] = Ld::raw(Pp + (int64_t)q * pitch);
+          for (int q = 1; q < kDepth; ++q) ring[q] = Ld::raw(Pp + (int64_t)asym_bin(q) * pitch);
+          {
+            const typename Ld::P g0 = Ld::raw(Pp + (int64_t)(kNFHalf - 1) * pitch);
+            const typename Ld::P g1 = Ld::raw(Pp + (int64_t)kNFHalf * pitch);
 #pragma unroll
-          for (int j = 0; j < kNF; ++j) {
-            const typename Ld::P pj = ring[j % kDepth];
-            if (j + kDepth < kNF) ring[j % kDepth] = Ld::raw(Pp + (int64_t)(j + kDepth) * pitch);
-            float2 cur_r, cur_i, cur_w;
-            Ld::cvt(pj, cur_r, cur_i, cur_w);
-            constexpr float kZero = 0.0f;
-            const float c = kZero + (float)(j - kNFHalf);
-            if (j == kNFHalf - 1 || j == kNFHalf) {
+            for (int h = 0; h < 2; ++h) {  // jp = -1 (x1 = a1), then jp = 0 (x1 = aa)
+              float2 cur_r, cur_i, cur_w;
+              Ld::cvt(h ? g1 : g0, cur_r, cur_i, cur_w);
               float wr, wi;
-              const float x1 = kNear && j == kNFHalf - 1 ? a1 : aa - c;
-              const float x2 = kNear && j == kNFHalf - 1 ? a1 + eps : ae - c;
-              w_general(x1, x2, sig, spi, cpsi, spsi, j == kNFHalf, wr, wi);
+              w_general(h ? aa : a1, h ? ae : a1 + eps, sig, spi, cpsi, spsi, h == 1, wr, wi);
               if (kR16) {
                 wr = round_f16(wr);
                 wi = round_f16(wi);
               }
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
-            } else {
-              acc_asym<kR16>(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
             }
+          }
+#pragma unroll
+          for (int k = 0; k < kAsym; ++k) {
+            const typename Ld::P pj = ring[k % kDepth];
+            if (k + kDepth < kAsym) ring[k % kDepth] = Ld::raw(Pp + (int64_t)asym_bin(k + kDepth) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(pj, cur_r, cur_i, cur_w);
+            constexpr float kZero = 0.0f;
+            const float c = kZero + (float)(asym_bin(k) - kNFHalf);
+            acc_asym<kR16>(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
           }
         } else {
           float jpf = -(float)kNFHalf;  // jp as an exact float (no int-to-float per bin)
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             const float x1 = xx.x, x2 = xx.y;
             if (jp >= JLO && jp <= JHI) {
               float wr, wi;
-              const bool near = kNear && jp == -1;
+              const bool near = jp == -1;
               w_general(near ? a1 : x1, near ? a1 + eps : x2, sig, spi, cpsi, spsi, true, wr, wi);
               if (kR16) {
                 wr = round_f16(wr);

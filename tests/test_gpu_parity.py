@@ -132,12 +132,11 @@ def test_reduced_precision_pixels_are_the_only_rounding(week, pixel):
     storage type: apart from storing u and w, they compute at FP32 accuracy. At N_seg = 1
     Upsilon is chi^2 with 2 degrees of freedom and can be ~1e-3 of its mean, so the pixel
     rounding alone moves it by up to ~7e-3 (FP16) or ~7e-2 (BF16) against the unrounded
-    oracle. These instantiations form the offset of the bin below f_nm from aa = f_nm/df
-    - k_c (the FP32-pixel one from x - rint(x), which costs them 4 % of kernel time),
-    which leaves W'' of that bin ~1e-3 off when f_nm sits just above it and the chirp is
-    slow. The error adds up over coherent tranches: measured 9.0e-5 at N_seg = 8 and
-    6.5e-4 at N_seg = 1 (5.8e-6 and 2.5e-5 with the x - rint(x) offsets), still ten times
-    below the pixel rounding; the bounds are 1e-4 for N_seg >= 64, 2e-4 at 8, 1e-3 at 1."""
+    oracle. Like the FP32-pixel instantiation they form the offset of the bin below f_nm
+    from x - rint(x), not from aa = f_nm/df - k_c ~ -1 (which would leave W'' of that bin
+    ~1e-3 off for slow chirps, adding up over coherent tranches to 9.0e-5 at N_seg = 8
+    and 6.5e-4 at N_seg = 1 on this grid); with it the FP32-arithmetic bound 1e-4 holds
+    at every N_seg (2.5e-5 at N_seg = 1 measured with FP32 pixels)."""
     th = synth.week_bank(1024, 0)
     lev = [512, 64, 8, 1]
     dq, wq = _round_pixels(week, pixel)
@@ -146,7 +145,7 @@ def test_reduced_precision_pixels_are_the_only_rounding(week, pixel):
     for i, L in enumerate(lev):
         ref = oracle.statistic(dq, wq, week.mask, th, L, week.dT)[0]
         mx, _ = rel_err(got[i], ref)
-        assert mx < {1: 1e-3, 8: 2e-4}.get(L, 1e-4), (pixel, L, mx)
+        assert mx < 1e-4, (pixel, L, mx)
 
 
 @pytest.mark.parametrize("path,pixel", CASES)
