@@ -165,7 +165,8 @@ def clocks_rejected(clocks):
 def kernel_source_sha1():
     """SHA-1 over the sources the statistic kernel is compiled from."""
     h = hashlib.sha1()
-    for f in ("tfs_eval_mixed.cu", "tfs_mixed_bins.cuh", "tfs_internal.cuh", "tfs_kernels.cuh"):
+    for f in ("tfs_eval_mixed.cu", "tfs_mixed_bins.cuh", "tfs_internal.cuh", "tfs_kernels.cuh",
+              "tfs_tdi.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2510_19047_b300", "csrc", f), "rb").read())
     return h.hexdigest()
 
