@@ -121,6 +121,7 @@ constexpr dd kCp1DD = {0.5729166666666666, 3.700743415417188e-17};        // 55 
 // residual is formed in dd, which squares the FP64 value's ~1e-16 relative error.
 struct ChirpDD {
   dd tc, P5, P3;
+  double F0, C2;  // f_src = F0 y^3 (1 + C2 y^2) (FP64)
 };
 
 TFS_HD ChirpDD chirp_dd(double Mc_sun, double eta, double f0, int pn_order) {
@@ -139,6 +140,8 @@ TFS_HD ChirpDD chirp_dd(double Mc_sun, double eta, double f0, int pn_order) {
     r.tc = dd_mul_d(w, 5.0 / 256.0);  // exact scaling
     r.P5 = dd_mul(dd_mul_d(k16Pi5DD, f0), r.tc);
     r.P3 = dd_from(0.0);
+    r.F0 = f0;
+    r.C2 = 0.0;
     return r;
   }
   // s = eta^(-3/5): s^5 eta^3 = 1
@@ -158,7 +161,7 @@ TFS_HD ChirpDD chirp_dd(double Mc_sun, double eta, double f0, int pn_order) {
     const double x2 = x0 * x0;
     const double dx = (x0 * x2 * (1.0 + cf.hi * x2) - yv.hi) / (x2 * (3.0 + 5.0 * cf.hi * x2));
     x0 -= dx;
-    if (fabs(dx) < 1e-16 * x0) break;
+    if (fabs(dx) < 1e-9 * x0) break;  // quadratic: the remaining error is ~1e-18 x0
   }
   {
     const dd x2 = dd_two_prod(x0, x0);
@@ -169,9 +172,16 @@ TFS_HD ChirpDD chirp_dd(double Mc_sun, double eta, double f0, int pn_order) {
     const dd x = dd_quick_two_sum(x0, -(g.hi + g.lo) / gp);
     const dd xx2 = dd_sqr(x), xx3 = dd_mul(xx2, x), xx4 = dd_sqr(xx2);
     const dd xx5 = dd_mul(xx4, x), xx8 = dd_sqr(xx4);
-    r.tc = dd_div(dd_mul_d(M, 5.0), dd_mul_d(xx8, eta));
-    r.P5 = dd_div(dd_from(2.0), dd_mul_d(xx5, eta));
-    r.P3 = dd_div(dd_mul_d(cp, 2.0), dd_mul_d(xx3, eta));
+    // t_c = 5 M / (eta x^8), P5 = 2 x^3 / (eta x^8), P3 = 2 cp x^5 / (eta x^8): one
+    // reciprocal
+    const dd rinv = dd_div(dd_from(1.0), dd_mul_d(xx8, eta));
+    r.tc = dd_mul(dd_mul_d(M, 5.0), rinv);
+    r.P5 = dd_mul_d(dd_mul(xx3, rinv), 2.0);
+    r.P3 = dd_mul(dd_mul_d(cp, 2.0), dd_mul(xx5, rinv));
+    // C2 = cf x^2; F0 = x^3 / (8 pi M) = f0 / (1 + C2) since x^3 (1 + cf x^2) = 8 pi M f0
+    const dd c2 = dd_mul(cf, xx2);
+    r.C2 = c2.hi + c2.lo;
+    r.F0 = f0 / (1.0 + r.C2);
   }
   return r;
 }

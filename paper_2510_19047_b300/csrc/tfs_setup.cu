@@ -205,7 +205,8 @@ __device__ double time_at_frequency(double tc, double F0, double C2, double f_ta
     const double gp = F0 * y2 * (3.0 + 5.0 * C2 * y2);
     const double dy = g / gp;
     y -= dy;
-    if (fabs(dy) < 1e-15 * y) break;
+    // quadratic convergence: after a step below 1e-9 y the error is ~1e-18 y
+    if (fabs(dy) < 1e-9 * y) break;
   }
   const double y2 = y * y, y4 = y2 * y2;
   return tc * (1.0 - 1.0 / (y4 * y4));
@@ -271,14 +272,15 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
     if (mix) mix[i] = mix_of(c);
     return;
   }
-  const SrcT<double> src = source_of<double>(th, pn_order);
+  SrcT<double> src;
+  source_geometry<double>(th, src);  // the chirp constants come from chirp_dd below
   // t_c, P5, P3 to double-double precision (their FP64 roundings would move a two-year
   // phase by ~1e-9 rad); the FP64 values are the dd values' leading parts
   const ChirpDD cd = chirp_dd(th[0], eta, f0, pn_order);
   c.tc = cd.tc.hi;
   c.tc_lo = cd.tc.lo;
-  c.F0 = src.F0;
-  c.C2 = src.C2;
+  c.F0 = cd.F0;
+  c.C2 = cd.C2;
   c.P5 = cd.P5.hi;
   c.P5_lo = cd.P5.lo;
   c.P3 = cd.P3.hi;
@@ -314,7 +316,7 @@ __global__ void k_setup(const double* __restrict__ theta, int64_t n, int pn_orde
   double f_start = c.F0;
   if (tp0 < c.tc) {
     const double u = 1.0 - tp0 / c.tc;
-    const double y = pow(u, -0.125), y2 = y * y;
+    const double y = 1.0 / sqrt(sqrt(sqrt(u))), y2 = y * y;  // u^(-1/8): a sort key only
     f_start = c.F0 * y * y2 * (1.0 + c.C2 * y2);
   }
   const int kc_lo = (int)fmin(65535.0, fmax(0.0, ceil(f_start / g.df)));

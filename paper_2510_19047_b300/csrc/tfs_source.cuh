@@ -71,10 +71,9 @@ struct SrcT {
   R nz;            // sin(beta)
 };
 
-// Template constants from theta = (Mc, eta, f0, phi0, lambda, beta, psi, iota).
+// The chirp constants (t_c, F0, C2, P5, P3) from (Mc, eta, f0).
 template <class R>
-__device__ SrcT<R> source_of(const R th[8], int pn_order) {
-  SrcT<R> s;
+__device__ void source_chirp(const R th[8], int pn_order, SrcT<R>& s) {
   const R Mc = th[0] * kGMsunS;
   const R eta = th[1];
   const R f0 = th[2];
@@ -112,6 +111,12 @@ __device__ SrcT<R> source_of(const R th[8], int pn_order) {
     s.P5 = (2.0 / eta) * r_pow(Theta0, 0.625);
     s.P3 = (2.0 / eta) * cp * r_pow(Theta0, 0.375);
   }
+}
+
+// The angle-dependent constants (phi0, polarisation tensors, barycentre delay, sky
+// direction) from (phi0, lambda, beta, psi, iota).
+template <class R>
+__device__ void source_geometry(const R th[8], SrcT<R>& s) {
   s.phi0 = th[3];
   R sl, cl, sb, cb, sps, cps;
   r_sincos(th[4], &sl, &cl);
@@ -135,6 +140,14 @@ __device__ SrcT<R> source_of(const R th[8], int pn_order) {
   s.dop_c = kAuS * cb * cl;
   s.dop_s = kAuS * cb * sl;
   s.nz = sb;
+}
+
+// Template constants from theta = (Mc, eta, f0, phi0, lambda, beta, psi, iota).
+template <class R>
+__device__ SrcT<R> source_of(const R th[8], int pn_order) {
+  SrcT<R> s;
+  source_chirp<R>(th, pn_order, s);
+  source_geometry<R>(th, s);
   return s;
 }
 
