@@ -350,20 +350,20 @@ def harmonics(args):
     out["cost_ratio_3h_vs_single_mode"] = (out["nu_half_1_3half"]["kernel_ms"]
                                            / out["single_mode_kernel"]["kernel_ms"])
     c.close()
-    # the paper's mapping (plain path) with the same harmonics on the first 20 000 templates
+    # the paper's mapping (plain path) with the same harmonics, timed over full waves of
+    # its one-thread-per-template launch (as the bench's plain leg)
+    import bench
     p = TFS(0, path="plain", pn_order=1, response=1, profile=1)
     p.load_tf_data(D.d, D.dt, D.dT)
     p.set_noise_weights(D.w, D.mask)
     p.set_harmonics(nu, cc)
-    sub = th[:, : min(n, 20_000)].contiguous()
-    p.eval_statistic(sub, lev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    p.eval_statistic(sub, lev)
-    e1.record()
-    e1.synchronize()
-    pv = sub.shape[1] / (e0.elapsed_time(e1) / 1000.0)
-    out["plain_nu_half_1_3half"] = {"templates_per_s": pv, "n_templates": sub.shape[1]}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    leg = bench._sized_leg(p, th, int(getattr(args, "plain_waves", 4)),
+                           float(getattr(args, "leg_seconds", 4.0)),
+                           torch.cuda.current_stream(), flush)
+    pv = leg["value"]
+    out["plain_nu_half_1_3half"] = {"templates_per_s": pv, "n_templates": leg["n_templates"],
+                                    "launch": leg["launch"]}
     out["mixed_vs_plain_3h"] = out["nu_half_1_3half"]["templates_per_s"] / pv
     p.close()
     return out

@@ -52,6 +52,7 @@ struct tfs_ctx {
   DevBuf u64, w64, u32, w32, Umix;
   DevBuf Ugrad;            // FP32 mixed-layout plane for the gradient (when Umix is not FP32)
   DevBuf gpart;            // the gradient's per-work-item partial sums (small batches)
+  DevBuf gsrc;             // the gradient's table of d(template constant)/d theta
   bool ugrad_ok = false;
   int pitch = 0;
   int pix_built = -1;
@@ -409,7 +410,7 @@ int tfs_destroy(tfs_ctx* c) {
   DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
-                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart,
+                   &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart, &c->gsrc,
                    &c->harmK, &c->tile_lo, &c->tile_hi, &c->rpart, &c->rdone, &c->tune_perm,
                    &c->live, &c->rank};
   for (DevBuf* b : all) buf_free(c, *b);
@@ -1074,12 +1075,14 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   int parts = 1;
   CUDA_TRY(c, grad_plan(c->opt.response, n_seg, c->n_sm, n_tpl, &parts));
   if (parts > 1 && (r = buf_ensure(c, c->gpart, (size_t)parts * 9 * n_tpl * 8))) return r;
+  if ((r = buf_ensure(c, c->gsrc, grad_src_bytes(n_tpl)))) return r;
   CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
                           (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
                           (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og,
-                          (unsigned*)c->counter.p, perm, parts, (double*)c->gpart.p, c->n_sm, s));
-  c->launches += parts > 1 ? 2 : 1;
+                          (unsigned*)c->counter.p, perm, parts, (double*)c->gpart.p,
+                          (double*)c->gsrc.p, c->n_sm, s));
+  c->launches += parts > 1 ? 3 : 2;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));

@@ -283,6 +283,7 @@ struct GradArgs {
   const int32_t* perm;  // queue order (longest templates first), or null for 0..n-1
   int parts;            // work items per template: contiguous groups of its segments
   double* part_out;     // parts > 1: [parts][9][n] partial (Upsilon, gradient) sums
+  const double* dsrc;   // [n][8][kSrcFields]: d(template constant)/d theta_p (k_grad_src)
 };
 
 // The track at the start of tranche m: the mixed kernel's double-float evaluation
@@ -537,12 +538,9 @@ __device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, con
 // Upsilon and the gradient are sums over segments, so the items' partial sums add up
 // to the template's (in a fixed order, by k_grad_reduce).
 template <bool TDI>
-__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, int lane, float4* seg,
-                                         double (*dsrc)[kSrcFields]) {
+__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, int lane, float4* seg) {
   const int nch = a.g.n_chan;
   const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
-  double th[8];
-  for (int p = 0; p < 8; ++p) th[p] = a.theta[(int64_t)p * a.n_tpl + i];
   const TplConst tc = a.tpl[i];
   const TplMix* cp = a.tplm + i;
   int mA = tc.m_lo, mB = tc.m_hi;
@@ -567,27 +565,6 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
   sf.P5c = df_make(tc.P5 * (0.5 / kPi));
   sf.P3c = df_make(tc.P3 * (0.5 / kPi));
   for (int q = lane; q < a.n_seg; q += 32) seg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  // derivatives of the template constants with respect to theta: lane p < 8 takes
-  // direction p (FP64 forward mode, once per template)
-  if (lane < 8) {
-    D1 thd[8];
-    for (int p = 0; p < 8; ++p) thd[p] = mk(th[p], p == lane ? 1.0 : 0.0);
-    const SrcT<D1> sd = source_of<D1>(thd, a.pn_order);
-    double* o = dsrc[lane];
-    o[0] = sd.tc.d;
-    o[1] = sd.F0.d;
-    o[2] = sd.C2.d;
-    o[3] = sd.P5.d;
-    o[4] = sd.P3.d;
-    o[5] = sd.phi0.d;
-    o[6] = sd.dop_c.d;
-    o[7] = sd.dop_s.d;
-    for (int q = 0; q < 6; ++q) {
-      o[8 + q] = sd.pp[q].d;
-      o[14 + q] = sd.px[q].d;
-    }
-    o[20] = sd.nz.d;
-  }
   __syncwarp();
 
   // ---- pass A: Z_n, N_n ----
@@ -898,7 +875,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
     if (k == 0) Gk += __shfl_sync(kFullG, Gown, kSrcFields);
     if (k == 3) Gk += __shfl_sync(kFullG, Gown, kSrcFields + 1);
     if (k == 4) Gk += __shfl_sync(kFullG, Gown, kSrcFields + 2);
-    if (lane < 8) v = fma(Gk, dsrc[lane][k], v);
+    if (lane < 8) v = fma(Gk, a.dsrc[((int64_t)i * 8 + lane) * kSrcFields + k], v);
   }
   if (lane < 8) {
     if (a.parts > 1)
@@ -907,6 +884,44 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
       a.out_grad[(int64_t)lane * a.n_tpl + i] = v;
   }
 }
+
+// Derivatives of the template constants with respect to theta (FP64 forward mode), one
+// thread per (template, direction p): computed once per call, not once per work item.
+__global__ void k_grad_src(const double* __restrict__ theta, int64_t n, int pn_order,
+                           double* __restrict__ dsrc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * 8) return;
+  const int64_t i = t >> 3;
+  const int p = (int)(t & 7);
+  D1 thd[8];
+  for (int q = 0; q < 8; ++q) thd[q] = mk(theta[(int64_t)q * n + i], q == p ? 1.0 : 0.0);
+  double* o = dsrc + t * kSrcFields;
+  // the chirp constants depend on (Mc, eta, f0) only, the rest on (phi0, lambda, beta,
+  // psi, iota) only: each direction evaluates its own half
+  SrcT<D1> sd;
+  if (p < 3) {
+    source_chirp<D1>(thd, pn_order, sd);
+    o[0] = sd.tc.d;
+    o[1] = sd.F0.d;
+    o[2] = sd.C2.d;
+    o[3] = sd.P5.d;
+    o[4] = sd.P3.d;
+    for (int k = 5; k < kSrcFields; ++k) o[k] = 0.0;
+  } else {
+    source_geometry<D1>(thd, sd);
+    for (int k = 0; k < 5; ++k) o[k] = 0.0;
+    o[5] = sd.phi0.d;
+    o[6] = sd.dop_c.d;
+    o[7] = sd.dop_s.d;
+    for (int q = 0; q < 6; ++q) {
+      o[8 + q] = sd.pp[q].d;
+      o[14 + q] = sd.px[q].d;
+    }
+    o[20] = sd.nz.d;
+  }
+}
+
+size_t grad_src_bytes(int64_t n) { return (size_t)n * 8 * kSrcFields * sizeof(double); }
 
 // Sum of the work items' partial sums, h = 0 .. parts-1 in order (deterministic).
 __global__ void k_grad_reduce(const double* __restrict__ part, int parts, int64_t n,
@@ -933,7 +948,6 @@ __global__ void k_grad_reduce(const double* __restrict__ part, int parts, int64_
 template <bool TDI>
 __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_grad(GradArgs a) {
   extern __shared__ float4 s_seg[];
-  __shared__ double s_dsrc[kGradWarps][8][kSrcFields];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* seg = s_seg + (size_t)warp * a.n_seg;
   for (;;) {
@@ -944,8 +958,8 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
     const int64_t q = (int64_t)(t / (unsigned)a.parts);
     const int h = (int)(t - (unsigned)q * (unsigned)a.parts);
     const int64_t i = a.perm ? (int64_t)a.perm[q] : q;
-    grad_one<TDI>(a, i, h, lane, seg, s_dsrc[warp]);
-    __syncwarp();  // seg and dsrc are rewritten by the next template
+    grad_one<TDI>(a, i, h, lane, seg);
+    __syncwarp();  // seg is rewritten by the next template
   }
 }
 
@@ -972,9 +986,11 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
                         unsigned* counter, const int32_t* perm, int parts, double* part_buf,
-                        int n_sm, cudaStream_t s) {
+                        double* src_buf, int n_sm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf)) return cudaErrorInvalidValue;
+  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf) || !src_buf)
+    return cudaErrorInvalidValue;
+  k_grad_src<<<(unsigned)((n * 8 + 127) / 128), 128, 0, s>>>(theta, n, pn_order, src_buf);
   GradArgs a;
   a.g = g;
   a.mc = mc;
@@ -999,6 +1015,7 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.perm = perm;
   a.parts = parts;
   a.part_out = part_buf;
+  a.dsrc = src_buf;
   const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
   auto kern = response == 2 ? k_grad<true> : k_grad<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
