@@ -94,6 +94,10 @@ typedef struct tfs_options {
   int warps_per_cta; /* mixed path CTA size in warps; 0 = autotuned on first use */
   int use_graph;     /* 1: replay the mixed evaluation as a CUDA graph per batch shape */
   int profile;       /* 1: time each kernel of a call with CUDA events (tfs_last_profile) */
+  int tile_variant;  /* with warps_per_cta set: the mixed kernel's compiled tile/schedule
+                        variant, 0..2 (default 0; 1 and 2 exist for two channels on the
+                        fixed plane pitch, TFS_ERR_ARG otherwise); the autotuner picks
+                        its own when warps_per_cta is 0 */
   int64_t max_device_bytes; /* cap on the context's device allocations, 0 = none */
 } tfs_options;
 

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("pixel", ctypes.c_int), ("pn_order", ctypes.c_int),
                 ("response", ctypes.c_int), ("checked", ctypes.c_int), ("sort", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("max_device_bytes", ctypes.c_int64)]
+                ("profile", ctypes.c_int), ("tile_variant", ctypes.c_int),
+                ("max_device_bytes", ctypes.c_int64)]
 
 
 class Swarm(ctypes.Structure):
@@ -140,8 +141,8 @@ class TFS:
     """A libtfs context on one CUDA device.
 
     Options (keyword arguments): path ('mixed' | 'plain' | 'fp64'), pixel ('f16' | 'bf16'
-    | 'f32'), pn_order (0 | 1), response (0 | 1), sort, warps_per_cta, profile,
-    checked, max_device_bytes.
+    | 'f32' | 'f16all' | 'bf16all'), pn_order (0 | 1), response (0 | 1 | 2), sort,
+    warps_per_cta, tile_variant, use_graph, profile, checked, max_device_bytes.
     """
 
     def __init__(self, device=0, **opts):

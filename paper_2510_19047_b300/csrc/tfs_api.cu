@@ -256,7 +256,7 @@ int issue_mixed(tfs_ctx* c, EvalArgs& a, int64_t n_tpl, const MixedShape& sh, cu
 }
 
 // Launch shape of the mixed kernel. With options.warps_per_cta set: that CTA size,
-// variant 0, as many CTAs as fit. Otherwise the autotuner's pick, timed once per
+// options.tile_variant, as many CTAs as fit. Otherwise the autotuner's pick, timed once per
 // (channels, pixel type, segment slots, per-template mode, response) on 24576 templates
 // taken at a fixed stride from the current (already sorted) queue: every compiled tile/schedule
 // variant (bin unroll, pixel-load lead, register target) x {4, 8} warps per CTA x
@@ -269,11 +269,15 @@ int mixed_shape(tfs_ctx* c, EvalArgs a, int64_t n_tpl, int fine_cap, int per_tem
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->n_sm * per_sm, need));
   };
   if (c->opt.warps_per_cta) {
+    const int v = c->opt.tile_variant;
+    if (v >= mixed_variants(n_chan, c->pitch))
+      return fail(c, TFS_ERR_ARG, "options.tile_variant " + std::to_string(v) +
+                                      " is not compiled for this channel count and plane pitch");
     int per_sm = 0;
-    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, 0, c->opt.warps_per_cta,
+    CUDA_TRY(c, mixed_occupancy(n_chan, pix, c->pitch, c->opt.response, v, c->opt.warps_per_cta,
                                 fine_cap, &per_sm));
     if (per_sm < 1) return fail(c, TFS_ERR_ARG, "mixed kernel does not fit on an SM with these shapes");
-    out->variant = 0;
+    out->variant = v;
     out->warps = c->opt.warps_per_cta;
     out->per_sm = per_sm;
     out->ctas = ctas_for(out->warps, per_sm);
@@ -353,6 +357,7 @@ void tfs_default_options(tfs_options* o) {
   o->checked = 0;
   o->sort = 1;
   o->warps_per_cta = 0;
+  o->tile_variant = 0;
   o->use_graph = 0;
   o->profile = 0;
   o->max_device_bytes = 0;
@@ -367,6 +372,8 @@ static int check_options(tfs_ctx* c, const tfs_options* o) {
   if (o->warps_per_cta < 0 || o->warps_per_cta > 8 ||
       (o->warps_per_cta && (o->warps_per_cta & (o->warps_per_cta - 1))))
     return fail(c, TFS_ERR_ARG, "options.warps_per_cta must be 0 or a power of two <= 8");
+  if (o->tile_variant < 0 || o->tile_variant > 2)
+    return fail(c, TFS_ERR_ARG, "options.tile_variant must be 0, 1 or 2");
   if (o->max_device_bytes < 0) return fail(c, TFS_ERR_ARG, "options.max_device_bytes must be >= 0");
   return TFS_OK;
 }

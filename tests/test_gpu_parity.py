@@ -401,18 +401,24 @@ def test_graph_replay_with_profiling(ae45, ae45_bank):
 
 
 def test_graph_replay_checked_mode_and_launch_shapes(ae45, ae45_bank):
-    """CUDA-graph replay, checked mode and every launch shape give the direct path's
-    result bit for bit (templates are independent and the fold is deterministic)."""
+    """CUDA-graph replay, checked mode and every launch shape (each compiled tile variant
+    at 4 and 8 warps per CTA) give the direct path's result bit for bit (templates are
+    independent and the fold is deterministic)."""
     import torch
     lev = [64, 16, 4]
     base = ctx_for(ae45, "mixed", "f16")
     ref, rneff, _ = base.eval_statistic(ae45_bank, lev)
-    for kw in ({"use_graph": 1}, {"checked": 1}, {"warps_per_cta": 4}, {"warps_per_cta": 8},
-               {"sort": 0}):
+    shapes = [{"warps_per_cta": w, "tile_variant": v} for v in range(3) for w in (4, 8)]
+    for kw in [{"use_graph": 1}, {"checked": 1}, {"sort": 0},
+               {"use_graph": 1, "warps_per_cta": 4, "tile_variant": 2}] + shapes:
         c = ctx_for(ae45, "mixed", "f16", **kw)
         for _ in range(2):  # second call replays the captured graph
             got, neff, _ = c.eval_statistic(ae45_bank, lev)
             assert np.array_equal(got, ref) and np.array_equal(neff, rneff), kw
+        if "tile_variant" in kw:  # the compiled variant asked for is the one launched
+            sh = c.last_launch_shape()
+            assert sh["variant"] == kw["tile_variant"], (kw, sh)
+            assert sh["threads_per_cta"] == 32 * kw["warps_per_cta"], (kw, sh)
     # a graph re-captures when the batch shape changes, and works on device arrays
     c = ctx_for(ae45, "mixed", "f16", use_graph=1)
     sub = ae45_bank[:, :100]
