@@ -423,6 +423,49 @@ def test_detector_tensor_invariants():
         assert np.abs(DA @ nc).max() < 1e-14 and np.abs(DE @ nc).max() < 1e-14
 
 
+def test_response_power_closed_form():
+    """The A and E tensors are traceless, orthogonal, of equal norm D:D = 9/16 and lie in
+    the constellation plane (test above), so they act as two 90-degree Michelsons 45
+    degrees apart, scaled by k^2 = (9/16) / (1/2) = 9/8. The textbook patterns of such a
+    Michelson for a source at angle theta from its normal and azimuth phi, polarisation
+    angle psi_d in its frame, F+ = a cos2phi cos2psi_d - c sin2phi sin2psi_d and
+    Fx = a cos2phi sin2psi_d + c sin2phi cos2psi_d with a = (1 + cos^2 theta)/2,
+    c = cos theta, give for the pair sum_{A,E} F+^2 = k^2 (a^2 cos^2 2psi_d + c^2 sin^2 2psi_d)
+    and sum Fx^2 = k^2 (a^2 sin^2 2psi_d + c^2 cos^2 2psi_d), whatever phi. So
+    sum |T_alpha|^2 (T = F+ A+ - i Fx Ax) is k^2 (a^2 + c^2) at iota = 0 (A+ = Ax = 1) for
+    every psi, and for any iota it is k^2 [(A+^2 + Ax^2)(a^2 + c^2) + (A+^2 - Ax^2)(a^2 - c^2)
+    cos 4psi_d] / 2, whose mean and cos 4psi amplitude eight equally spaced psi recover
+    exactly."""
+    rng = np.random.default_rng(11)
+    k2 = 9.0 / 8.0
+    for _ in range(40):
+        lam, beta = rng.uniform(0, 2 * np.pi), math.asin(rng.uniform(-1, 1))
+        t = rng.uniform(0, 2 * YEAR_S)
+        a_orb = 2 * np.pi * t / YEAR_S
+        nc = np.array([-0.5 * math.cos(a_orb), -0.5 * math.sin(a_orb), math.sqrt(3) / 2])
+        nhat = np.array([math.cos(beta) * math.cos(lam), math.cos(beta) * math.sin(lam),
+                         math.sin(beta)])
+        c = float(nhat @ nc)
+        a = 0.5 * (1 + c * c)
+        iota = rng.uniform(0, np.pi)
+        ap, ax = 0.5 * (1 + math.cos(iota) ** 2), math.cos(iota)
+        psi0 = rng.uniform(0, np.pi)
+        face_on, vals = [], []
+        for j in range(8):
+            psi = psi0 + j * np.pi / 8
+            th0 = np.array([30.0, 0.2, 0.01, 0.3, lam, beta, psi, 0.0])
+            face_on.append(np.sum(np.abs(oracle.response(th0, [t])) ** 2))
+            th = th0.copy()
+            th[7] = iota
+            vals.append(np.sum(np.abs(oracle.response(th, [t])) ** 2))
+        vals = np.array(vals)
+        assert np.allclose(face_on, k2 * (a * a + c * c), rtol=1e-12, atol=0)
+        assert abs(vals.mean() - k2 * (ap * ap + ax * ax) * (a * a + c * c) / 2) < 1e-12
+        # the cos 4psi amplitude: k^2 |A+^2 - Ax^2| |a^2 - c^2| / 2
+        amp4 = abs(np.sum(vals * np.exp(4j * (psi0 + np.arange(8) * np.pi / 8)))) * 2 / 8
+        assert abs(amp4 - k2 * abs(ap * ap - ax * ax) * abs(a * a - c * c) / 2) < 1e-12
+
+
 def test_sky_and_polarisation_average_of_antenna_power():
     # <(D : e+)^2> over isotropic sources and polarisation angles = (2/5) D:D = 9/40
     rng = np.random.default_rng(2)
