@@ -58,7 +58,8 @@ struct tfs_ctx {
   int pix_built = -1;
   double su = 1.0, sw = 1.0;
   // per-call scratch
-  DevBuf theta, tpl, tplm, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad, segZ;
+  DevBuf theta, tpl, tplm, perm, sortbuf, stat, neff, diag, counter, deverr, nseg, idx64, grad;
+  DevBuf segZ;  // the gradient's per-segment adjoint weights (lambda, mu)
   // search steps: tile corners of the swarms, partial sums and block counter of the
   // refinement step's mean
   DevBuf tile_lo, tile_hi, rpart, rdone;
@@ -1083,13 +1084,14 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   CUDA_TRY(c, grad_plan(c->opt.response, n_seg, c->n_sm, n_tpl, &parts));
   if (parts > 1 && (r = buf_ensure(c, c->gpart, (size_t)parts * 9 * n_tpl * 8))) return r;
   if ((r = buf_ensure(c, c->gsrc, grad_src_bytes(n_tpl)))) return r;
+  if ((r = buf_ensure(c, c->segZ, (size_t)n_tpl * n_seg * 16))) return r;
   CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
                           (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
                           (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og,
                           (unsigned*)c->counter.p, perm, parts, (double*)c->gpart.p,
-                          (double*)c->gsrc.p, c->n_sm, s));
-  c->launches += parts > 1 ? 3 : 2;
+                          (double*)c->gsrc.p, (float4*)c->segZ.p, c->n_sm, s));
+  c->launches += parts > 1 ? 4 : 3;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));

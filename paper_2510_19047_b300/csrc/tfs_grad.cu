@@ -279,11 +279,12 @@ struct GradArgs {
   float twopidT, pidT2;  // 2 pi dT and pi dT^2 (FP32, formed on the host)
   double* out_stat;
   double* out_grad;     // [8][n]
-  unsigned* counter;    // work ticket of the persistent launch (zero at launch)
+  unsigned* counter;    // work tickets of the persistent launches: [0] pass A, [1] pass B
   const int32_t* perm;  // queue order (longest templates first), or null for 0..n-1
   int parts;            // work items per template: contiguous groups of its segments
   double* part_out;     // parts > 1: [parts][9][n] partial (Upsilon, gradient) sums
   const double* dsrc;   // [n][8][kSrcFields]: d(template constant)/d theta_p (k_grad_src)
+  float4* lam;          // [n][n_seg]: (Re lambda, Im lambda, mu, 0) per segment (k_grad_a)
 };
 
 // The track at the start of tranche m: the mixed kernel's double-float evaluation
@@ -531,39 +532,33 @@ __device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, con
 
 }  // namespace
 
-// Statistic and gradient of template i by one warp. seg: this warp's n_seg float4
-// slots in shared memory; dsrc: its 8 x kSrcFields derivative table.
 // Work item (i, h): template i's segments split into a.parts contiguous groups of
 // (nearly) equal count; item h covers the tranches of group h inside [m_lo, m_hi).
 // Upsilon and the gradient are sums over segments, so the items' partial sums add up
 // to the template's (in a fixed order, by k_grad_reduce).
-template <bool TDI>
-__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, int lane, float4* seg) {
-  const int nch = a.g.n_chan;
-  const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
-  const TplConst tc = a.tpl[i];
-  const TplMix* cp = a.tplm + i;
-  int mA = tc.m_lo, mB = tc.m_hi;
+// Tranche range [mA, mB) of work item (template with range [m_lo, m_hi), group h);
+// false for an empty group.
+__device__ __forceinline__ bool item_range(const GradArgs& a, int m_lo, int m_hi, int h, int& mA,
+                                           int& mB) {
+  mA = m_lo;
+  mB = m_hi;
   if (a.parts > 1 && mB > mA) {
     const int s_lo = mA / a.seg_len, n_s = (mB - 1) / a.seg_len - s_lo + 1;
     mA = max(mA, (s_lo + (h * n_s) / a.parts) * a.seg_len);
     mB = min(mB, (s_lo + ((h + 1) * n_s) / a.parts) * a.seg_len);
   }
-  if (mB <= mA) {  // empty group: zero partial sums
-    if (a.parts > 1 && lane < 9) a.part_out[((int64_t)h * 9 + lane) * a.n_tpl + i] = 0.0;
-    return;
-  }
-  SrcF sf;
-  sf.tc = (float)tc.tc;
-  sf.tc_inv = (float)(1.0 / tc.tc);
-  sf.inv8tc = (float)(0.125 / tc.tc);
-  sf.F0 = (float)tc.F0;
-  sf.C2 = (float)tc.C2;
-  sf.P5 = (float)tc.P5;
-  sf.P3 = (float)tc.P3;
-  sf.tc_inv_d = df_make(1.0 / tc.tc);
-  sf.P5c = df_make(tc.P5 * (0.5 / kPi));
-  sf.P3c = df_make(tc.P3 * (0.5 / kPi));
+  return mB > mA;
+}
+
+// Pass A of work item (i, [mA, mB)): Z_n, N_n of its segments folded in the warp's seg
+// slots, then the adjoint weights (lambda, mu) of those segments stored to a.lam. Returns
+// the item's share of Upsilon (on every lane).
+template <bool TDI>
+__device__ __forceinline__ double grad_pass_a(const GradArgs& a, int64_t i, int mA, int mB, int lane,
+                                              float4* seg) {
+  const int nch = a.g.n_chan;
+  const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
+  const TplMix* cp = a.tplm + i;
   for (int q = lane; q < a.n_seg; q += 32) seg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
 
@@ -656,29 +651,56 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
     }
   }
   __syncwarp();
-  // adjoint weights per segment, replacing (Z, N) by (lambda, mu)
+  // adjoint weights of the item's segments, lambda = 2 s conj(Z)/N, mu = -s |Z|^2/N^2
   double ups = 0.0;
-  for (int q = lane; q < a.n_seg; q += 32) {
+  const int qa = mA / a.seg_len, qb = (mB - 1) / a.seg_len;
+  for (int q = qa + lane; q <= qb; q += 32) {
     const float4 v = seg[q];
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
     if (v.z > 0.f) {
       const double zz = (double)v.x * v.x + (double)v.y * v.y;
       const double inz = 1.0 / (double)v.z, t = a.scale * inz;
       ups += t * zz;
-      o.x = (float)(2.0 * t * v.x);  // lambda = 2 s conj(Z)/N
+      o.x = (float)(2.0 * t * v.x);
       o.y = (float)(-2.0 * t * v.y);
-      o.z = (float)(-t * zz * inz);  // mu
+      o.z = (float)(-t * zz * inz);
     }
-    seg[q] = o;
+    a.lam[(int64_t)i * a.n_seg + q] = o;
   }
   for (int o = 16; o > 0; o >>= 1) ups += __shfl_xor_sync(kFullG, ups, o);
-  if (lane == 0) {
-    if (a.parts > 1)
-      a.part_out[(int64_t)h * 9 * a.n_tpl + i] = ups;
-    else
-      a.out_stat[i] = ups;
-  }
   __syncwarp();
+  return ups;
+}
+
+// Pass B of work item (i, h): the adjoints of the template constants from the stored
+// (lambda, mu), contracted with the constants' theta-derivatives.
+template <bool TDI>
+__device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, int lane) {
+  const int nch = a.g.n_chan;
+  const int64_t pitch2 = 2 * (int64_t)a.pitch;  // float4 units per pixel row
+  const TplConst tc = a.tpl[i];
+  const TplMix* cp = a.tplm + i;
+  int mA, mB;
+  if (!item_range(a, tc.m_lo, tc.m_hi, h, mA, mB)) {  // empty group: zero gradient
+    if (lane >= 1 && lane < 9) {
+      if (a.parts > 1)
+        a.part_out[((int64_t)h * 9 + lane) * a.n_tpl + i] = 0.0;
+      else
+        a.out_grad[(int64_t)(lane - 1) * a.n_tpl + i] = 0.0;
+    }
+    return;
+  }
+  SrcF sf;
+  sf.tc = (float)tc.tc;
+  sf.tc_inv = (float)(1.0 / tc.tc);
+  sf.inv8tc = (float)(0.125 / tc.tc);
+  sf.F0 = (float)tc.F0;
+  sf.C2 = (float)tc.C2;
+  sf.P5 = (float)tc.P5;
+  sf.P3 = (float)tc.P3;
+  sf.tc_inv_d = df_make(1.0 / tc.tc);
+  sf.P5c = df_make(tc.P5 * (0.5 / kPi));
+  sf.P3c = df_make(tc.P3 * (0.5 / kPi));
 
   // ---- pass B: adjoints of the template constants ----
   // per 32-tranche block the lanes' FP32 contributions are summed over the warp; lane
@@ -697,7 +719,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
     int JLO, JHI;
     general_range(L.ok, L.aa, L.eps, L.sig, JLO, JHI);
     if (L.ok) {
-      const float4 lm = seg[m / a.seg_len];
+      const float4 lm = __ldg(a.lam + (int64_t)i * a.n_seg + m / a.seg_len);
       const float lr = lm.x, li = lm.y, mu = lm.z;
       // general bins j in [g0, g1) (warp-uniform); the rest take the asymptotic form
       const int g0 = max(0, min(kNF, JLO + kNFHalf)), g1 = max(g0, min(kNF, JHI + kNFHalf + 1));
@@ -945,8 +967,13 @@ __global__ void k_grad_reduce(const double* __restrict__ part, int parts, int64_
 // Persistent launch: every warp takes templates from the queue until it is empty, so
 // the long templates (first in the sorted queue) do not leave a tail of idle SMs.
 // TDI: the TDI-1.5 response (code 2), as its own instantiation.
+// Pass A (Upsilon and the adjoint weights) in a kernel of its own: it needs far fewer
+// registers than pass B, and runs at twice the resident warps.
+#ifndef TFS_GRADA_MINB
+#define TFS_GRADA_MINB 8
+#endif
 template <bool TDI>
-__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_grad(GradArgs a) {
+__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 4 : TFS_GRADA_MINB) k_grad_a(GradArgs a) {
   extern __shared__ float4 s_seg[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float4* seg = s_seg + (size_t)warp * a.n_seg;
@@ -958,8 +985,33 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
     const int64_t q = (int64_t)(t / (unsigned)a.parts);
     const int h = (int)(t - (unsigned)q * (unsigned)a.parts);
     const int64_t i = a.perm ? (int64_t)a.perm[q] : q;
-    grad_one<TDI>(a, i, h, lane, seg);
-    __syncwarp();  // seg is rewritten by the next template
+    int mA, mB;
+    double ups = 0.0;
+    if (item_range(a, a.tpl[i].m_lo, a.tpl[i].m_hi, h, mA, mB))
+      ups = grad_pass_a<TDI>(a, i, mA, mB, lane, seg);
+    if (lane == 0) {
+      if (a.parts > 1)
+        a.part_out[(int64_t)h * 9 * a.n_tpl + i] = ups;
+      else
+        a.out_stat[i] = ups;
+    }
+    __syncwarp();  // seg is rewritten by the next item
+  }
+}
+
+// Pass B, after k_grad_a has stored every item's (lambda, mu).
+template <bool TDI>
+__global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_grad(GradArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(a.counter + 1, 1u);
+    t = __shfl_sync(kFullG, t, 0);
+    if ((int64_t)t >= a.n_tpl * a.parts) break;  // whole warp leaves together
+    const int64_t q = (int64_t)(t / (unsigned)a.parts);
+    const int h = (int)(t - (unsigned)q * (unsigned)a.parts);
+    const int64_t i = a.perm ? (int64_t)a.perm[q] : q;
+    grad_one<TDI>(a, i, h, lane);
   }
 }
 
@@ -967,12 +1019,9 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
 // a small batch (fewer than ~3 waves of templates) splits each template's segments into
 // up to 4 groups so that the persistent queue still ends in a short tail.
 cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts) {
-  const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
   auto kern = response == 2 ? k_grad<true> : k_grad<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, 0);
   if (e != cudaSuccess) return e;
   const int64_t resident = (int64_t)n_sm * std::max(per_sm, 1) * kGradWarps;
   int p = 1;
@@ -986,9 +1035,9 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
                         unsigned* counter, const int32_t* perm, int parts, double* part_buf,
-                        double* src_buf, int n_sm, cudaStream_t s) {
+                        double* src_buf, float4* lam_buf, int n_sm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf) || !src_buf)
+  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf) || !src_buf || !lam_buf)
     return cudaErrorInvalidValue;
   k_grad_src<<<(unsigned)((n * 8 + 127) / 128), 128, 0, s>>>(theta, n, pn_order, src_buf);
   GradArgs a;
@@ -1016,19 +1065,34 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.parts = parts;
   a.part_out = part_buf;
   a.dsrc = src_buf;
-  const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
-  auto kern = response == 2 ? k_grad<true> : k_grad<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
-  if (e != cudaSuccess) return e;
+  a.lam = lam_buf;
   const int64_t need = (n * parts + kGradWarps - 1) / kGradWarps;
-  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s);  // tickets of A and B
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, kGradWarps * 32, smem, s>>>(a);
-  e = cudaGetLastError();
+  // pass A: Upsilon and (lambda, mu) per segment
+  {
+    const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
+    auto kern = response == 2 ? k_grad_a<true> : k_grad_a<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
+    kern<<<(unsigned)ctas, kGradWarps * 32, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // pass B: the gradient
+  {
+    auto kern = response == 2 ? k_grad<true> : k_grad<false>;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
+    kern<<<(unsigned)ctas, kGradWarps * 32, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || parts == 1) return e;
   const int64_t blocks = std::min<int64_t>((9 * n + 255) / 256, (int64_t)n_sm * 8);
   k_grad_reduce<<<(unsigned)blocks, 256, 0, s>>>(part_buf, parts, n, out_stat, out_grad);

@@ -148,8 +148,9 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
                         unsigned* counter, const int32_t* perm, int parts, double* part_buf,
-                        double* src_buf, int n_sm, cudaStream_t s);
-// Bytes of launch_grad's src_buf for n templates (the constants' theta-derivatives).
+                        double* src_buf, float4* lam_buf, int n_sm, cudaStream_t s);
+// Bytes of launch_grad's src_buf for n templates (the constants' theta-derivatives);
+// lam_buf holds n * n_seg float4 (the segments' adjoint weights).
 size_t grad_src_bytes(int64_t n);
 
 }  // namespace tfs
