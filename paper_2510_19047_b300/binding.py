@@ -300,15 +300,23 @@ class TFS:
                 self.h, int(nu.size), nu.ctypes.data_as(ctypes.c_void_p),
                 cr.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p)))
 
-    def grad_statistic(self, theta, n_seg):
-        """(Upsilon [n], d Upsilon / d theta [8, n]) at one N_seg."""
+    def grad_statistic(self, theta, n_seg, out=None):
+        """(Upsilon [n], d Upsilon / d theta [8, n]) at one N_seg. out: optional
+        (stat [n], grad [8, n]) float64 arrays to write into (contiguous; CUDA tensors
+        for a device theta)."""
         dev = _is_torch(theta) and theta.is_cuda
         if _is_torch(theta):
             theta = theta.double().contiguous()
         else:
             theta = np.ascontiguousarray(theta, dtype=np.float64)
         n = theta.shape[1]
-        if dev:
+        if out is not None:
+            stat, grad = out
+            for a, shape in ((stat, (n,)), (grad, (8, n))):
+                if tuple(a.shape) != shape or str(a.dtype).split(".")[-1] != "float64" or \
+                        not (a.is_contiguous() if _is_torch(a) else a.flags.c_contiguous):
+                    raise ValueError("out must be contiguous float64 arrays of shapes [n], [8, n]")
+        elif dev:
             import torch
             stat = torch.empty(n, dtype=torch.float64, device=theta.device)
             grad = torch.empty((8, n), dtype=torch.float64, device=theta.device)

@@ -158,3 +158,31 @@ def test_autograd_and_ascent(ae45):
     pred = t * norm ** 2
     ratio = (u1 - u0) / pred
     assert np.mean((ratio > 0.5) & (ratio < 1.5)) > 0.8, ratio
+
+
+@pytest.mark.parametrize("n", [64, 8192])
+def test_templates_without_active_tranches_give_zeros(ae45, n):
+    """A template whose track never enters the band (f_0 above the top bin, or so far
+    below the bottom of the window range that it does not reach it in 45 days) has no
+    active tranche: its statistic and gradient are exactly zero, both when a small batch
+    splits every template into several work items (n = 64) and when each template is one
+    item (n = 8192, over three waves), and its neighbours in the batch are unaffected."""
+    import torch
+    th = synth.candidates_near(ae45.injections, n, seed=9)
+    top = ae45.n_bins / ae45.dT  # frequency of the top bin [Hz]
+    dead = np.arange(5, n, 7)
+    th[2, dead[::2]] = 3.0 * top            # above the band from the start
+    th[2, dead[1::2]] = 2e-4                # below bin 10 for the whole grid
+    c = ctx_for(ae45)
+    _, ne, dg = c.eval_statistic(th, 16, diag=True)
+    idle = dg[0] == 0
+    assert idle[dead].all() and idle.sum() < len(dead) + n // 10
+    # poison the outputs so that an unwritten entry would show
+    u = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+    g = torch.full((8, n), np.nan, dtype=torch.float64, device="cuda")
+    c.grad_statistic(torch.from_numpy(th).cuda(), 16, out=(u, g))
+    u, g = u.cpu().numpy(), g.cpu().numpy()
+    assert np.all(u[idle] == 0) and np.all(g[:, idle] == 0)
+    assert np.all(np.isfinite(u)) and np.all(np.isfinite(g))
+    ref_u, _ = c.grad_statistic(th[:, ~idle][:, :32], 16)
+    np.testing.assert_allclose(u[~idle][:32], ref_u, rtol=1e-12)  # work-item split may differ
