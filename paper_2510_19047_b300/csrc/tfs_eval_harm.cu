@@ -242,14 +242,21 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
       fine_len = a.lv.fine_len;
     }
     const int n_fine = g.n_tranche / fine_len;
+    // m / fine_len = umulhi(m, ceil(2^32 / fine_len)), exact while m * fine_len < 2^32
+    // (n_tranche < 2^16, checked by the host)
+    const unsigned fmagic = fine_len > 1 ? 0xFFFFFFFFu / (unsigned)fine_len + 1u : 0u;
     for (int q = lane; q < n_fine; q += 32) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     int nact = 0, nnc = 0;
     __syncwarp();
 
-    for (int m0 = m_lo; m0 < m_hi; m0 += 32) {
-      const int m = m0 + lane;
-      const bool inr = m < m_hi;
-      bool act = inr && a.mask[m];
+    // the template's range walked over unmasked tranches only (a gap idles no lane);
+    // lane l of a block takes the block's l-th unmasked tranche
+    const int r_lo = a.rank[m_lo], r_hi = a.rank[m_hi];
+    for (int i0 = r_lo; i0 < r_hi; i0 += 32) {
+      const int il = i0 + lane;
+      const bool inr = il < r_hi;
+      const int m = inr ? a.live[il] : 0;
+      bool act = inr;
       {
       TrackH tk;
       tk.x = df{0.f, 0.f};
@@ -418,28 +425,40 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         ++nact;
         if (tks[128] > ncomp) ++nnc;
       }
-      // segmented (by finest segment) suffix sums across the warp; the first lane of
-      // each run adds its segment's sum to shared memory
-      const int key = inr ? m / fine_len : 0x7fffffff;
+      // inclusive prefix sums across the warp; a lane whose next lane lies in another
+      // finest segment (or past the block) adds its prefix to its own segment's slot and
+      // subtracts it from the next segment's, so that each slot gains the sum of its
+      // segment's lanes, in a fixed order
+      const int key = inr ? (fine_len > 1 ? (int)__umulhi((unsigned)m, fmagic) : m) : 0x7fffffff;
+      const int key_up = __shfl_down_sync(kFull, key, 1);
+      const bool nin = lane < 31 && il + 1 < r_hi;
+      const int keyn = nin ? key_up : 0x7fffffff;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const float zr2 = __shfl_down_sync(kFull, Zr, o);
-        const float zi2 = __shfl_down_sync(kFull, Zi, o);
-        const float n2 = __shfl_down_sync(kFull, Nn, o);
-        const int k2 = __shfl_down_sync(kFull, key, o);
-        if (lane + o < 32 && k2 == key) {
+        const float zr2 = __shfl_up_sync(kFull, Zr, o);
+        const float zi2 = __shfl_up_sync(kFull, Zi, o);
+        const float n2 = __shfl_up_sync(kFull, Nn, o);
+        if (lane >= o) {
           Zr += zr2;
           Zi += zi2;
           Nn += n2;
         }
       }
-      const int kprev = __shfl_up_sync(kFull, key, 1);
-      if (inr && (lane == 0 || kprev != key)) {
+      const bool seg_end = inr && keyn != key;
+      if (seg_end) {
         float4 v = acc[key];
         v.x += Zr;
         v.y += Zi;
         v.z += Nn;
         acc[key] = v;
+      }
+      __syncwarp();
+      if (seg_end && nin) {
+        float4 v = acc[keyn];
+        v.x -= Zr;
+        v.y -= Zi;
+        v.z -= Nn;
+        acc[keyn] = v;
       }
     }
     __syncwarp();
