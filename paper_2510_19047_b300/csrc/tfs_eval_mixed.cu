@@ -68,6 +68,13 @@ struct MixedVariant<2> {
 // TDI: the TDI-1.5 response (response code 2) instead of the long-wavelength one, as
 // its own instantiation so the long-wavelength kernel carries none of its code.
 // V: the tile/schedule variant (MixedVariant).
+// Number of general-form bins on each side of f_nm in an unrolled window (a type, so that
+// the window's loops unroll at compile time).
+template <int G>
+struct GeneralBins {
+  static constexpr int value = G;
+};
+
 template <int NCH, int PIX, int PITCH, bool TDI, int V>
 __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalArgs a) {
   constexpr int kBinUnroll = MixedVariant<V>::unroll;
@@ -289,36 +296,39 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
         s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
         // pixel loads run one bin ahead of the arithmetic
         typename Ld::P cur = Ld::raw(Pp);
-        if (JLO >= -1 && JHI <= 0) {
-          // Only the two bins next to f_nm (jp = -1, 0) can need the general form:
-          // fully unrolled, no per-bin branch. For jp >= 1, x2 < -r6 < 0; for jp <= -2,
-          // x1 > 1 > r6; and only jp = 0 can hold the sweep (x1 = aa <= 0 < x2).
-          // The two general bins first, so that a1 and the general form's temporaries are
-          // dead before the asymptotic bins run; pixel loads of those run kDepth bins
-          // ahead (a ring of packed elements in registers, started before the general
-          // bins so that their latency is covered)
-          constexpr int kAsym = kNF - 2;
-          // the k-th asymptotic bin: 0..kNFHalf-2, then kNFHalf+1..kNF-1
-          auto asym_bin = [](int k) { return k < kNFHalf - 1 ? k : k + 2; };
+        // Fully unrolled window, no per-bin branch: the general form on the 2G bins
+        // jp = -G .. G-1 next to f_nm, the asymptotic form on the others (for jp >= G,
+        // x2 < -r6 < 0; for jp < -G, x1 > G > r6). Only jp >= 0 can hold the sweep
+        // (x1 < 0 <= x2), and jp = -1 takes its offset from rb (a1). The general bins
+        // come first, so that a1 and the general form's temporaries are dead before the
+        // asymptotic bins run; pixel loads of those run kDepth bins ahead (a ring of
+        // packed elements in registers, started before the general bins so that their
+        // latency is covered).
+        auto unrolled = [&](auto gtag) {
+          constexpr int G = decltype(gtag)::value;
+          constexpr int kAsym = kNF - 2 * G;
+          // the k-th asymptotic bin: 0 .. kNFHalf-G-1, then kNFHalf+G .. kNF-1
+          auto asym_bin = [](int k) { return k < kNFHalf - G ? k : k + 2 * G; };
           typename Ld::P ring[kDepth];
           ring[0] = cur;
 #pragma unroll
           for (int q = 1; q < kDepth; ++q) ring[q] = Ld::raw(Pp + (int64_t)asym_bin(q) * pitch);
-          {
-            const typename Ld::P g0 = Ld::raw(Pp + (int64_t)(kNFHalf - 1) * pitch);
-            const typename Ld::P g1 = Ld::raw(Pp + (int64_t)kNFHalf * pitch);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {  // jp = -1 (x1 = a1), then jp = 0 (x1 = aa)
-              float2 cur_r, cur_i, cur_w;
-              Ld::cvt(h ? g1 : g0, cur_r, cur_i, cur_w);
-              float wr, wi;
-              w_general(h ? aa : a1, h ? ae : a1 + eps, sig, spi, cpsi, spsi, h == 1, wr, wi);
-              if (kR16) {
-                wr = round_f16(wr);
-                wi = round_f16(wi);
-              }
-              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+          for (int h = 0; h < 2 * G; ++h) {
+            const int jp = h - G;
+            const typename Ld::P gp = Ld::raw(Pp + (int64_t)(kNFHalf + jp) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(gp, cur_r, cur_i, cur_w);
+            constexpr float kZero = 0.0f;
+            const float c = kZero + (float)jp;
+            float wr, wi;
+            w_general(jp == -1 ? a1 : aa - c, jp == -1 ? a1 + eps : ae - c, sig, spi, cpsi, spsi,
+                      jp >= 0, wr, wi);
+            if (kR16) {
+              wr = round_f16(wr);
+              wi = round_f16(wi);
             }
+            acc_general(s, cur_r, cur_i, cur_w, wr, wi);
           }
 #pragma unroll
           for (int k = 0; k < kAsym; ++k) {
@@ -330,6 +340,11 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
             const float c = kZero + (float)(asym_bin(k) - kNFHalf);
             acc_asym<kR16>(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
           }
+        };
+        if (JLO >= -1 && JHI <= 0) {
+          unrolled(GeneralBins<1>{});  // ~72 % of the units on the two-year bank
+        } else if (JLO >= -2 && JHI <= 1) {
+          unrolled(GeneralBins<2>{});  // ~18 %
         } else {
           float jpf = -(float)kNFHalf;  // jp as an exact float (no int-to-float per bin)
 #pragma unroll kBinUnroll
