@@ -359,30 +359,49 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         const float2 xae = make_float2(q.aa, ae);
         BinAcc s;
         s.u1r = s.u1i = s.u2r = s.u2i = s.nn = make_float2(0.f, 0.f);
-        if (JLO >= -1 && JHI <= 0) {
-          // only the two bins next to f_nm (jp = -1, 0) can need the general form, and
-          // only jp = 0 can hold the sweep: fully unrolled, loads kHarmDepth bins ahead
+        // fully unrolled window, no per-bin branch: the general form on the 2G bins
+        // jp = -G .. G-1 next to f_nm (first, so that their temporaries are dead before
+        // the asymptotic bins run), the asymptotic form on the others; only jp >= 0 can
+        // hold the sweep, and jp = -1 takes its offset from rb (a1)
+        auto unrolled = [&](auto gtag) {
+          constexpr int G = decltype(gtag)::value;
+          constexpr int kAsym = kNF - 2 * G;
+          // the k-th asymptotic bin: 0 .. kNFHalf-G-1, then kNFHalf+G .. kNF-1
+          auto asym_bin = [](int k) { return k < kNFHalf - G ? k : k + 2 * G; };
           typename Ld::P ring[kHarmDepth];
 #pragma unroll
-          for (int r = 0; r < kHarmDepth; ++r) ring[r] = Ld::raw(Pp + (int64_t)r * pitch);
+          for (int r = 0; r < kHarmDepth; ++r) ring[r] = Ld::raw(Pp + (int64_t)asym_bin(r) * pitch);
 #pragma unroll
-          for (int j = 0; j < kNF; ++j) {
-            const typename Ld::P pj = ring[j % kHarmDepth];
-            if (j + kHarmDepth < kNF) ring[j % kHarmDepth] = Ld::raw(Pp + (int64_t)(j + kHarmDepth) * pitch);
+          for (int hb = 0; hb < 2 * G; ++hb) {
+            const int jp = hb - G;
+            const typename Ld::P gp = Ld::raw(Pp + (int64_t)(kNFHalf + jp) * pitch);
+            float2 cur_r, cur_i, cur_w;
+            Ld::cvt(gp, cur_r, cur_i, cur_w);
+            constexpr float kZero = 0.0f;
+            const float c = kZero + (float)jp;
+            float wr, wi;
+            w_general(jp == -1 ? q.a1 : q.aa - c, jp == -1 ? q.a1 + q.eps : ae - c, q.sig, spi,
+                      q.cpsi, q.spsi, jp >= 0, wr, wi);
+            acc_general(s, cur_r, cur_i, cur_w, wr, wi);
+          }
+#pragma unroll
+          for (int k = 0; k < kAsym; ++k) {
+            const typename Ld::P pj = ring[k % kHarmDepth];
+            if (k + kHarmDepth < kAsym)
+              ring[k % kHarmDepth] = Ld::raw(Pp + (int64_t)asym_bin(k + kHarmDepth) * pitch);
             float2 cur_r, cur_i, cur_w;
             Ld::cvt(pj, cur_r, cur_i, cur_w);
             constexpr float kZero = 0.0f;
-            const float c = kZero + (float)(j - kNFHalf);
-            if (j == kNFHalf - 1 || j == kNFHalf) {
-              float wr, wi;
-              const float x1 = kNear && j == kNFHalf - 1 ? q.a1 : q.aa - c;
-              const float x2 = kNear && j == kNFHalf - 1 ? q.a1 + q.eps : ae - c;
-              w_general(x1, x2, q.sig, spi, q.cpsi, q.spsi, j == kNFHalf, wr, wi);
-              acc_general(s, cur_r, cur_i, cur_w, wr, wi);
-            } else {
-              acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
-            }
+            const float c = kZero + (float)(asym_bin(k) - kNFHalf);
+            acc_asym(s, cur_r, cur_i, cur_w, __fadd2_rn(xae, make_float2(-c, -c)), m2c);
           }
+        };
+        if (JLO >= -1 && JHI <= 0) {
+          unrolled(GeneralBins<1>{});
+        } else if (JLO >= -2 && JHI <= 1) {
+          unrolled(GeneralBins<2>{});
+        } else if (JLO >= -3 && JHI <= 2) {
+          unrolled(GeneralBins<3>{});
         } else {
           typename Ld::P cur = Ld::raw(Pp);
           float jpf = -(float)kNFHalf;

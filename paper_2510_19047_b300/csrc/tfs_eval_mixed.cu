@@ -68,13 +68,6 @@ struct MixedVariant<2> {
 // TDI: the TDI-1.5 response (response code 2) instead of the long-wavelength one, as
 // its own instantiation so the long-wavelength kernel carries none of its code.
 // V: the tile/schedule variant (MixedVariant).
-// Number of general-form bins on each side of f_nm in an unrolled window (a type, so that
-// the window's loops unroll at compile time).
-template <int G>
-struct GeneralBins {
-  static constexpr int value = G;
-};
-
 template <int NCH, int PIX, int PITCH, bool TDI, int V>
 __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalArgs a) {
   constexpr int kBinUnroll = MixedVariant<V>::unroll;

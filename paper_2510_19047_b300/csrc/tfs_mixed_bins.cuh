@@ -81,6 +81,13 @@ struct PixLoad<TFS_PIX_BF16_ALL> {
   }
 };
 
+// Number of general-form bins on each side of f_nm in an unrolled window (a type, so that
+// the window's loops unroll at compile time).
+template <int G>
+struct GeneralBins {
+  static constexpr int value = G;
+};
+
 // x rounded to FP16 and back: a template value held at FP16 precision (precision studies).
 __device__ __forceinline__ float round_f16(float x) { return __half2float(__float2half_rn(x)); }
 
