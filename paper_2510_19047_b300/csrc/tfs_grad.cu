@@ -68,6 +68,16 @@ static_assert(kSrcFields + 3 <= 32, "one lane per field and per phase share");
 #define TFS_GRAD_UNROLL 3
 #endif
 constexpr int kGradUnroll = TFS_GRAD_UNROLL;  // asymptotic-bin loop unroll (load batching)
+#ifndef TFS_GRAD_DEPTH
+#define TFS_GRAD_DEPTH 3
+#endif
+constexpr int kGradDepth = TFS_GRAD_DEPTH;  // pixel-load lead of pass A's unrolled window, in bins
+// number of general-form bins on each side of f_nm in an unrolled window (a type, so that
+// the window unrolls at compile time)
+template <int G>
+struct GradBins {
+  static constexpr int value = G;
+};
 
 // The paper's auxiliary Fresnel functions and their derivatives at a = |v| (the
 // hardware reciprocal in place of IEEE division: ~1 ulp).
@@ -576,47 +586,87 @@ __device__ __forceinline__ double grad_pass_a(const GradArgs& a, int64_t i, int 
       if (L.ok) {
         const int g0 = max(0, min(kNF, JLO + kNFHalf)), g1 = max(g0, min(kNF, JHI + kNFHalf + 1));
         const float4* Pp = a.P + (int64_t)(L.kc - kNFHalf) * pitch2 + 2 * (int64_t)m;
-        float zr[2], zi[2], nn[2];
-        {
-          // asymptotic bins: A1 = sum u/v1, A2 = sum u/v2, Q = sum w |pi W|^2 (channels
-          // paired); sum conj(u) W over them = (i/pi)(conj(A1) - e^{i Psi} conj(A2))
-          float2 A1r = f2(0.f), A1i = f2(0.f), A2r = f2(0.f), A2i = f2(0.f), Q = f2(0.f);
-          const float m2c = -2.0f * L.cps;
+        // asymptotic bins: A1 = sum u/v1, A2 = sum u/v2, Q = sum w |pi W|^2 (channels
+        // paired); sum conj(u) W over them = (i/pi)(conj(A1) - e^{i Psi} conj(A2))
+        float2 A1r = f2(0.f), A1i = f2(0.f), A2r = f2(0.f), A2i = f2(0.f), Q = f2(0.f);
+        const float m2c = -2.0f * L.cps;
+        auto asym = [&](const float4& u, const float4& w, float v1) {
+          const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
+          const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
+          A1r = __ffma2_rn(ur, f2(q1), A1r);
+          A1i = __ffma2_rn(ui, f2(q1), A1i);
+          A2r = __ffma2_rn(ur, f2(q2), A2r);
+          A2i = __ffma2_rn(ui, f2(q2), A2i);
+          Q = __ffma2_rn(make_float2(w.x, w.y), f2(fmaf(q1, fmaf(m2c, q2, q1), q2 * q2)), Q);
+        };
+        // general bins: direct sums of conj(u) W and w |W|^2
+        float gzr[2] = {0.f, 0.f}, gzi[2] = {0.f, 0.f}, gnn[2] = {0.f, 0.f};
+        auto general = [&](const float4& u, const float4& w, float v1) {
+          const BinW b = bin_w<false>(v1, v1 + L.e2, L.cps, L.sps);
+          const float ww = b.wr * b.wr + b.wi * b.wi;
+          gzr[0] += u.x * b.wr + u.z * b.wi;
+          gzi[0] += u.x * b.wi - u.z * b.wr;
+          gnn[0] += w.x * ww;
+          gzr[1] += u.y * b.wr + u.w * b.wi;
+          gzi[1] += u.y * b.wi - u.w * b.wr;
+          gnn[1] += w.y * ww;
+        };
+        // fully unrolled window when the warp's general bins lie in jp = -G .. G-1: those
+        // first, then the asymptotic bins with their loads kGradDepth bins ahead
+        auto unrolled = [&](auto gtag) {
+          constexpr int G = decltype(gtag)::value;
+          constexpr int kAsym = kNF - 2 * G;
+          auto asym_bin = [](int k) { return k < kNFHalf - G ? k : k + 2 * G; };
+          float4 ru[kGradDepth], rw[kGradDepth];
+#pragma unroll
+          for (int q = 0; q < kGradDepth; ++q) {
+            ru[q] = __ldg(Pp + asym_bin(q) * pitch2);
+            rw[q] = __ldg(Pp + asym_bin(q) * pitch2 + 1);
+          }
+#pragma unroll
+          for (int h = 0; h < 2 * G; ++h) {
+            const int jp = h - G;
+            const float4 u = __ldg(Pp + (kNFHalf + jp) * pitch2), w = __ldg(Pp + (kNFHalf + jp) * pitch2 + 1);
+            general(u, w, (L.aa - (float)jp) * L.sig);
+          }
+#pragma unroll
+          for (int k = 0; k < kAsym; ++k) {
+            const float4 u = ru[k % kGradDepth], w = rw[k % kGradDepth];
+            if (k + kGradDepth < kAsym) {
+              ru[k % kGradDepth] = __ldg(Pp + asym_bin(k + kGradDepth) * pitch2);
+              rw[k % kGradDepth] = __ldg(Pp + asym_bin(k + kGradDepth) * pitch2 + 1);
+            }
+            asym(u, w, (L.aa - (float)(asym_bin(k) - kNFHalf)) * L.sig);
+          }
+        };
+        if (JLO >= -1 && JHI <= 0) {
+          unrolled(GradBins<1>{});
+        } else if (JLO >= -2 && JHI <= 1) {
+          unrolled(GradBins<2>{});
+        } else {
+          const int g0 = max(0, min(kNF, JLO + kNFHalf)), g1 = max(g0, min(kNF, JHI + kNFHalf + 1));
           // the asymptotic bins j in [0, g0) and [g1, kNF) as one counted loop
           const int n_as = kNF - (g1 - g0);
 #pragma unroll kGradUnroll
           for (int i = 0; i < n_as; ++i) {
             const int j = i < g0 ? i : i + (g1 - g0);
-            const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
-            const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
-            const float q1 = rcp_approx(v1), q2 = rcp_approx(v1 + L.e2);
-            const float2 ur = make_float2(u.x, u.y), ui = make_float2(u.z, u.w);
-            A1r = __ffma2_rn(ur, f2(q1), A1r);
-            A1i = __ffma2_rn(ui, f2(q1), A1i);
-            A2r = __ffma2_rn(ur, f2(q2), A2r);
-            A2i = __ffma2_rn(ui, f2(q2), A2i);
-            Q = __ffma2_rn(make_float2(w.x, w.y), f2(fmaf(q1, fmaf(m2c, q2, q1), q2 * q2)), Q);
+            asym(__ldg(Pp + j * pitch2), __ldg(Pp + j * pitch2 + 1),
+                 (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig);
           }
+          for (int j = g0; j < g1; ++j)
+            general(__ldg(Pp + j * pitch2), __ldg(Pp + j * pitch2 + 1),
+                    (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig);
+        }
+        float zr[2], zi[2], nn[2];
+        {
           const float ip = (float)(1.0 / kPi), ip2 = ip * ip;
           const float c = L.cps, sn = L.sps;
-          zr[0] = ip * (A1i.x + sn * A2r.x - c * A2i.x);
-          zi[0] = ip * (A1r.x - c * A2r.x - sn * A2i.x);
-          nn[0] = ip2 * Q.x;
-          zr[1] = ip * (A1i.y + sn * A2r.y - c * A2i.y);
-          zi[1] = ip * (A1r.y - c * A2r.y - sn * A2i.y);
-          nn[1] = ip2 * Q.y;
-        }
-        for (int j = g0; j < g1; ++j) {  // general bins
-          const float4 u = __ldg(Pp + j * pitch2), w = __ldg(Pp + j * pitch2 + 1);
-          const float v1 = (L.aa - (small_int_f(j) - (float)kNFHalf)) * L.sig;
-          const BinW b = bin_w<false>(v1, v1 + L.e2, L.cps, L.sps);
-          const float ww = b.wr * b.wr + b.wi * b.wi;
-          zr[0] += u.x * b.wr + u.z * b.wi;
-          zi[0] += u.x * b.wi - u.z * b.wr;
-          nn[0] += w.x * ww;
-          zr[1] += u.y * b.wr + u.w * b.wi;
-          zi[1] += u.y * b.wi - u.w * b.wr;
-          nn[1] += w.y * ww;
+          zr[0] = ip * (A1i.x + sn * A2r.x - c * A2i.x) + gzr[0];
+          zi[0] = ip * (A1r.x - c * A2r.x - sn * A2i.x) + gzi[0];
+          nn[0] = ip2 * Q.x + gnn[0];
+          zr[1] = ip * (A1i.y + sn * A2r.y - c * A2i.y) + gzr[1];
+          zi[1] = ip * (A1r.y - c * A2r.y - sn * A2i.y) + gzi[1];
+          nn[1] = ip2 * Q.y + gnn[1];
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
