@@ -171,7 +171,10 @@ int tfs_eval_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, const i
  * A batch smaller than about three waves of the kernel (a few thousand templates on a
  * B300) splits each template's segments into up to four work items whose partial sums
  * are added in a fixed order: results are deterministic for a given batch size, and a
- * template's values may differ in the last bits between a small and a large batch. */
+ * template's values may differ in the last bits between a small and a large batch.
+ * A template with no active tranche gets Upsilon = 0 and a zero gradient. The context
+ * keeps per template 1344 bytes of the constants' theta-derivatives and 16 N_seg bytes
+ * of per-segment adjoint weights (device memory, grown as needed). */
 int tfs_grad_statistic(tfs_ctx* ctx, const double* theta, int64_t n_tpl, int32_t n_seg,
                        double* out_stat, double* out_grad, void* stream);
 
