@@ -403,6 +403,27 @@ def main():
     if rejected is not None:
         result["clocks_rejected_first_run"] = rejected
 
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers, on every rank at once (the
+        # whole job's templates over the slowest rank's time)
+        ctx.set_options(path=args.path, pixel=args.pixel, profile=0)
+        th_host = torch.from_numpy(theta_np).pin_memory()
+        out_host = torch.empty((len(N_SEG), n), dtype=torch.float64).pin_memory()
+        ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
+        ets = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
+            torch.cuda.synchronize()
+            ets.append(time.perf_counter() - t0)
+        e2e_s = max_over_ranks(statistics.mean(ets))
+        result["e2e"] = {"value": n_total / e2e_s, "unit": "templates/s",
+                         "h2d_bytes_per_step": int(8 * 8 * n_total),
+                         "d2h_bytes_per_step": int(len(N_SEG) * n_total * (8 + 4))}
+        ctx.set_options(path=args.path, pixel=args.pixel, profile=1, use_graph=use_graph)
+
     if rank == 0 and not args.no_plain and args.path == "mixed":
         mixed_rate = n / (statistics.mean(step_ms) / 1000.0)
         legs = comparison_legs(ctx, theta, args, stream, flush)
@@ -411,22 +432,6 @@ def main():
         result["mixed_vs_plain"] = mixed_rate / legs["plain"]["value"]
         result["mixed_f32_vs_plain"] = legs["mixed_f32"]["value"] / legs["plain"]["value"]
         ctx.set_options(path=args.path, pixel=args.pixel, profile=1, use_graph=use_graph)
-
-    if rank == 0 and not args.no_e2e:
-        ctx.set_options(path=args.path, pixel=args.pixel, profile=0)
-        th_host = torch.from_numpy(theta_np).pin_memory()
-        out_host = torch.empty((len(N_SEG), n), dtype=torch.float64).pin_memory()
-        ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
-        ets = []
-        for _ in range(max(1, min(args.steps, 3))):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ctx.eval_statistic(th_host, N_SEG, out=out_host.numpy())
-            torch.cuda.synchronize()
-            ets.append(time.perf_counter() - t0)
-        result["e2e"] = {"value": n / statistics.mean(ets), "unit": "templates/s",
-                         "h2d_bytes_per_step": int(theta_np.nbytes),
-                         "d2h_bytes_per_step": int(len(N_SEG) * n * (8 + 4))}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -440,6 +445,7 @@ def main():
         print(json.dumps(result), flush=True)
     ctx.close()
     if world > 1:
+        barrier()  # the other ranks wait for rank 0's legs before the group goes away
         torch.distributed.destroy_process_group()
 
 
