@@ -48,6 +48,7 @@ struct tfs_ctx {
   GridDesc g{};
   double dt = 0;
   DevBuf d_re, d_im, w_in, mask, tabD, tabF;
+  DevBuf tdiF;  // per-tranche constellation geometry of the TDI transfer
   // packed pixels
   DevBuf u64, w64, u32, w32, Umix;
   DevBuf Ugrad;            // FP32 mixed-layout plane for the gradient (when Umix is not FP32)
@@ -415,7 +416,7 @@ int tfs_create(tfs_ctx** out, int device, const tfs_options* opt) {
 int tfs_destroy(tfs_ctx* c) {
   if (!c) return TFS_OK;
   cudaSetDevice(c->device);
-  DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->u64,
+  DevBuf* all[] = {&c->d_re, &c->d_im, &c->w_in, &c->mask, &c->tabD, &c->tabF, &c->tdiF, &c->u64,
                    &c->w64, &c->u32, &c->w32, &c->Umix, &c->theta, &c->tpl, &c->tplm,
                    &c->perm, &c->sortbuf, &c->stat, &c->neff, &c->diag, &c->counter,
                    &c->deverr, &c->nseg, &c->idx64, &c->grad, &c->segZ, &c->Ugrad, &c->gpart, &c->gsrc,
@@ -523,13 +524,15 @@ int tfs_load_tf_data(tfs_ctx* c, int n_chan, int n_tranche, int n_bins, double d
   int r;
   if ((r = buf_ensure(c, c->d_re, n * 8)) || (r = buf_ensure(c, c->d_im, n * 8)) ||
       (r = buf_ensure(c, c->tabD, (size_t)n_tranche * sizeof(TrancheD))) ||
-      (r = buf_ensure(c, c->tabF, (size_t)n_tranche * sizeof(TrancheF))))
+      (r = buf_ensure(c, c->tabF, (size_t)n_tranche * sizeof(TrancheF))) ||
+      (r = buf_ensure(c, c->tdiF, (size_t)n_tranche * 7 * sizeof(float4))))
     return r;
   const cudaMemcpyKind k1 = is_device_ptr(d_re) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind k2 = is_device_ptr(d_im) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CUDA_TRY(c, cudaMemcpy(c->d_re.p, d_re, n * 8, k1));
   CUDA_TRY(c, cudaMemcpy(c->d_im.p, d_im, n * 8, k2));
-  CUDA_TRY(c, launch_tranche_table(c->g, (TrancheD*)c->tabD.p, (TrancheF*)c->tabF.p, 0));
+  CUDA_TRY(c, launch_tranche_table(c->g, (TrancheD*)c->tabD.p, (TrancheF*)c->tabF.p,
+                                   (float4*)c->tdiF.p, 0));
   c->launches = 1;
   CUDA_TRY(c, cudaDeviceSynchronize());
   c->has_data = true;
@@ -743,6 +746,7 @@ static int eval_impl(tfs_ctx* c, const double* theta, int64_t n_tpl, const int32
   a.pitch = c->pitch;
   a.tabD = (const TrancheD*)c->tabD.p;
   a.tabF = (const TrancheF*)c->tabF.p;
+  a.tdiF = (const float4*)c->tdiF.p;
   a.u64 = (const double2*)c->u64.p;
   a.w64 = (const double*)c->w64.p;
   a.u32 = (const float2*)c->u32.p;

@@ -89,7 +89,7 @@ __device__ __forceinline__ float bin_x1(const HarmM& q, float j) {
 // single-mode kernel.
 template <bool TDI, bool NEAR>
 __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
-                                         float2 Kh, int h, float sig_k, float dTf) {
+                                         float2 Kh, int h, float sig_k, float dTf, int m) {
   HarmM q;
   q.act = false;
   const df nu = {a.harm.nu_hi[h], a.harm.nu_lo[h]};
@@ -134,7 +134,8 @@ __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, co
       const float pp[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
       const float px[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
       Cplx<float> TA, TE;
-      tdi_transfer<float>(nu.hi * tk.f, tk.ca, tk.sa, nq.x, nq.y, nq.z, pp, px, TA, TE);
+      tdi_transfer_geom<float>(nu.hi * tk.f, tdi_geom_load(a.tdiF + (int64_t)m * kTdiGeomF4), nq.x,
+                               nq.y, nq.z, pp, px, TA, TE);
       fpA = TA.re;
       fxA = -TA.im;
       fpE = TE.re;
@@ -159,10 +160,10 @@ __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, c
   const typename Ld::P* PX = (const typename Ld::P*)a.Umix;
   float N = 0.0f;
   for (int ha = 0; ha < a.harm.n; ++ha) {
-    const HarmM A = harm_of<TDI, kNear>(a, tk, cptr, Kp[ha], ha, sig_k, dTf);
+    const HarmM A = harm_of<TDI, kNear>(a, tk, cptr, Kp[ha], ha, sig_k, dTf, m);
     if (!A.act) continue;
     for (int hb = ha + 1; hb < a.harm.n; ++hb) {
-      const HarmM B = harm_of<TDI, kNear>(a, tk, cptr, Kp[hb], hb, sig_k, dTf);
+      const HarmM B = harm_of<TDI, kNear>(a, tk, cptr, Kp[hb], hb, sig_k, dTf, m);
       if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
       // conj(T_a) T_b per channel
       const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
       for (int h = 0; h < H; ++h) {
         HarmM q;
         q.act = false;
-        if (act) q = harm_of<TDI, kNear>(a, get_track(tks), cptr, Kp[h], h, sig_k, dTf);
+        if (act) q = harm_of<TDI, kNear>(a, get_track(tks), cptr, Kp[h], h, sig_k, dTf, m);
         // general-bin range of the harmonic, joined over the warp (as in the mixed kernel)
         int jlo = 100, jhi = -100;
         if (q.act) {

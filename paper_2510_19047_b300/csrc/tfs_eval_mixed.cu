@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(256, MixedVariant<V>::minb) k_eval_mixed(EvalA
               if (TDI) {  // TDI-1.5 transfer at (t_nm, f_nm)
                 const float4 nq = ldg_nc4(pq + 3);  // (nx, ny, nz, pad)
                 Cplx<float> TA, TE;
-                tdi_transfer<float>(f.hi, tr.ca_hi, tr.sa_hi, nq.x, nq.y, nq.z, pp, px, TA, TE);
+                tdi_transfer_geom<float>(f.hi, tdi_geom_load(a.tdiF + (int64_t)m * kTdiGeomF4), nq.x,
+                                         nq.y, nq.z, pp, px, TA, TE);
                 fp = make_float2(TA.re, TE.re);
                 fx = make_float2(-TA.im, -TE.im);
               } else {

@@ -35,6 +35,7 @@ struct EvalArgs {
   int pitch;                    // m-dimension pitch of the mixed planes
   const TrancheD* tabD;         // [N_t]
   const TrancheF* tabF;         // [N_t]
+  const float4* tdiF;           // [N_t][7]: the constellation geometry of the TDI transfer
   const double2* u64;           // [c][m][k] FP64 u = d~ w
   const double* w64;            // [c][m][k] FP64 w
   const float2* u32;            // [c][m][k] scaled FP32 u
@@ -62,7 +63,8 @@ struct EvalArgs {
   const float2* harm_K;         // [n_tpl][harm.n] frac(nu_h Phi_const) as double-float (mixed path)
 };
 
-cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, cudaStream_t s);
+cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, float4* tdi,
+                                 cudaStream_t s);
 cudaError_t launch_absmax(int64_t n, const double* d_re, const double* d_im, const double* w,
                           unsigned long long* umax, unsigned long long* wmax, int* bad,
                           int n_sm, cudaStream_t s);

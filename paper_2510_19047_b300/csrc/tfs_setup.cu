@@ -9,6 +9,7 @@
 #include "tfs_internal.cuh"
 #include "tfs_kernels.cuh"
 #include "tfs_source.cuh"
+#include "tfs_tdi.cuh"
 
 namespace tfs {
 
@@ -59,7 +60,7 @@ __device__ void lw_tensors(double t, double DA[6], double DE[6], double* ca_out,
   }
 }
 
-__global__ void k_tranche_table(GridDesc g, TrancheD* td, TrancheF* tf) {
+__global__ void k_tranche_table(GridDesc g, TrancheD* td, TrancheF* tf, float4* tdi) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= g.n_tranche) return;
   const double t = g.t0 + (double)m * g.dT;
@@ -80,6 +81,7 @@ __global__ void k_tranche_table(GridDesc g, TrancheD* td, TrancheF* tf) {
     f.D[p] = make_float2((float)d.DA[p], (float)d.DE[p]);
   }
   tf[m] = f;
+  tdi_geom_store(tdi + (int64_t)m * kTdiGeomF4, tdi_geom<double>(d.ca, d.sa));
 }
 
 // Largest |Re u|, |Im u| and w over the grid, and a count of invalid weights
@@ -337,8 +339,9 @@ __global__ void k_check_tpl(const TplConst* __restrict__ tpl, int64_t n, int n_t
 // ---------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------
-cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, cudaStream_t s) {
-  k_tranche_table<<<(g.n_tranche + 127) / 128, 128, 0, s>>>(g, td, tf);
+cudaError_t launch_tranche_table(const GridDesc& g, TrancheD* td, TrancheF* tf, float4* tdi,
+                                 cudaStream_t s) {
+  k_tranche_table<<<(g.n_tranche + 127) / 128, 128, 0, s>>>(g, td, tf, tdi);
   return cudaGetLastError();
 }
 

@@ -64,12 +64,19 @@ __device__ __forceinline__ Cplx<T> cadd(Cplx<T> a, Cplx<T> b) { return {a.re + b
 template <class T>
 __device__ __forceinline__ Cplx<T> csub(Cplx<T> a, Cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
 
-// T_A, T_E at GW frequency f [Hz], orbital phase (ca, sa), source direction n.
+// The constellation's geometry at orbital phase (ca, sa) = (cos a, sin a): spacecraft
+// positions p_i relative to the guiding centre [s] and the products of the unit vectors
+// of arms 01, 02, 12 (xx, yy, zz, xy, xz, yz). It depends on the time only, so the
+// mixed kernels read it from a per-tranche table (tfs_setup.cu) instead of forming it
+// for every template.
 template <class T>
-__device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, const T pp[6],
-                                             const T px[6], Cplx<T>& TA, Cplx<T>& TE) {
-  using M = TdiMath<T>;
-  const T L = T(kArmS);
+struct TdiGeom {
+  T p[3][3];
+  T q[3][6];
+};
+template <class T>
+__device__ __forceinline__ TdiGeom<T> tdi_geom(T ca, T sa) {
+  TdiGeom<T> G;
   const T h3 = T(0.8660254037844386);  // sqrt3 / 2
   const T rad = T(kArmS / 1.7320508075688772);
   const T e1[3] = {h3 * ca, h3 * sa, T(0.5)};
@@ -77,27 +84,79 @@ __device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, 
   // cos and sin of sigma_i = -a + 2 pi i / 3
   const T cs[3] = {ca, T(-0.5) * ca + h3 * sa, T(-0.5) * ca - h3 * sa};
   const T sn[3] = {-sa, T(0.5) * sa + h3 * ca, T(0.5) * sa - h3 * ca};
-  T p[3][3], kp[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[i][k] = rad * (cs[i] * e1[k] + sn[i] * e2[k]);
-    kp[i] = -(nx * p[i][0] + ny * p[i][1] + nz * p[i][2]);  // k . p_i
+    for (int k = 0; k < 3; ++k) G.p[i][k] = rad * (cs[i] * e1[k] + sn[i] * e2[k]);
+  const int arm_i[3] = {0, 0, 1}, arm_j[3] = {1, 2, 2};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const T iL = T(1) / T(kArmS);
+    const int i = arm_i[r], j = arm_j[r];
+    const T a0 = (G.p[j][0] - G.p[i][0]) * iL, a1 = (G.p[j][1] - G.p[i][1]) * iL,
+            a2 = (G.p[j][2] - G.p[i][2]) * iL;
+    G.q[r][0] = a0 * a0;
+    G.q[r][1] = a1 * a1;
+    G.q[r][2] = a2 * a2;
+    G.q[r][3] = a0 * a1;
+    G.q[r][4] = a0 * a2;
+    G.q[r][5] = a1 * a2;
   }
-  // n.P.n of the arm (i, j)
-  auto nPn = [&](int i, int j) {
-    const T iL = T(1) / L;
-    const T a0 = (p[j][0] - p[i][0]) * iL, a1 = (p[j][1] - p[i][1]) * iL, a2 = (p[j][2] - p[i][2]) * iL;
-    const T q[6] = {a0 * a0, a1 * a1, a2 * a2, a0 * a1, a0 * a2, a1 * a2};
+  return G;
+}
+
+// A geometry as a table entry of 7 float4: p[0][0..2], p[1][0..2], p[2][0..2], then
+// q[0][0..5], q[1][0..5], q[2][0..5], one float of padding.
+constexpr int kTdiGeomF4 = 7;
+__device__ __forceinline__ void tdi_geom_store(float4* g, const TdiGeom<double>& G) {
+  float v[4 * kTdiGeomF4];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[i] = (float)G.p[i / 3][i % 3];
+#pragma unroll
+  for (int i = 0; i < 18; ++i) v[9 + i] = (float)G.q[i / 6][i % 6];
+  v[27] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kTdiGeomF4; ++i) g[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ TdiGeom<float> tdi_geom_load(const float4* __restrict__ g) {
+  float v[4 * kTdiGeomF4];
+#pragma unroll
+  for (int i = 0; i < kTdiGeomF4; ++i) {
+    const float4 x = __ldg(g + i);
+    v[4 * i] = x.x;
+    v[4 * i + 1] = x.y;
+    v[4 * i + 2] = x.z;
+    v[4 * i + 3] = x.w;
+  }
+  TdiGeom<float> G;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) G.p[i / 3][i % 3] = v[i];
+#pragma unroll
+  for (int i = 0; i < 18; ++i) G.q[i / 6][i % 6] = v[9 + i];
+  return G;
+}
+
+// The A and E transfer factors from a precomputed geometry (see tdi_transfer).
+template <class T>
+__device__ __forceinline__ void tdi_transfer_geom(T f, const TdiGeom<T>& G, T nx, T ny, T nz,
+                                                  const T pp[6], const T px[6], Cplx<T>& TA,
+                                                  Cplx<T>& TE) {
+  using M = TdiMath<T>;
+  const T L = T(kArmS);
+  T kp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) kp[i] = -(nx * G.p[i][0] + ny * G.p[i][1] + nz * G.p[i][2]);  // k . p_i
+  // n.P.n of arm r
+  auto nPn = [&](int r) {
     T ep = T(0), ex = T(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      ep += q[k] * pp[k];
-      ex += q[k] * px[k];
+      ep += G.q[r][k] * pp[k];
+      ex += G.q[r][k] * px[k];
     }
     return Cplx<T>{ep, -ex};
   };
-  const Cplx<T> q01 = nPn(0, 1), q02 = nPn(0, 2), q12 = nPn(1, 2);
+  const Cplx<T> q01 = nPn(0), q02 = nPn(1), q12 = nPn(2);
   const T fL = f * L;
   // both directions of an arm share the phase factor (k.(p_s + p_r) is symmetric) and
   // differ in the sinc argument (1 - k.n versus 1 + k.n)
@@ -126,6 +185,13 @@ __device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, 
   const T r2 = T(0.7071067811865476), r6 = T(0.4082482904638631);
   TA = {(Z.re - X.re) * r2, (Z.im - X.im) * r2};
   TE = {(X.re - T(2) * Y.re + Z.re) * r6, (X.im - T(2) * Y.im + Z.im) * r6};
+}
+
+// T_A, T_E at GW frequency f [Hz], orbital phase (ca, sa), source direction n.
+template <class T>
+__device__ __forceinline__ void tdi_transfer(T f, T ca, T sa, T nx, T ny, T nz, const T pp[6],
+                                             const T px[6], Cplx<T>& TA, Cplx<T>& TE) {
+  tdi_transfer_geom<T>(f, tdi_geom<T>(ca, sa), nx, ny, nz, pp, px, TA, TE);
 }
 
 // ---------------------------------------------------------------------------------
