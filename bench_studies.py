@@ -33,6 +33,20 @@ import numpy as np
 # the reverse-mode step through track and response (~500): 1250 + 21 x 83 + 500 ~ 3500.
 PEAK_FP32_TFLOPS = 148 * 128 * 2 * 2.032 / 1000.0
 GRAD_FLOP_PER_UNIT = 3500
+# algorithmic FP32 flops per active (template, tranche) unit of the other statistic
+# kernels: the TDI-1.5 transfer adds ~250 to the long-wavelength kernel's 1250; a set of H
+# harmonics costs ~150 per tranche plus ~1150 per harmonic window (counted for every
+# harmonic of an active tranche, so an upper estimate where a window leaves the band)
+TDI_FLOP_PER_UNIT = 1500
+def harm_flop_per_unit(h):
+    return 150 + 1150 * h
+
+
+def _roofline(units, flop_per_unit, kernel_ms, kernel):
+    achieved = units * flop_per_unit / (kernel_ms / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / PEAK_FP32_TFLOPS, "kernel": kernel, "kernel_ms": kernel_ms,
+            "units_per_launch": units, "flop_per_unit": flop_per_unit}
 
 
 def _ctx(D, **kw):
@@ -298,6 +312,10 @@ def tdi(args):
             ks.append(c.last_profile()["statistic"])
         out[f"response{resp}"] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
                                   "kernel_ms": statistics.median(ks)}
+        _, _, dg = c.eval_statistic(th, [256, 64, 16], diag=True)
+        units = int(dg[0].sum().item())
+        out[f"response{resp}"]["roofline"] = _roofline(
+            units, 1250 if resp == 1 else TDI_FLOP_PER_UNIT, statistics.median(ks), "k_eval_mixed")
         c.close()
     return out
 
@@ -337,6 +355,11 @@ def harmonics(args):
             ks.append(c.last_profile()["statistic"])
         out[name] = {"templates_per_s": n / (statistics.median(ss) / 1000.0),
                      "kernel_ms": statistics.median(ks)}
+        _, _, dg = c.eval_statistic(th, lev, diag=True)
+        units = int(dg[0].sum().item())
+        fpu = harm_flop_per_unit(len(nu)) if nu else 1250
+        out[name]["roofline"] = _roofline(units, fpu, statistics.median(ks),
+                                          "k_eval_harm" if nu else "k_eval_mixed")
     nu, cc = sets["nu_half_1_3half"]
     c.set_harmonics(nu, cc)
     sample = bank[:, :192]
