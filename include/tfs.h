@@ -133,9 +133,9 @@ int tfs_load_tf_data(tfs_ctx* ctx, int n_chan, int n_tranche, int n_bins, double
 int tfs_set_noise_weights(tfs_ctx* ctx, const double* inv_psd, const uint8_t* tranche_mask);
 
 /* Replace the loaded data by a noise-only realisation drawn from the current noise
- * weights, for false-alarm backgrounds (Sec. "False alarm probabilities": the paper
- * estimates the background of the search maximum from independent noise-only
- * realisations). Per pixel d~ = sqrt(S / (4 delta f)) (g1 + i g2) with S = 1/w (d~ = 0
+ * weights, for false-alarm backgrounds (Secs. "Search results on the full dataset" and
+ * "Injected and recovered signals": the paper builds the background of the search
+ * maximum from independent noise-only realisations). Per pixel d~ = sqrt(S / (4 delta f)) (g1 + i g2) with S = 1/w (d~ = 0
  * where w = 0), so E|d~|^2 = S / (2 delta f), the data's convention; g1, g2 are
  * independent standard normals from the Box-Muller transform
  *   g1 + i g2 = sqrt(-2 ln(1 - a)) e^{2 pi i b}

@@ -186,8 +186,8 @@ cudaError_t launch_pso_step(const PsoArgs& a, const double* f, int64_t iter, int
 }
 
 // ---------------------------------------------------------------------------------
-// Noise-only data for false-alarm backgrounds (Sec. "False alarm probabilities": the
-// background comes from independent noise-only realisations): per pixel
+// Noise-only data for false-alarm backgrounds (Sec. "Search results on the full dataset":
+// the background comes from independent noise-only realisations): per pixel
 //   d~ = sqrt(S / (4 df)) (g1 + i g2),  S = 1/w (d~ = 0 where w = 0),
 // so that E|d~|^2 = S / (2 df), with g1, g2 independent standard normals from the
 // Box-Muller transform of the two uniforms of one Philox4x32-10 block keyed by the seed,

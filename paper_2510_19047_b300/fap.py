@@ -3,7 +3,8 @@
 The paper estimates the false-alarm probability of a candidate by running the search on
 independent simulated noise-only realisations of the data. This builds the background
 distribution p0 of the search maximum of Upsilon, and two fits extrapolate its tail
-(Sec. "False alarm probabilities", Table "tab:false-alarm"):
+(Sec. "Search results on the full dataset" for the backgrounds; Sec. "Injected and
+recovered signals" and its table of false-alarm probabilities for the fits):
 
 - a power law p0(U) ∝ U^delta above a threshold, which gives the conservative estimate;
 - a Gumbel distribution G(mu, beta) with location mu and scale beta, which gives the
