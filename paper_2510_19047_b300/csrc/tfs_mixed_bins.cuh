@@ -93,7 +93,7 @@ __device__ __forceinline__ float round_f16(float x) { return __half2float(__floa
 
 // The paper's auxiliary Fresnel functions f, g in FP32 with approximate division,
 // branch-free: the rational forms for a <= 6 and the printed asymptotic form
-// f = 1/(pi a), g = 0 beyond (Sec. "Fresnel integrals").
+// f = 1/(pi a), g = 0 beyond (Sec. "Time-frequency waveform representation").
 __device__ __forceinline__ void fg_sel(float a, float& f, float& g) {
   const bool big = a > 6.0f;
   const float num = big ? 1.0f : fmaf(0.926f, a, 1.0f);
