@@ -68,7 +68,9 @@ def precision(args):
     from paper_2510_19047_b300 import synth
     D = synth.week_one_channel(seed=0)
     bank = synth.week_bank(1024, 0)
+    t0 = time.perf_counter()
     ref = oracle.statistic(D.d, D.w, D.mask, bank, 8, D.dT)[0]
+    oracle_s = time.perf_counter() - t0
     # the FP64 path carries the phase in FP64 (double-double), the mixed paths in
     # double-float; f16all / bf16all hold u, w and the template values in 16 bits
     variants = [("fp64", "f32"), ("plain", "f32"), ("mixed", "f32"), ("mixed", "f16"),
@@ -79,7 +81,9 @@ def precision(args):
         c = _ctx(D, path=path, pixel=pix)
         got = c.eval_statistic(bank, 8)[0]
         mx, p99 = _rel(got, ref)
-        errors[f"{path}-{pix}"] = {"max": mx, "p99": p99}
+        t0 = time.perf_counter()
+        c.eval_statistic(bank, 8)  # host in, host out: synchronous
+        errors[f"{path}-{pix}"] = {"max": mx, "p99": p99, "gpu_s": time.perf_counter() - t0}
         ctxs[(path, pix)] = c
     # ROC: threshold = (1 - FAP) quantile over noise-only realisations of the bank's
     # largest Upsilon_8; detection = matched template above it in signal realisations
@@ -105,6 +109,7 @@ def precision(args):
                                  "p_detect": float(np.mean(np.array(matched[v]) > thr))}
     base = roc["fp64-f32"]["p_detect"]
     return {"study": "precision", "workload": "1ch-week-256x512, 1024 templates, N_seg 8",
+            "oracle_s": oracle_s, "oracle_threads": oracle.max_threads(),
             "error_vs_oracle": errors, "roc": roc, "roc_fap": fap, "roc_snr": snr,
             "roc_realisations": n_real,
             "max_p_detect_shift_vs_fp64": max(abs(r["p_detect"] - base) for r in roc.values())}
