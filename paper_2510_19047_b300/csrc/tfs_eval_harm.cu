@@ -40,17 +40,16 @@ struct TrackH {
   float amp;   // (f / F0)^(2/3)
   float f;     // f_nm (FP32, for the TDI transfer)
   float fpA, fxA, fpE, fxE;  // long-wavelength F+, Fx of A and E
-  float ca, sa;              // orbital phase of the tranche (TDI transfer)
 };
-constexpr int kTrkF = 15;  // floats of a TrackH
+constexpr int kTrkF = 11;  // floats of a TrackH
 
 // A lane's TrackH in shared memory (field k at t[32 k]): held there across the
 // harmonic loop instead of in registers.
 __device__ __forceinline__ void put_track(float* t, const TrackH& k) {
   const float v[kTrkF] = {k.x.hi, k.x.lo, k.S.hi, k.S.lo, k.fdot, k.amp, k.f, k.fpA, k.fxA, k.fpE,
-                          k.fxE, k.ca, k.sa, 0.f, 0.f};
+                          k.fxE};
 #pragma unroll
-  for (int i = 0; i < 13; ++i) t[32 * i] = v[i];
+  for (int i = 0; i < kTrkF; ++i) t[32 * i] = v[i];
 }
 __device__ __forceinline__ TrackH get_track(const float* t) {
   TrackH k;
@@ -63,8 +62,6 @@ __device__ __forceinline__ TrackH get_track(const float* t) {
   k.fxA = t[256];
   k.fpE = t[288];
   k.fxE = t[320];
-  k.ca = t[352];
-  k.sa = t[384];
   return k;
 }
 
@@ -265,7 +262,6 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
       tk.fdot = 1.f;
       tk.amp = tk.f = 0.f;
       tk.fpA = tk.fxA = tk.fpE = tk.fxE = 0.f;
-      tk.ca = tk.sa = 0.f;
       if (act) {
         const float4* cq = reinterpret_cast<const float4*>(cptr);
         const float4 c0 = ldg_nc4(cq), c1 = ldg_nc4(cq + 1), c2 = ldg_nc4(cq + 2),
@@ -276,8 +272,6 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
         const df C2 = {c3.x, c3.y};
         const float fd_k = c3.z, C2x5 = c3.w;
         const TrancheF tr = a.tabF[m];
-        tk.ca = tr.ca_hi;
-        tk.sa = tr.sa_hi;
         const df tt = {tr.t_hi, tr.t_lo};
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (a.response) {
