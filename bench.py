@@ -381,7 +381,7 @@ def main():
             "kernel": "k_eval_mixed", "kernel_ms": kms, "units_per_launch": units,
             "flop_per_unit": flop_per_unit(D.n_chan),
             "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz"}
-    if clocks.get("sm_mhz"):
+    if clocks and clocks.get("sm_mhz"):
         # the same peak at the median SM clock sampled under load (the power cap can hold
         # the clock below its maximum)
         at = PEAK_FP32_TFLOPS * clocks["sm_mhz"] / 2032.0
