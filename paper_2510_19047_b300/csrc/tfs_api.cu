@@ -1084,18 +1084,19 @@ int tfs_grad_statistic(tfs_ctx* c, const double* theta, int64_t n_tpl, int32_t n
   }
   prof_record(c, 2, s);
   const double scale = 4.0 * c->g.df * c->sw / (c->su * c->su);
-  int parts = 1;
-  CUDA_TRY(c, grad_plan(c->opt.response, n_seg, c->n_sm, n_tpl, &parts));
-  if (parts > 1 && (r = buf_ensure(c, c->gpart, (size_t)parts * 9 * n_tpl * 8))) return r;
+  int parts = 1, parts_a = 1;
+  CUDA_TRY(c, grad_plan(c->opt.response, n_seg, c->n_sm, n_tpl, &parts, &parts_a));
+  const int parts_max = std::max(parts, parts_a);
+  if (parts_max > 1 && (r = buf_ensure(c, c->gpart, (size_t)parts_max * 9 * n_tpl * 8))) return r;
   if ((r = buf_ensure(c, c->gsrc, grad_src_bytes(n_tpl)))) return r;
   if ((r = buf_ensure(c, c->segZ, (size_t)n_tpl * n_seg * 16))) return r;
   CUDA_TRY(c, launch_grad(c->g, mix_const(c->g), c->opt.response, c->opt.pn_order, c->pitch,
                           (const TrancheF*)c->tabF.p, (const float4*)plane,
                           (const uint8_t*)c->mask.p, (const double*)th, (const TplConst*)c->tpl.p,
                           (const TplMix*)c->tplm.p, n_tpl, n_seg, scale, os, og,
-                          (unsigned*)c->counter.p, perm, parts, (double*)c->gpart.p,
+                          (unsigned*)c->counter.p, perm, parts, parts_a, (double*)c->gpart.p,
                           (double*)c->gsrc.p, (float4*)c->segZ.p, c->n_sm, s));
-  c->launches += parts > 1 ? 4 : 3;
+  c->launches += parts_max > 1 ? 4 : 3;
   prof_record(c, 3, s);
   if (!dev_stat) CUDA_TRY(c, cudaMemcpyAsync(out_stat, os, (size_t)n_tpl * 8, cudaMemcpyDeviceToHost, s));
   if (!dev_grad) CUDA_TRY(c, cudaMemcpyAsync(out_grad, og, (size_t)n_tpl * 64, cudaMemcpyDeviceToHost, s));

@@ -292,7 +292,9 @@ struct GradArgs {
   unsigned* counter;    // work tickets of the persistent launches: [0] pass A, [1] pass B
   const int32_t* perm;  // queue order (longest templates first), or null for 0..n-1
   int parts;            // work items per template: contiguous groups of its segments
-  double* part_out;     // parts > 1: [parts][9][n] partial (Upsilon, gradient) sums
+  int parts_a;          // work items per template of pass A (it holds more warps)
+  double* part_out;     // [max(parts, parts_a)][9][n] partial sums: field 0 (Upsilon) from
+                        // pass A when parts_a > 1, fields 1-8 from pass B when parts > 1
   const double* dsrc;   // [n][8][kSrcFields]: d(template constant)/d theta_p (k_grad_src)
   float4* lam;          // [n][n_seg]: (Re lambda, Im lambda, mu, 0) per segment (k_grad_a)
 };
@@ -548,14 +550,14 @@ __device__ __forceinline__ float tdi_adjoint(const TplMix* cp, const Trk& k, con
 // to the template's (in a fixed order, by k_grad_reduce).
 // Tranche range [mA, mB) of work item (template with range [m_lo, m_hi), group h);
 // false for an empty group.
-__device__ __forceinline__ bool item_range(const GradArgs& a, int m_lo, int m_hi, int h, int& mA,
-                                           int& mB) {
+__device__ __forceinline__ bool item_range(const GradArgs& a, int parts, int m_lo, int m_hi, int h,
+                                           int& mA, int& mB) {
   mA = m_lo;
   mB = m_hi;
-  if (a.parts > 1 && mB > mA) {
+  if (parts > 1 && mB > mA) {
     const int s_lo = mA / a.seg_len, n_s = (mB - 1) / a.seg_len - s_lo + 1;
-    mA = max(mA, (s_lo + (h * n_s) / a.parts) * a.seg_len);
-    mB = min(mB, (s_lo + ((h + 1) * n_s) / a.parts) * a.seg_len);
+    mA = max(mA, (s_lo + (h * n_s) / parts) * a.seg_len);
+    mB = min(mB, (s_lo + ((h + 1) * n_s) / parts) * a.seg_len);
   }
   return mB > mA;
 }
@@ -731,7 +733,7 @@ __device__ __forceinline__ void grad_one(const GradArgs& a, int64_t i, int h, in
   const TplConst tc = a.tpl[i];
   const TplMix* cp = a.tplm + i;
   int mA, mB;
-  if (!item_range(a, tc.m_lo, tc.m_hi, h, mA, mB)) {  // empty group: zero gradient
+  if (!item_range(a, a.parts, tc.m_lo, tc.m_hi, h, mA, mB)) {  // empty group: zero gradient
     if (lane >= 1 && lane < 9) {
       if (a.parts > 1)
         a.part_out[((int64_t)h * 9 + lane) * a.n_tpl + i] = 0.0;
@@ -996,13 +998,15 @@ __global__ void k_grad_src(const double* __restrict__ theta, int64_t n, int pn_o
 size_t grad_src_bytes(int64_t n) { return (size_t)n * 8 * kSrcFields * sizeof(double); }
 
 // Sum of the work items' partial sums, h = 0 .. parts-1 in order (deterministic).
-__global__ void k_grad_reduce(const double* __restrict__ part, int parts, int64_t n,
+__global__ void k_grad_reduce(const double* __restrict__ part, int parts_a, int parts, int64_t n,
                               double* __restrict__ out_stat, double* __restrict__ out_grad) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 9 * n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = t / n, i = t - r * n;
+    const int np = r == 0 ? parts_a : parts;
+    if (np <= 1) continue;  // that pass wrote its output directly
     double v = 0.0;
-    for (int h = 0; h < parts; ++h) v += part[((int64_t)h * 9 + r) * n + i];
+    for (int h = 0; h < np; ++h) v += part[((int64_t)h * 9 + r) * n + i];
     if (r == 0)
       out_stat[i] = v;
     else
@@ -1031,16 +1035,16 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 4 : TFS_GRADA_MINB) k_g
     unsigned t = 0;
     if (lane == 0) t = atomicAdd(a.counter, 1u);
     t = __shfl_sync(kFullG, t, 0);
-    if ((int64_t)t >= a.n_tpl * a.parts) break;  // whole warp leaves together
-    const int64_t q = (int64_t)(t / (unsigned)a.parts);
-    const int h = (int)(t - (unsigned)q * (unsigned)a.parts);
+    if ((int64_t)t >= a.n_tpl * a.parts_a) break;  // whole warp leaves together
+    const int64_t q = (int64_t)(t / (unsigned)a.parts_a);
+    const int h = (int)(t - (unsigned)q * (unsigned)a.parts_a);
     const int64_t i = a.perm ? (int64_t)a.perm[q] : q;
     int mA, mB;
     double ups = 0.0;
-    if (item_range(a, a.tpl[i].m_lo, a.tpl[i].m_hi, h, mA, mB))
+    if (item_range(a, a.parts_a, a.tpl[i].m_lo, a.tpl[i].m_hi, h, mA, mB))
       ups = grad_pass_a<TDI>(a, i, mA, mB, lane, seg);
     if (lane == 0) {
-      if (a.parts > 1)
+      if (a.parts_a > 1)
         a.part_out[(int64_t)h * 9 * a.n_tpl + i] = ups;
       else
         a.out_stat[i] = ups;
@@ -1068,15 +1072,26 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
 // Resident warps of the gradient kernel and the number of work items per template:
 // a small batch (fewer than ~3 waves of templates) splits each template's segments into
 // up to 4 groups so that the persistent queue still ends in a short tail.
-cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts) {
-  auto kern = response == 2 ? k_grad<true> : k_grad<false>;
+cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts, int* parts_a) {
+  auto split = [&](int per_sm) {
+    const int64_t resident = (int64_t)n_sm * std::max(per_sm, 1) * kGradWarps;
+    int p = 1;
+    while (p < kGradMaxParts && p < n_seg && n * p < 3 * resident) ++p;
+    return p;
+  };
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, response == 2 ? k_grad<true> : k_grad<false>, kGradWarps * 32, 0);
   if (e != cudaSuccess) return e;
-  const int64_t resident = (int64_t)n_sm * std::max(per_sm, 1) * kGradWarps;
-  int p = 1;
-  while (p < kGradMaxParts && p < n_seg && n * p < 3 * resident) ++p;
-  *parts = p;
+  *parts = split(per_sm);
+  // pass A's occupancy with its shared segment slots
+  const size_t smem = (size_t)kGradWarps * n_seg * sizeof(float4);
+  auto kern_a = response == 2 ? k_grad_a<true> : k_grad_a<false>;
+  e = cudaFuncSetAttribute(kern_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern_a, kGradWarps * 32, smem);
+  if (e != cudaSuccess) return e;
+  *parts_a = split(per_sm);
   return cudaSuccess;
 }
 
@@ -1084,10 +1099,12 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        unsigned* counter, const int32_t* perm, int parts, double* part_buf,
-                        double* src_buf, float4* lam_buf, int n_sm, cudaStream_t s) {
+                        unsigned* counter, const int32_t* perm, int parts, int parts_a,
+                        double* part_buf, double* src_buf, float4* lam_buf, int n_sm,
+                        cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  if (parts < 1 || parts > kGradMaxParts || (parts > 1 && !part_buf) || !src_buf || !lam_buf)
+  if (parts < 1 || parts > kGradMaxParts || parts_a < 1 || parts_a > kGradMaxParts ||
+      ((parts > 1 || parts_a > 1) && !part_buf) || !src_buf || !lam_buf)
     return cudaErrorInvalidValue;
   k_grad_src<<<(unsigned)((n * 8 + 127) / 128), 128, 0, s>>>(theta, n, pn_order, src_buf);
   GradArgs a;
@@ -1113,10 +1130,10 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
   a.counter = counter;
   a.perm = perm;
   a.parts = parts;
+  a.parts_a = parts_a;
   a.part_out = part_buf;
   a.dsrc = src_buf;
   a.lam = lam_buf;
-  const int64_t need = (n * parts + kGradWarps - 1) / kGradWarps;
   cudaError_t e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s);  // tickets of A and B
   if (e != cudaSuccess) return e;
   // pass A: Upsilon and (lambda, mu) per segment
@@ -1128,6 +1145,7 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, smem);
     if (e != cudaSuccess) return e;
+    const int64_t need = (n * parts_a + kGradWarps - 1) / kGradWarps;
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
     kern<<<(unsigned)ctas, kGradWarps * 32, smem, s>>>(a);
     e = cudaGetLastError();
@@ -1139,13 +1157,14 @@ cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGradWarps * 32, 0);
     if (e != cudaSuccess) return e;
+    const int64_t need = (n * parts + kGradWarps - 1) / kGradWarps;
     const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)n_sm * std::max(per_sm, 1)));
     kern<<<(unsigned)ctas, kGradWarps * 32, 0, s>>>(a);
     e = cudaGetLastError();
   }
-  if (e != cudaSuccess || parts == 1) return e;
+  if (e != cudaSuccess || (parts == 1 && parts_a == 1)) return e;
   const int64_t blocks = std::min<int64_t>((9 * n + 255) / 256, (int64_t)n_sm * 8);
-  k_grad_reduce<<<(unsigned)blocks, 256, 0, s>>>(part_buf, parts, n, out_stat, out_grad);
+  k_grad_reduce<<<(unsigned)blocks, 256, 0, s>>>(part_buf, parts_a, parts, n, out_stat, out_grad);
   return cudaGetLastError();
 }
 

@@ -144,13 +144,14 @@ cudaError_t launch_ascent(double* theta, const double* grad, int64_t n, const As
 // Work items per template of the gradient kernel (1 .. kGradMaxParts) for a batch of n:
 // parts > 1 needs a [parts][9][n] FP64 buffer for the partial sums.
 constexpr int kGradMaxParts = 4;
-cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts);
+cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts, int* parts_a);
 cudaError_t launch_grad(const GridDesc& g, const MixConst& mc, int response, int pn_order,
                         int pitch, const TrancheF* tabF, const float4* P, const uint8_t* mask,
                         const double* theta, const TplConst* tpl, const TplMix* tplm, int64_t n,
                         int n_seg, double scale, double* out_stat, double* out_grad,
-                        unsigned* counter, const int32_t* perm, int parts, double* part_buf,
-                        double* src_buf, float4* lam_buf, int n_sm, cudaStream_t s);
+                        unsigned* counter, const int32_t* perm, int parts, int parts_a,
+                        double* part_buf, double* src_buf, float4* lam_buf, int n_sm,
+                        cudaStream_t s);
 // Bytes of launch_grad's src_buf for n templates (the constants' theta-derivatives);
 // lam_buf holds n * n_seg float4 (the segments' adjoint weights).
 size_t grad_src_bytes(int64_t n);
