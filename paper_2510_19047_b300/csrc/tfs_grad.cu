@@ -1072,11 +1072,17 @@ __global__ void __launch_bounds__(kGradWarps * 32, TDI ? 2 : TFS_GRAD_MINB) k_gr
 // Resident warps of the gradient kernel and the number of work items per template:
 // a small batch (fewer than ~3 waves of templates) splits each template's segments into
 // up to 4 groups so that the persistent queue still ends in a short tail.
+// A batch is split until its work items fill about kGradWaves waves of resident warps.
+#ifndef TFS_GRAD_WAVES
+#define TFS_GRAD_WAVES 3
+#endif
+constexpr int kGradWaves = TFS_GRAD_WAVES;
+
 cudaError_t grad_plan(int response, int n_seg, int n_sm, int64_t n, int* parts, int* parts_a) {
   auto split = [&](int per_sm) {
     const int64_t resident = (int64_t)n_sm * std::max(per_sm, 1) * kGradWarps;
     int p = 1;
-    while (p < kGradMaxParts && p < n_seg && n * p < 3 * resident) ++p;
+    while (p < kGradMaxParts && p < n_seg && n * p < kGradWaves * resident) ++p;
     return p;
   };
   int per_sm = 0;
