@@ -381,6 +381,61 @@ def test_two_year_full_bank_sampled(two_year):
             assert rel_err(got[i], ref)[0] < tol, (path, L)
 
 
+def _four_bin_window_share(D, th):
+    """Per template, the share of its active tranches that sit in 32-tranche blocks whose
+    general-form bins all lie in jp = -2 .. 1 with at least one lane beyond jp = -1, 0:
+    the blocks the statistic kernel evaluates in its four-general-bin window. From the
+    oracle's track with the kernel's test (a bin needs the general form when |v| <= 6
+    on either offset or the sweep crosses it: jp in [ceil(a - 6/sigma), floor(a + eps +
+    6/sigma)], a = f/df - ceil(f/df), with a 0.01-bin margin)."""
+    from oracle.api import PN_1PN, RESP_LW
+    live = np.flatnonzero(D.mask)
+    df = 1.0 / D.dT
+    share = np.zeros(th.shape[1])
+    for j in range(th.shape[1]):
+        tr = oracle.track(th[:, j], live * D.dT, pn_order=PN_1PN, response=RESP_LW)
+        x, fd = tr["f"] / df, tr["fdot"]
+        ok = np.isfinite(x) & (fd > 0) & (np.ceil(x) - 10 >= 1) & (np.ceil(x) + 10 <= D.n_bins - 1)
+        if not ok.any():
+            continue
+        fd = np.where(fd > 0, fd, 1.0)
+        r6 = 6.0 / (df * np.sqrt(2.0 / fd))
+        a = x - np.ceil(x)
+        lo = np.ceil(a - r6 - 0.01)
+        hi = np.floor(a + fd * D.dT * D.dT + r6 + 0.01)
+        act = np.flatnonzero(ok)
+        n4 = 0
+        for b0 in range(act[0], act[-1] + 1, 32):
+            o = ok[b0:b0 + 32]
+            if o.any():
+                JLO, JHI = lo[b0:b0 + 32][o].min(), hi[b0:b0 + 32][o].max()
+                if JLO >= -2 and JHI <= 1 and not (JLO >= -1 and JHI <= 0):
+                    n4 += int(o.sum())
+        share[j] = n4 / ok.sum()
+    return share
+
+
+@pytest.mark.parametrize("pixel", ["f16", "f32"])
+def test_four_general_bin_window(two_year, pixel):
+    """Templates of the bench bank chosen for the tranche blocks that the statistic
+    kernel evaluates in its four-general-bin window (18 % of the units on this bank),
+    against the oracle at N_seg 256/64/16."""
+    D = two_year
+    pool = synth.two_year_bank(400, seed=2002)
+    share = _four_bin_window_share(D, pool)
+    pick = np.argsort(share)[-16:]
+    assert share[pick].min() > 0.3  # these templates really use that window
+    th = pool[:, pick]
+    lev = [256, 64, 16]
+    got, neff, _ = ctx_for(D, "mixed", pixel).eval_statistic(th, lev)
+    tol = TOL[("mixed", pixel)][0]
+    for i, L in enumerate(lev):
+        ref, rneff, _, _ = oracle.statistic(D.d, D.w, D.mask, th, L, D.dT, pn_order=1, response=1)
+        mx, _ = rel_err(got[i], ref)
+        assert mx < tol, (pixel, L, mx)
+        assert np.array_equal(neff[i], rneff)
+
+
 def test_graph_replay_with_profiling(ae45, ae45_bank):
     """The bench's call pattern: a profiled context replaying a CUDA graph, first with
     the diagnostic outputs and then without, repeatedly; the kernel times are reported
