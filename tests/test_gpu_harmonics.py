@@ -145,8 +145,9 @@ def test_harmonic_settings_and_errors(ae45, bank):
 
 def test_two_year_full_bank_three_harmonics_sampled():
     """The bench workload with three harmonics (1e6 templates, N_seg 256/64/16 in one
-    launch of the harmonic kernel): sampled templates against the oracle, the FP64 path
-    on the same sample, and properties that hold for every template."""
+    launch of the harmonic kernel): 60 templates spread over the queue against the
+    oracle (max and p99), the FP64 path on the same sample, and properties that hold for
+    every template."""
     import torch
     D = synth.cached(synth.two_year_two_channel)
     lev = [256, 64, 16]
@@ -159,13 +160,14 @@ def test_two_year_full_bank_three_harmonics_sampled():
     assert np.all(st[0] >= st[1] * (1 - 3e-3)) and np.all(st[1] >= st[2] * (1 - 3e-3))
     act = ne[0] > 0
     assert abs(np.mean(st[0][act]) / np.mean(2 * ne[0][act]) - 1) < 0.02  # noise: chi^2
-    idx = np.linspace(0, th.shape[1] - 1, 12).astype(int)
+    idx = np.linspace(0, th.shape[1] - 1, 60).astype(int)
     t64 = ctx_for(D, "fp64", "f16", NU, C)
     g64, _, _ = t64.eval_statistic(th[:, idx], lev)
     for i, L in enumerate(lev):
         ref, rneff, _, _ = oracle.statistic_harm(D.d, D.w, D.mask, th[:, idx], L, D.dT, NU, C,
                                                  pn_order=1, response=1)
-        assert rel_err(st[i, idx], ref)[0] < TOL[("mixed", "f16")][0], L
+        mx, p99 = rel_err(st[i, idx], ref)
+        assert mx < TOL[("mixed", "f16")][0] and p99 < TOL[("mixed", "f16")][1], (L, mx, p99)
         assert np.array_equal(ne[i, idx], rneff)
         assert rel_err(g64[i], ref)[0] < FP64_TOL, L
 
