@@ -73,7 +73,7 @@ def parse():
     p.add_argument("--no-graph", action="store_true",
                    help="headline step without CUDA-graph replay")
     p.add_argument("--cpu-sample", type=int, default=1200)  # ~10-20 s of oracle work
-    p.add_argument("--ref-sample", type=int, default=48)    # per reference-arm step
+    p.add_argument("--ref-sample", type=int, default=192)   # per reference-arm step (12 per host thread on 16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
