@@ -53,7 +53,7 @@ def _worker(rank, world, port, n, k, out):
 def test_two_ranks_gloo():
     n, k, world = 5000, 50, 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a threaded process
         out = m.dict()
         mp.spawn(_worker, args=(world, port, n, k, out), nprocs=world, join=True)
         res = dict(out)
