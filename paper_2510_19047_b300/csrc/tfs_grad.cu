@@ -259,8 +259,9 @@ struct TdiMath<DF4> {
       float s, c;
       const float r = x.v - 2.0f * rint_small(0.5f * x.v);
       __sincosf(3.141592654f * r, &s, &c);
-      v = s / px;
-      dv = (c - v) / x.v;
+      const float ipx = rcp_approx(px);  // 1/x = pi/(pi x)
+      v = s * ipx;
+      dv = (c - v) * (3.141592654f * ipx);
     }
     DF4 o;
     o.v = v;

@@ -143,6 +143,7 @@ __device__ __forceinline__ void tdi_transfer_geom(T f, const TdiGeom<T>& G, T nx
                                                   Cplx<T>& TE) {
   using M = TdiMath<T>;
   const T L = T(kArmS);
+  const T iL = T(1.0 / kArmS);  // a product, not a division per arm
   T kp[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) kp[i] = -(nx * G.p[i][0] + ny * G.p[i][1] + nz * G.p[i][2]);  // k . p_i
@@ -161,7 +162,7 @@ __device__ __forceinline__ void tdi_transfer_geom(T f, const TdiGeom<T>& G, T nx
   // both directions of an arm share the phase factor (k.(p_s + p_r) is symmetric) and
   // differ in the sinc argument (1 - k.n versus 1 + k.n)
   auto arm = [&](int i, int j, Cplx<T> q, Cplx<T>& Gij, Cplx<T>& Gji) {
-    const T kn = (kp[j] - kp[i]) / L;  // k . n_ij
+    const T kn = (kp[j] - kp[i]) * iL;  // k . n_ij
     T s, c;
     M::cis_cycles(T(-0.5) * f * (L + kp[i] + kp[j]), s, c);
     const Cplx<T> eq = cmul(Cplx<T>{c, s}, Cplx<T>{-q.im, q.re});  // i q e^{i ph}
@@ -178,13 +179,15 @@ __device__ __forceinline__ void tdi_transfer_geom(T f, const TdiGeom<T>& G, T nx
   M::cis_cycles(-fL, zs, zc);
   const Cplx<T> z = {zc, zs};
   const Cplx<T> z2 = cmul(z, z);
-  const Cplx<T> w = {T(1) - z2.re, -z2.im};
-  const Cplx<T> X = cmul(w, csub(cadd(G10, cmul(z, G01)), cadd(G20, cmul(z, G02))));
-  const Cplx<T> Y = cmul(w, csub(cadd(G21, cmul(z, G12)), cadd(G01, cmul(z, G10))));
-  const Cplx<T> Z = cmul(w, csub(cadd(G02, cmul(z, G20)), cadd(G12, cmul(z, G21))));
+  // X, Y, Z share the factor w = 1 - z^2: the combinations A and E are formed first
+  // and multiplied by w / sqrt2 and w / sqrt6
   const T r2 = T(0.7071067811865476), r6 = T(0.4082482904638631);
-  TA = {(Z.re - X.re) * r2, (Z.im - X.im) * r2};
-  TE = {(X.re - T(2) * Y.re + Z.re) * r6, (X.im - T(2) * Y.im + Z.im) * r6};
+  const Cplx<T> w2 = {(T(1) - z2.re) * r2, -z2.im * r2}, w6 = {(T(1) - z2.re) * r6, -z2.im * r6};
+  const Cplx<T> X = csub(cadd(G10, cmul(z, G01)), cadd(G20, cmul(z, G02)));
+  const Cplx<T> Y = csub(cadd(G21, cmul(z, G12)), cadd(G01, cmul(z, G10)));
+  const Cplx<T> Z = csub(cadd(G02, cmul(z, G20)), cadd(G12, cmul(z, G21)));
+  TA = cmul(w2, csub(Z, X));
+  TE = cmul(w6, Cplx<T>{X.re - T(2) * Y.re + Z.re, X.im - T(2) * Y.im + Z.im});
 }
 
 // T_A, T_E at GW frequency f [Hz], orbital phase (ca, sa), source direction n.
@@ -211,6 +214,7 @@ __device__ __forceinline__ void tdi_arms(T f, G ca, G sa, T nx, T ny, T nz, TdiA
                                          G q[3][6]) {
   using M = TdiMath<T>;
   const G L = G(kArmS);
+  const G iL = G(1.0 / kArmS);
   const G h3 = G(0.8660254037844386);
   const G rad = G(kArmS / 1.7320508075688772);
   const G e1[3] = {h3 * ca, h3 * sa, G(0.5)};
@@ -228,8 +232,8 @@ __device__ __forceinline__ void tdi_arms(T f, G ca, G sa, T nx, T ny, T nz, TdiA
   const int ai[3] = {0, 0, 1}, aj[3] = {1, 2, 2};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const G a0 = (p[aj[r]][0] - p[ai[r]][0]) / L, a1 = (p[aj[r]][1] - p[ai[r]][1]) / L,
-            a2 = (p[aj[r]][2] - p[ai[r]][2]) / L;
+    const G a0 = (p[aj[r]][0] - p[ai[r]][0]) * iL, a1 = (p[aj[r]][1] - p[ai[r]][1]) * iL,
+            a2 = (p[aj[r]][2] - p[ai[r]][2]) * iL;
     q[r][0] = a0 * a0;
     q[r][1] = a1 * a1;
     q[r][2] = a2 * a2;
@@ -241,7 +245,7 @@ __device__ __forceinline__ void tdi_arms(T f, G ca, G sa, T nx, T ny, T nz, TdiA
   // link coefficient c_sr = i pi f L sinc(pi f L (1 - k.n_sr)) e^{-i pi f (L + k.(p_s + p_r))};
   // both directions of an arm share the phase factor
   auto lc = [&](int i, int j, Cplx<T>& cij, Cplx<T>& cji) {
-    const T kn = (kp[j] - kp[i]) / L;
+    const T kn = (kp[j] - kp[i]) * iL;
     T s, c;
     M::cis_cycles(T(-0.5) * f * (L + kp[i] + kp[j]), s, c);
     const T pfl = T(kPi) * fL;
