@@ -374,8 +374,7 @@ __device__ __forceinline__ Trk track_df(const GradArgs& a, const TplMix* cp, int
   float cyc = __fadd_rn(__fsub_rn(ph.hi, rintf(ph.hi)), ph.lo);
   cyc = __fsub_rn(cyc, rint_small(cyc));
   __sincosf(6.283185307f * cyc, &k.sph, &k.cph);
-  const float cb = cbrtf(onec.hi);
-  k.amp = y2f * cb * cb;
+  k.amp = y2f * pow_2_3(onec.hi);  // (f/F0)^(2/3) = y^2 (1 + C2 y^2)^(2/3)
   k.P = k.amp * rsqrt_approx(2.0f * fdot);
   k.u = u.hi;
   k.tpr = tpr.hi;

@@ -241,6 +241,14 @@ __device__ __forceinline__ float pow_m18(float x) {
   return r;
 }
 
+// x^(2/3) the same way (x near 1: ~1e-7 relative, as a cube root squared).
+__device__ __forceinline__ float pow_2_3(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"((2.0f / 3.0f) * l));
+  return r;
+}
+
 __device__ __forceinline__ df two_prod(float a, float b) {
   df r;
   r.hi = __fmul_rn(a, b);
