@@ -294,7 +294,7 @@ def tdi(args):
     long-wavelength one (code 1) on the bench's two-year workload: 1e6 templates,
     N_seg 256/64/16 in one pass. The timing does not depend on the data's content;
     parity of the TDI path is tested on a 45-day grid whose injections went through
-    the time-domain single-link response."""
+    the time-domain single-link response, and on templates sampled from this launch."""
     import torch
     from paper_2510_19047_b300 import synth
     from paper_2510_19047_b300.binding import TFS

@@ -384,6 +384,33 @@ def test_two_year_full_bank_sampled(two_year):
             assert rel_err(got[i], ref)[0] < tol, (path, L)
 
 
+def test_two_year_full_bank_sampled_tdi(two_year):
+    """The TDI study's workload: the bench bank (1e6 templates, N_seg 256/64/16 in one
+    mixed launch, FP16 pixels) with the TDI-1.5 response (code 2): 120 templates spread
+    over the sorted queue's range against the oracle (max and p99 at the FP16 bounds),
+    N_eff exact, the active-tranche count within one."""
+    import torch
+    from paper_2510_19047_b300.binding import TFS
+    D = two_year
+    lev = [256, 64, 16]
+    th = synth.two_year_bank(1_000_000, seed=2002)
+    c = TFS(0, path="mixed", pixel="f16", pn_order=D.pn_order, response=2)
+    c.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    c.set_noise_weights(D.w, D.mask)
+    st, ne, dg = c.eval_statistic(torch.from_numpy(th).cuda(), lev, diag=True)
+    st, ne, dg = st.cpu().numpy(), ne.cpu().numpy(), dg.cpu().numpy()
+    assert np.all(np.isfinite(st)) and np.all(st >= 0)
+    idx = np.linspace(0, th.shape[1] - 1, 120).astype(int)
+    for i, L in enumerate(lev):
+        ref, rneff, rnact, _ = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT,
+                                                pn_order=1, response=2)
+        mx, p99 = rel_err(st[i, idx], ref)
+        assert mx < TOL[("mixed", "f16")][0] and p99 < TOL[("mixed", "f16")][1], (L, mx, p99)
+        assert np.array_equal(ne[i, idx], rneff)
+        if i == 0:
+            assert np.abs(dg[0, idx] - rnact).max() <= 1
+
+
 def _four_bin_window_share(D, th):
     """Per template, the share of its active tranches that sit in 32-tranche blocks whose
     general-form bins all lie in jp = -2 .. 1 with at least one lane beyond jp = -1, 0:
