@@ -292,15 +292,18 @@ def pso(args):
 def tdi(args):
     """Throughput of the statistic with the TDI-1.5 response (code 2) against the
     long-wavelength one (code 1) on the bench's two-year workload: 1e6 templates,
-    N_seg 256/64/16 in one pass. The timing does not depend on the data's content;
-    parity of the TDI path is tested on a 45-day grid whose injections went through
-    the time-domain single-link response, and on templates sampled from this launch."""
+    N_seg 256/64/16 in one pass (--n-templates for another bank size). The timing does
+    not depend on the data's content; parity of the TDI path is tested on a 45-day grid
+    whose injections went through the time-domain single-link response, and on
+    templates sampled from this launch."""
     import torch
     from paper_2510_19047_b300 import synth
     from paper_2510_19047_b300.binding import TFS
     D = synth.cached(synth.two_year_two_channel)
-    th = torch.from_numpy(synth.two_year_bank(1_000_000, seed=2002)).cuda()
-    out = {"study": "tdi", "workload": "AE-2yr-2048x6144, 1e6 templates, N_seg 256/64/16"}
+    n = int(getattr(args, "n_templates", 1_000_000))
+    th = torch.from_numpy(synth.two_year_bank(n, seed=2002)).cuda()
+    out = {"study": "tdi", "workload": "AE-2yr-2048x6144, %s templates, N_seg 256/64/16"
+                                       % ("%.0e" % n).replace("e+0", "e")}
     for resp in (1, 2):
         c = TFS(0, pn_order=1, response=resp, profile=1)
         c.load_tf_data(D.d, D.dt, D.dT)
@@ -315,7 +318,7 @@ def tdi(args):
             e1.synchronize()
             ss.append(e0.elapsed_time(e1))
             ks.append(c.last_profile()["statistic"])
-        out[f"response{resp}"] = {"templates_per_s": 1e6 / (statistics.median(ss) / 1000.0),
+        out[f"response{resp}"] = {"templates_per_s": n / (statistics.median(ss) / 1000.0),
                                   "kernel_ms": statistics.median(ks)}
         _, _, dg = c.eval_statistic(th, [256, 64, 16], diag=True)
         units = int(dg[0].sum().item())
