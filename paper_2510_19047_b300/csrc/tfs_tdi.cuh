@@ -35,6 +35,11 @@ struct TdiMath<double> {
     const double px = kPi * x;
     return fabs(px) < 1e-6 ? 1.0 - px * px / 6.0 : sinpi(x) / px;
   }
+  // pi a sinc(pi a u) = sin(pi a u) / u
+  __device__ static double pi_a_sinc(double a, double u) {
+    const double x = a * u, px = kPi * x;
+    return fabs(px) < 1e-6 ? kPi * a * (1.0 - px * px / 6.0) : sinpi(x) / u;
+  }
 };
 
 template <>
@@ -48,6 +53,16 @@ struct TdiMath<float> {
     if (fabsf(px) < 1e-3f) return 1.0f - px * px * (1.0f / 6.0f);
     const float r = x - 2.0f * rint_small(0.5f * x);  // sin(pi x) = sin(pi r), |r| <= 1
     return __sinf(3.141592654f * r) * rcp_approx(px);
+  }
+  // pi a sinc(pi a u) = sin(pi a u) / u (the series below |pi a u| = 1e-3)
+  __device__ static float pi_a_sinc(float a, float u) {
+    const float x = a * u;
+    if (fabsf(x) < 1e-3f / 3.141592654f) {
+      const float px = 3.141592654f * x;
+      return 3.141592654f * a * (1.0f - px * px * (1.0f / 6.0f));
+    }
+    const float r = x - 2.0f * rint_small(0.5f * x);
+    return __sinf(3.141592654f * r) * rcp_approx(u);
   }
 };
 
@@ -160,32 +175,40 @@ __device__ __forceinline__ void tdi_transfer_geom(T f, const TdiGeom<T>& G, T nx
   const Cplx<T> q01 = nPn(0), q02 = nPn(1), q12 = nPn(2);
   const T fL = f * L;
   // both directions of an arm share the phase factor (k.(p_s + p_r) is symmetric) and
-  // differ in the sinc argument (1 - k.n versus 1 + k.n)
-  auto arm = [&](int i, int j, Cplx<T> q, Cplx<T>& Gij, Cplx<T>& Gji) {
+  // differ in the sinc argument (1 - k.n versus 1 + k.n): G_ij = a_ij e, G_ji = a_ji e
+  // with e = i q e^{i ph} and a = pi f L sinc(pi f L (1 -+ k.n))
+  auto arm = [&](int i, int j, Cplx<T> q, Cplx<T>& e, T& aij, T& aji) {
     const T kn = (kp[j] - kp[i]) * iL;  // k . n_ij
     T s, c;
     M::cis_cycles(T(-0.5) * f * (L + kp[i] + kp[j]), s, c);
-    const Cplx<T> eq = cmul(Cplx<T>{c, s}, Cplx<T>{-q.im, q.re});  // i q e^{i ph}
-    const T pfl = T(kPi) * fL;
-    const T aij = pfl * M::sinc_pi(fL * (T(1) - kn)), aji = pfl * M::sinc_pi(fL * (T(1) + kn));
-    Gij = {aij * eq.re, aij * eq.im};
-    Gji = {aji * eq.re, aji * eq.im};
+    e = cmul(Cplx<T>{c, s}, Cplx<T>{-q.im, q.re});
+    aij = M::pi_a_sinc(fL, T(1) - kn);
+    aji = M::pi_a_sinc(fL, T(1) + kn);
   };
-  Cplx<T> G01, G10, G02, G20, G12, G21;
-  arm(0, 1, q01, G01, G10);
-  arm(0, 2, q02, G02, G20);
-  arm(1, 2, q12, G12, G21);
+  Cplx<T> e01, e02, e12;
+  T a01, a10, a02, a20, a12, a21;
+  arm(0, 1, q01, e01, a01, a10);
+  arm(0, 2, q02, e02, a02, a20);
+  arm(1, 2, q12, e12, a12, a21);
   T zs, zc;
   M::cis_cycles(-fL, zs, zc);
   const Cplx<T> z = {zc, zs};
+  // z G_ij = a_ij (z e): one rotation per arm
+  const Cplx<T> y01 = cmul(z, e01), y02 = cmul(z, e02), y12 = cmul(z, e12);
+  // X, Y, Z without their common factor w = 1 - z^2:
+  //   X = G10 + z G01 - G20 - z G02, Y = G21 + z G12 - G01 - z G10,
+  //   Z = G02 + z G20 - G12 - z G21
+  auto comb = [](T c1, Cplx<T> v1, T c2, Cplx<T> v2, T c3, Cplx<T> v3, T c4, Cplx<T> v4) {
+    return Cplx<T>{c1 * v1.re + c2 * v2.re - c3 * v3.re - c4 * v4.re,
+                   c1 * v1.im + c2 * v2.im - c3 * v3.im - c4 * v4.im};
+  };
+  const Cplx<T> X = comb(a10, e01, a01, y01, a20, e02, a02, y02);
+  const Cplx<T> Y = comb(a21, e12, a12, y12, a01, e01, a10, y01);
+  const Cplx<T> Z = comb(a02, e02, a20, y02, a12, e12, a21, y12);
+  // A = w (Z - X) / sqrt2, E = w (X - 2Y + Z) / sqrt6
   const Cplx<T> z2 = cmul(z, z);
-  // X, Y, Z share the factor w = 1 - z^2: the combinations A and E are formed first
-  // and multiplied by w / sqrt2 and w / sqrt6
   const T r2 = T(0.7071067811865476), r6 = T(0.4082482904638631);
   const Cplx<T> w2 = {(T(1) - z2.re) * r2, -z2.im * r2}, w6 = {(T(1) - z2.re) * r6, -z2.im * r6};
-  const Cplx<T> X = csub(cadd(G10, cmul(z, G01)), cadd(G20, cmul(z, G02)));
-  const Cplx<T> Y = csub(cadd(G21, cmul(z, G12)), cadd(G01, cmul(z, G10)));
-  const Cplx<T> Z = csub(cadd(G02, cmul(z, G20)), cadd(G12, cmul(z, G21)));
   TA = cmul(w2, csub(Z, X));
   TE = cmul(w6, Cplx<T>{X.re - T(2) * Y.re + Z.re, X.im - T(2) * Y.im + Z.im});
 }
