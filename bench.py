@@ -70,6 +70,10 @@ def parse():
     p.add_argument("--leg-seconds", type=float, default=4.0,
                    help="comparison legs: grow the batch (up to the whole bank) while a call "
                         "is estimated to stay under this")
+    p.add_argument("--warps-per-cta", type=int, default=0,
+                   help="pin the mixed launch's CTA size (0: autotuned)")
+    p.add_argument("--tile-variant", type=int, default=0,
+                   help="with --warps-per-cta: the mixed kernel's compiled tile variant")
     p.add_argument("--no-graph", action="store_true",
                    help="headline step without CUDA-graph replay")
     p.add_argument("--cpu-sample", type=int, default=1200)  # ~10-20 s of oracle work
@@ -171,12 +175,12 @@ def kernel_source_sha1():
     return h.hexdigest()
 
 
-def traffic_record(units):
-    """DRAM bytes (read + write) of one full-size statistic launch, from a committed
-    one-pass ncu capture of this bench's workload; valid only while the kernel source is
-    unchanged and the launch processes the same number of units. The traffic is not
-    proportional to the units (the grid is read about once per launch and then served
-    from L2), so a capture of another size is not rescaled."""
+def traffic_record(units, variant):
+    """DRAM bytes (read + write) of one full-size statistic launch of the given tile
+    variant, from a committed one-pass ncu capture of this bench's workload; valid only
+    while the kernel source is unchanged and the launch processes the same number of
+    units. The traffic is not proportional to the units (the grid is read about once
+    per launch and then served from L2), so a capture of another size is not rescaled."""
     path = os.path.join(ROOT, "profiles", "k_eval_mixed_dram.json")
     if not os.path.exists(path):
         return None
@@ -184,7 +188,10 @@ def traffic_record(units):
     h = kernel_source_sha1()
     if rec.get("source_sha1") != h or int(rec.get("units_per_launch", -1)) != units:
         return None
-    return rec
+    for r in rec.get("records", []):
+        if int(r["variant"]) == int(variant):
+            return r
+    return None
 
 
 def _timed_calls(ctx, th, reps, stream, flush):
@@ -316,6 +323,8 @@ def main():
     theta = torch.from_numpy(theta_np).cuda()
     use_graph = 0 if args.no_graph else 1
     ctx = TFS(local, path=args.path, pixel=args.pixel, profile=1, use_graph=use_graph)
+    if args.warps_per_cta:
+        ctx.set_options(warps_per_cta=args.warps_per_cta, tile_variant=args.tile_variant)
     ctx.load_tf_data(D.d, D.dt, D.dT)
     ctx.set_noise_weights(D.w, D.mask)
     stat = torch.empty((len(N_SEG), n), dtype=torch.float64, device="cuda")
@@ -374,7 +383,7 @@ def main():
     kms = statistics.mean(kern_ms)
     flops = units * flop_per_unit(D.n_chan)
     achieved = flops / (kms / 1000.0) / 1e12
-    trec = traffic_record(units)
+    trec = traffic_record(units, shape["variant"])
     roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / PEAK_FP32_TFLOPS,
             "traffic": trec["dram_bytes_per_launch"] if trec else None,

@@ -29,7 +29,15 @@ def test_clock_records_that_force_a_second_measurement():
     assert b.clocks_rejected({**ok, "sm_mhz": 1400.0})  # well below max, no reason: a lock
 
 
-def test_traffic_record_is_keyed_on_sources_and_units():
+def test_traffic_record_is_keyed_on_sources_units_and_variant():
+    import json
     b = _bench()
-    rec = b.traffic_record(-1)  # no capture has this unit count
-    assert rec is None
+    assert b.traffic_record(-1, 0) is None  # no capture has this unit count
+    rec = json.load(open(os.path.join(os.path.dirname(b.__file__), "profiles",
+                                      "k_eval_mixed_dram.json")))
+    if rec["source_sha1"] == b.kernel_source_sha1():
+        u = int(rec["units_per_launch"])
+        for r in rec["records"]:
+            assert b.traffic_record(u, r["variant"]) == r
+            assert r["dram_bytes_per_launch"] == r["dram_read_bytes"] + r["dram_write_bytes"]
+        assert b.traffic_record(u, 99) is None  # a variant without a capture
