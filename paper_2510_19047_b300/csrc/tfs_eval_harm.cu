@@ -71,20 +71,18 @@ struct HarmM {
   bool act;
   int kc;
   float aa, eps, sig, cpsi, spsi;
-  float a1;  // x - (k_c - 1) (NEAR only)
+  float a1;  // x - (k_c - 1)
   float Tr0, Ti0, Tr1, Ti1;
 };
 
-// x1 = x - (k_c + j) of window bin j; with NEAR, j = -1 comes from a1
-template <bool NEAR>
+// x1 = x - (k_c + j) of window bin j; j = -1 comes from a1
 __device__ __forceinline__ float bin_x1(const HarmM& q, float j) {
-  return NEAR && j == -1.0f ? q.a1 : q.aa - j;
+  return j == -1.0f ? q.a1 : q.aa - j;
 }
 
-// NEAR (every pixel type): the bin below f_nm (x1 = x - (k_c - 1)) and Psi are formed from
-// rb = x - rint(x), to full relative precision when f_nm is just above a bin, as in the
-// single-mode kernel.
-template <bool TDI, bool NEAR>
+// The bin below f_nm (x1 = x - (k_c - 1)) and Psi are formed from rb = x - rint(x), to
+// full relative precision when f_nm is just above a bin, as in the single-mode kernel.
+template <bool TDI>
 __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
                                          float2 Kh, int h, float sig_k, float dTf, int m) {
   HarmM q;
@@ -95,21 +93,15 @@ __device__ __forceinline__ HarmM harm_of(const EvalArgs& a, const TrackH& tk, co
   float kcf = rint_small(inband ? x.hi : 0.0f);  // ceil(x) = rint(x) (+1 if below x)
   // rb = x - rint(x) in [-1/2, 1/2]; rb > 0 exactly when ceil(x) = rint(x) + 1
   const float rb = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
-  if (NEAR) {
-    q.kc = int_small(rb > 0.f ? kcf + 1.0f : kcf);
-    q.aa = rb > 0.f ? rb - 1.0f : rb;
-    q.a1 = rb > 0.f ? rb : rb + 1.0f;
-  } else {
-    if (kcf < x.hi || (kcf == x.hi && x.lo > 0.f)) kcf += 1.0f;
-    q.kc = int_small(kcf);
-    q.aa = __fadd_rn(__fsub_rn(x.hi, kcf), x.lo);
-  }
+  q.kc = int_small(rb > 0.f ? kcf + 1.0f : kcf);
+  q.aa = rb > 0.f ? rb - 1.0f : rb;
+  q.a1 = rb > 0.f ? rb : rb + 1.0f;
   if (!inband || q.kc - kNFHalf < 1 || q.kc + kNFHalf > a.g.n_bins - 1) return q;
   q.act = true;
   const float fdh = nu.hi * tk.fdot;
   q.sig = sig_k * rsqrt_approx(fdh);
   q.eps = fdh * dTf * dTf;
-  const float psi = fmaf(2.0f, NEAR ? rb : q.aa, q.eps);  // Psi / pi (mod 2), reduced to [-1, 1]
+  const float psi = fmaf(2.0f, rb, q.eps);  // Psi / pi (mod 2), reduced to [-1, 1]
   __sincosf(3.141592654f * (psi - 2.0f * rint_small(0.5f * psi)), &q.spsi, &q.cpsi);
   // phase frac(nu K) - nu S in cycles, reduced in two steps as in the mixed kernel
   const df ph = df_sub(df{Kh.x, Kh.y}, df_mul(tk.S, nu));
@@ -153,14 +145,13 @@ template <int NCH, int PIX, bool TDI>
 __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, const TplMix* cptr,
                                           const float2* Kp, int m, float sig_k, float dTf) {
   using Ld = PixLoad<PIX>;
-  constexpr bool kNear = true;  // see harm_of
   const typename Ld::P* PX = (const typename Ld::P*)a.Umix;
   float N = 0.0f;
   for (int ha = 0; ha < a.harm.n; ++ha) {
-    const HarmM A = harm_of<TDI, kNear>(a, tk, cptr, Kp[ha], ha, sig_k, dTf, m);
+    const HarmM A = harm_of<TDI>(a, tk, cptr, Kp[ha], ha, sig_k, dTf, m);
     if (!A.act) continue;
     for (int hb = ha + 1; hb < a.harm.n; ++hb) {
-      const HarmM B = harm_of<TDI, kNear>(a, tk, cptr, Kp[hb], hb, sig_k, dTf, m);
+      const HarmM B = harm_of<TDI>(a, tk, cptr, Kp[hb], hb, sig_k, dTf, m);
       if (!B.act || abs(A.kc - B.kc) > 2 * kNFHalf) continue;
       // conj(T_a) T_b per channel
       const float y0r = A.Tr0 * B.Tr0 + A.Ti0 * B.Ti0, y0i = A.Tr0 * B.Ti0 - A.Ti0 * B.Tr0;
@@ -169,11 +160,9 @@ __device__ __noinline__ float cross_terms(const EvalArgs& a, const TrackH& tk, c
       for (int k = k0; k <= k1; ++k) {
         const float ja = (float)(k - A.kc), jb = (float)(k - B.kc);
         float war, wai, wbr, wbi;
-        const float xa = bin_x1<kNear>(A, ja), xb = bin_x1<kNear>(B, jb);
-        w_general(xa, kNear ? xa + A.eps : A.aa + A.eps - ja, A.sig, A.sig * (float)kPi, A.cpsi,
-                  A.spsi, true, war, wai);
-        w_general(xb, kNear ? xb + B.eps : B.aa + B.eps - jb, B.sig, B.sig * (float)kPi, B.cpsi,
-                  B.spsi, true, wbr, wbi);
+        const float xa = bin_x1(A, ja), xb = bin_x1(B, jb);
+        w_general(xa, xa + A.eps, A.sig, A.sig * (float)kPi, A.cpsi, A.spsi, true, war, wai);
+        w_general(xb, xb + B.eps, B.sig, B.sig * (float)kPi, B.cpsi, B.spsi, true, wbr, wbi);
         const float xr = war * wbr + wai * wbi, xi = war * wbi - wai * wbr;  // conj(Wa) Wb
         float2 ur, ui, w;
         Ld::cvt(Ld::raw(PX + (int64_t)k * a.pitch + m), ur, ui, w);
@@ -198,7 +187,6 @@ template <int NCH, int PIX, int PITCH, bool TDI>
 __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
   extern __shared__ float4 s_acc[];
   using Ld = PixLoad<PIX>;
-  constexpr bool kNear = true;  // see harm_of
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   // per warp: the fine-segment sums, then the lanes' TrackH (kTrkF x 32 floats)
@@ -336,7 +324,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
       for (int h = 0; h < H; ++h) {
         HarmM q;
         q.act = false;
-        if (act) q = harm_of<TDI, kNear>(a, get_track(tks), cptr, Kp[h], h, sig_k, dTf, m);
+        if (act) q = harm_of<TDI>(a, get_track(tks), cptr, Kp[h], h, sig_k, dTf, m);
         // general-bin range of the harmonic, joined over the warp (as in the mixed kernel)
         int jlo = 100, jhi = -100;
         if (q.act) {
@@ -410,7 +398,7 @@ __global__ void __launch_bounds__(256, TFS_HARM_MINB) k_eval_harm(EvalArgs a) {
             const float x1 = xx.x, x2 = xx.y;
             if (jp >= JLO && jp <= JHI) {
               float wr, wi;
-              const bool near = kNear && jp == -1;
+              const bool near = jp == -1;
               w_general(near ? q.a1 : x1, near ? q.a1 + q.eps : x2, q.sig, spi, q.cpsi, q.spsi,
                         true, wr, wi);
               acc_general(s, cur_r, cur_i, cur_w, wr, wi);
