@@ -9,10 +9,13 @@ The arithmetic lives in ``tfs_oracle.cpp`` (C++17, FP64, OpenMP over templates);
 module compiles it on first use and wraps its ``extern "C"`` entry points with numpy.
 Every function cites, in the C++ source, the passage of the paper it follows.
 
-Functions whose exact numeric form is not fixed by the paper and is therefore only
-pinned through invariants ("parity unpinned" for the exact form): the long-wavelength
-A/E detector tensors and the 1PN TaylorT3 coefficients (pinned only through
-f = (1/2pi) dPhi/dt, the Newtonian limit and the tensor invariants).
+Functions whose exact numeric form the paper does not fix, and what pins them: the
+long-wavelength A/E detector tensors (the closed-form antenna power of two 90-degree
+Michelsons 45 degrees apart pins the constellation's tilt and normal, the polarisation
+tensors and the amplitude factors; the in-plane orientation at t = 0 is a convention
+of the detector model and stays "parity unpinned"), and the 1PN TaylorT3 coefficients
+(pinned through f = (1/2pi) dPhi/dt, the Newtonian limit and the paper's printed table
+of the injections' coalescence times).
 """
 from .build import load_library, build  # noqa: F401
 from .api import (  # noqa: F401
