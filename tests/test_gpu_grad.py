@@ -186,3 +186,30 @@ def test_templates_without_active_tranches_give_zeros(ae45, n):
     assert np.all(np.isfinite(u)) and np.all(np.isfinite(g))
     ref_u, _ = c.grad_statistic(th[:, ~idle][:, :32], 16)
     np.testing.assert_allclose(u[~idle][:32], ref_u, rtol=1e-12)  # work-item split may differ
+
+
+@pytest.mark.parametrize("response", [1, 2])
+def test_refine_launch_matches_oracle(response):
+    """The refine study's launch: 4096 candidates near the two-year bank's injections at
+    N_seg 16 in one gradient call (with the work-item split a batch of this size takes),
+    with the long-wavelength and the TDI-1.5 response; 32 candidates spread over the
+    batch against the oracle at the bounds above."""
+    from paper_2510_19047_b300.binding import TFS
+    D = synth.cached(synth.two_year_two_channel)
+    cand = synth.candidates_near(D.injections, 4096, seed=2005)
+    c = TFS(0, pn_order=D.pn_order, response=response)
+    c.load_tf_data(D.d, D.dt, D.dT, D.t0)
+    c.set_noise_weights(D.w, D.mask)
+    u, g = c.grad_statistic(cand, 16)
+    idx = np.linspace(0, cand.shape[1] - 1, 32).astype(int)
+    u, g = np.asarray(u)[idx], np.asarray(g)[:, idx]
+    kw = dict(pn_order=1, response=response)
+    ref_u, ref_g = oracle.gradient(D.d, D.w, D.mask, cand[:, idx], 16, D.dT, **kw)
+    S = oracle.gradient_scale(D.d, D.w, D.mask, cand[:, idx], 16, D.dT, tranche_level=True, **kw)
+    np.testing.assert_allclose(u, ref_u, rtol=1e-4)
+    assert np.all(np.abs(g[3]) <= PHI0_TOL * ref_u)
+    for p in (0, 1, 2, 4, 5, 6, 7):
+        err = np.abs(g[p] - ref_g[p])
+        assert np.all(err <= GRAD_TOL * S[p]), (p, (err / S[p]).max())
+        big = np.abs(ref_g[p]) >= 0.2 * S[p]
+        assert np.all(err[big] <= 1e-4 * np.abs(ref_g[p][big])), p
