@@ -384,6 +384,29 @@ def test_two_year_full_bank_sampled(two_year):
             assert rel_err(got[i], ref)[0] < tol, (path, L)
 
 
+@pytest.mark.parametrize("pixel", ["f32", "bf16"])
+def test_two_year_full_bank_sampled_pixels(two_year, pixel):
+    """The bench bank (1e6 templates, N_seg 256/64/16 in one mixed launch) with FP32
+    pixels (the bench's equal-accuracy leg, held to the FP32 path's 1e-4) and with BF16
+    u (a precision-study variant, at its stated bound): 120 templates spread over the
+    sorted queue's range against the oracle, N_eff exact."""
+    import torch
+    D = two_year
+    lev = [256, 64, 16]
+    th = synth.two_year_bank(1_000_000, seed=2002)
+    c = ctx_for(D, "mixed", pixel)
+    st, ne, _ = c.eval_statistic(torch.from_numpy(th).cuda(), lev)
+    st, ne = st.cpu().numpy(), ne.cpu().numpy()
+    assert np.all(np.isfinite(st)) and np.all(st >= 0)
+    idx = np.linspace(0, th.shape[1] - 1, 120).astype(int)
+    for i, L in enumerate(lev):
+        ref, rneff, _, _ = oracle.statistic(D.d, D.w, D.mask, th[:, idx], L, D.dT,
+                                            pn_order=1, response=1)
+        mx, p99 = rel_err(st[i, idx], ref)
+        assert mx < TOL[("mixed", pixel)][0] and p99 < TOL[("mixed", pixel)][1], (L, mx, p99)
+        assert np.array_equal(ne[i, idx], rneff)
+
+
 def test_two_year_full_bank_sampled_tdi(two_year):
     """The TDI study's workload: the bench bank (1e6 templates, N_seg 256/64/16 in one
     mixed launch, FP16 pixels) with the TDI-1.5 response (code 2): 120 templates spread
